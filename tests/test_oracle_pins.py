@@ -1,0 +1,539 @@
+"""Pins of the FP64 oracle against facts the paper or the mathematics fixes.
+
+Each test pins one oracle function to something other than itself: a closed form,
+brute force on a tiny input, a textbook routine, an identity of the paper
+(Prop. 5.1, eq. 2.7, Galerkin, Thm 5.6, Thm 3.2), or the paper's two-level bound.
+"""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+import fegen
+import oracle as O
+import oracle.lsamg_oracle as OL
+
+
+def _cfg(cfg, N):
+    c = fegen.config(cfg, N=N)
+    mats = c["elem_mats"] if c["coef"] is None else c["elem_mats"] * c["coef"][:, None, None]
+    return c, np.ascontiguousarray(mats)
+
+
+@pytest.fixture(scope="module")
+def cfg1():
+    c, mats = _cfg(1, 16)
+    H = O.setup(c["n"], c["elem_dofs"], mats, c_tau=c["c_tau"])
+    return c, mats, H
+
+
+# ----------------------------------------------------------------------------- generator
+def test_generator_sizes_match_mesh_counts():
+    # DOF counts of the five workloads (edge/interior/vertex/node counts of the meshes)
+    N, k = 256, 3
+    assert 2 * N * (N + 1) * (k + 1) + N * N * 2 * k * (k + 1) == 2_099_200
+    assert fegen.rt_quad(16, 0, 1e-4)[0] == 544
+    assert fegen.rt_quad(128, 1, 1e-6)[0] == 131_584
+    assert 4 * 513 ** 2 == 1_052_676 and fegen.bfs_quad(4)[0] == 4 * 25
+    assert 3 * 97 ** 3 == 2_738_019 and fegen.q2_elasticity(2)[0] == 3 * 5 ** 3
+    n, d, K = fegen.rt_quad(4, 3, 1e-6)
+    assert n == 2 * 4 * 5 * 4 + 16 * 24 and d.shape == (16, 40)
+    # every DOF is used, edge DOFs shared by at most two elements
+    cnt = np.bincount(d.ravel(), minlength=n)
+    assert cnt.min() == 1 and cnt.max() == 2
+
+
+def test_rt0_element_closed_form():
+    # RT_[0] on the unit reference square: div u = (c1 - c0) + (c3 - c2) and the mass of
+    # the linear-in-normal-direction component is [[1/3, 1/6], [1/6, 1/3]] per component.
+    bh2 = 0.37
+    K = fegen._rt_ref(0, bh2, 2)
+    d = np.array([-1.0, 1.0, -1.0, 1.0])
+    Mx = np.array([[1 / 3, 1 / 6], [1 / 6, 1 / 3]])
+    ref = np.outer(d, d) + bh2 * sla.block_diag(Mx, Mx)
+    np.testing.assert_allclose(K, ref, rtol=0, atol=1e-14)
+
+
+# ----------------------------------------------------------------------------- Gram factor
+def test_element_gram_reconstructs_and_rank():
+    c, mats = _cfg(4, 2)
+    G0 = OL.element_gram(mats[1])         # interior element: 6 rigid-body modes
+    assert G0.shape == (81 - 6, 81)
+    np.testing.assert_allclose(G0.T @ G0, mats[1], atol=1e-12 * np.abs(mats[1]).max())
+    G1 = OL.element_gram(mats[0])         # Nitsche-clamped element: full rank
+    assert G1.shape[0] == 81
+    with pytest.raises(OL.NotSPSD):
+        OL.element_gram(np.diag([1.0, -1.0]))
+    # non-uniqueness (Section 5.2): U G gives the same block
+    U, _ = np.linalg.qr(np.random.default_rng(0).standard_normal((81, 81)))
+    np.testing.assert_allclose((U @ G1).T @ (U @ G1), mats[0], atol=1e-11 * np.abs(mats[0]).max())
+
+
+def test_gram_stacking_prop51(cfg1):
+    c, mats, H = cfg1
+    L0 = H.levels[0]
+    A = L0.A
+    # A = G^T G with G stacked from G_T R_T (Prop. 5.1)
+    rows = []
+    for dofs, GT in zip(L0.elems, L0.G):
+        R = np.zeros((GT.shape[0], c["n"]))
+        R[:, dofs] = GT
+        rows.append(R)
+    G = np.vstack(rows)
+    np.testing.assert_allclose(G.T @ G, A.toarray(), atol=1e-12 * abs(A).max())
+    x = np.random.default_rng(1).standard_normal(c["n"])
+    np.testing.assert_allclose(O.gram_spmv(L0.elems, L0.G, x), A @ x, rtol=1e-12, atol=1e-12 * np.abs(A @ x).max())
+
+
+# ----------------------------------------------------------------------------- hash / MIS(2)
+def test_hash32_is_a_bijection():
+    x = np.arange(1 << 20, dtype=np.uint64) * np.uint64(2654435761) & np.uint64(0xFFFFFFFF)
+    h = O.hash32(x)
+    # invert each step: xorshift-right by s is undone by repeated application; the
+    # multipliers are odd so they have inverses mod 2^32
+    m = (1 << 32) - 1
+
+    def unxs(y, s):
+        r = y.copy()
+        for _ in range(32 // s + 1):
+            r = y ^ (r >> np.uint64(s))
+        return r
+
+    y = unxs(h, 16)
+    y = (y * np.uint64(pow(0x846CA68B, -1, 1 << 32))) & np.uint64(m)
+    y = unxs(y, 15)
+    y = (y * np.uint64(pow(0x7FEB352D, -1, 1 << 32))) & np.uint64(m)
+    y = unxs(y, 16)
+    np.testing.assert_array_equal(y, x)
+    assert len(np.unique(h)) == len(h)
+
+
+def _random_graph(n, p, seed):
+    rng = np.random.default_rng(seed)
+    M = rng.random((n, n)) < p
+    M = np.triu(M, 1)
+    M = M | M.T | np.eye(n, dtype=bool)
+    return sp.csr_matrix(M.astype(float))
+
+
+def _greedy_mis2(S, prio):
+    """Lexicographically-first distance-2 MIS: visit nodes by descending (prio, index)."""
+    n = S.shape[0]
+    S2 = (S @ S).toarray() > 0
+    order = sorted(range(n), key=lambda i: (int(prio[i]), i), reverse=True)
+    chosen = np.zeros(n, bool)
+    for i in order:
+        if not (chosen & S2[i]).any():
+            chosen[i] = True
+    return chosen
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_mis2_equals_greedy_in_priority_order(seed):
+    S = _random_graph(60, 0.05, seed)
+    prio = O.hash32(np.arange(60))
+    st = O.mis2(S, prio)
+    np.testing.assert_array_equal(st == 1, _greedy_mis2(S, prio))
+
+
+def test_mis2_on_mesh_graph_brute_force():
+    c, _ = _cfg(1, 8)
+    S = O.structural_graph(c["n"], c["elem_dofs"])
+    prio = O.hash32(np.arange(c["n"]))
+    np.testing.assert_array_equal(O.mis2(S, prio) == 1, _greedy_mis2(S, prio))
+
+
+def test_aggregation_pass_rules_brute_force():
+    c, _ = _cfg(1, 8)
+    n = c["n"]
+    S = O.structural_graph(n, c["elem_dofs"])
+    prio = O.hash32(np.arange(n))
+    agg, nroot = O.aggregate_mis2(S, prio)
+    roots = np.flatnonzero(O.mis2(S, prio) == 1)
+    assert nroot == len(roots)
+    Sd = S.toarray() > 0
+    # partition, one root per aggregate, ids ascending in root index
+    assert agg.min() == 0 and agg.max() == nroot - 1
+    np.testing.assert_array_equal(agg[roots], np.arange(nroot))
+    first = np.zeros(n, bool)
+    for i, r in enumerate(roots):
+        first[Sd[r]] = True
+        assert (agg[Sd[r]] == i).all()
+    for p in np.flatnonzero(~first):
+        cand = [q for q in np.flatnonzero(Sd[p]) if first[q]]
+        q = min(cand, key=lambda q: (int(prio[q]), q))
+        assert agg[p] == agg[q]
+
+
+def test_second_pass_graph_brute_force():
+    c, _ = _cfg(1, 8)
+    n = c["n"]
+    S = O.structural_graph(n, c["elem_dofs"])
+    a1, n1 = O.aggregate_mis2(S, O.hash32(np.arange(n)))
+    Sd = S.toarray() > 0
+    adj = np.zeros((n1, n1), bool)
+    for p in range(n):
+        for q in np.flatnonzero(Sd[p]):
+            adj[a1[p], a1[q]] = True
+    a2, n2 = O.aggregate_mis2(sp.csr_matrix(adj.astype(float)), O.hash32(np.arange(n1)))
+    agg, nagg = O.aggregate_two_pass(S, 2)
+    np.testing.assert_array_equal(agg, a2[a1])
+    assert nagg == n2
+
+
+# ----------------------------------------------------------------------------- closure
+def test_closure_equals_row_definition_thm56(cfg1):
+    c, mats, H = cfg1
+    L0 = H.levels[0]
+    rng = np.random.default_rng(11)
+
+    def row_sets(rotate):
+        rows, owner = [], []
+        for t, (dofs, GT) in enumerate(zip(L0.elems, L0.G)):
+            if rotate:   # footnote to Assumption 5.5: U G_T has a full-support row
+                U, _ = np.linalg.qr(rng.standard_normal((GT.shape[0], GT.shape[0])))
+                GT = U @ GT
+                assert any(np.all(r != 0.0) for r in GT)
+            for r in GT:
+                rows.append(set(int(d) for d, v in zip(dofs, r) if v != 0.0))
+                owner.append(t)
+        return rows, owner
+
+    for rotate in (False, True):
+        rows, owner = row_sets(rotate)
+        for i in range(L0.nagg):
+            w = set(np.flatnonzero(L0.agg == i).tolist())
+            touching = [j for j, s in enumerate(rows) if s & w]          # eq. 2.3
+            OmG = set().union(*[rows[j] for j in touching])              # eq. 2.4
+            Omcl = set(L0.Omega[i].tolist())                             # Def. 5.4
+            assert OmG <= Omcl                                           # Thm 5.6, always
+            if rotate:
+                assert OmG == Omcl                                       # Thm 5.6 under Ass. 5.5
+            assert sorted(w) == L0.omega[i].tolist()
+        if rotate:
+            for j, s in enumerate(rows):                                 # eq. 2.5
+                assert len(set(L0.agg[list(s)].tolist())) == L0.mult[owner[j]]
+    assert L0.tau == pytest.approx(0.75 * L0.mult.max())
+
+
+# ----------------------------------------------------------------------------- splitting
+def test_exact_spsd_splitting_eq27(cfg1):
+    c, mats, H = cfg1
+    L0 = H.levels[0]
+    n = c["n"]
+    total = np.zeros((n, n))
+    for i in range(L0.nagg):
+        At, Aww, loc = OL.local_blocks(i, L0.elems, L0.mats, L0.mult, L0.ael, L0.omega, L0.Omega)
+        w = np.linalg.eigvalsh(At)
+        assert w[0] >= -1e-12 * w[-1]
+        total[np.ix_(loc, loc)] += At
+        # At = H^T H with H = W^{1/2} G(rows touching omega_i, Omega_i)  (eq. 2.6)
+        pos = {int(g): j for j, g in enumerate(loc)}
+        Hrows = []
+        for t in L0.ael[i]:
+            for r in L0.G[t]:
+                h = np.zeros(len(loc))
+                h[[pos[int(d)] for d in L0.elems[t]]] = r / np.sqrt(L0.mult[t])
+                Hrows.append(h)
+        Hm = np.array(Hrows)
+        np.testing.assert_allclose(Hm.T @ Hm, At, atol=1e-12 * abs(At).max())
+        # Aww is the principal submatrix of A on omega_i
+        np.testing.assert_allclose(Aww, L0.A[L0.omega[i]][:, L0.omega[i]].toarray(), atol=1e-13 * abs(Aww).max())
+    Ad = L0.A.toarray()
+    np.testing.assert_allclose(total, Ad, atol=1e-12 * abs(Ad).max())
+
+
+def test_theorem32_round_trip(cfg1):
+    # Thm 3.2 (splitting => local Gram): factor each splitting piece and stack
+    c, mats, H = cfg1
+    L0 = H.levels[0]
+    n = c["n"]
+    rows = []
+    for i in range(L0.nagg):
+        At, _, loc = OL.local_blocks(i, L0.elems, L0.mats, L0.mult, L0.ael, L0.omega, L0.Omega)
+        Gi = OL.element_gram(At, check=False)
+        R = np.zeros((Gi.shape[0], n))
+        R[:, loc] = Gi
+        rows.append(R)
+    G = np.vstack(rows)
+    Ad = L0.A.toarray()
+    np.testing.assert_allclose(G.T @ G, Ad, atol=1e-11 * abs(Ad).max())
+
+
+# ----------------------------------------------------------------------------- local GEP
+def test_local_gep_residual_and_normalisation():
+    # well-conditioned RT_[1] (beta = 1): an independently formed Schur complement (SVD
+    # pseudo-inverse) agrees with the oracle's to rounding, so the residual bound is tight
+    n, d, K = fegen.rt_quad(6, 1, 1.0)
+    H = O.setup(n, d, np.broadcast_to(K, (d.shape[0],) + K.shape), opts=dict(max_levels=2))
+    L0 = H.levels[0]
+    for i in range(L0.nagg):
+        At, Aww, _ = OL.local_blocks(i, L0.elems, L0.mats, L0.mult, L0.ael, L0.omega, L0.Omega)
+        Z, mu, gap = OL.local_problem(At, Aww, L0.tau)
+        nw = Aww.shape[0]
+        S = At[:nw, :nw] - At[:nw, nw:] @ np.linalg.pinv(At[nw:, nw:], rcond=1e-15) @ At[nw:, :nw]
+        kept = mu[mu < 1 / L0.tau]
+        np.testing.assert_allclose(Z.T @ Aww @ Z, np.eye(Z.shape[1]), atol=1e-9)
+        R = S @ Z - Aww @ Z * kept
+        assert np.abs(R).max() <= 1e-10 * abs(S).max() * max(1, np.abs(Z).max())
+        assert np.all(np.diff(mu) >= -1e-12)
+        for j in range(Z.shape[1]):
+            assert Z[np.argmax(np.abs(Z[:, j])), j] > 0
+
+
+def test_schur_equals_gram_projection_form():
+    # S = At_ww - At_wG At_GG^+ At_Gw equals H_w^T (I - Q Q^T) H_w, Q an orthonormal basis
+    # of range(H_G), for At = H^T H (Section 2, Schur complement of the splitting)
+    rng = np.random.default_rng(3)
+    Hm = rng.standard_normal((30, 12))
+    Hm[:, 8:] = Hm[:, 4:8] @ rng.standard_normal((4, 4))      # rank-deficient Gamma block
+    At = Hm.T @ Hm
+    nw = 5
+    S = At[:nw, :nw] - At[:nw, nw:] @ OL.pinv_sym(At[nw:, nw:]) @ At[nw:, :nw]
+    Q, Rr, piv = sla.qr(Hm[:, nw:], pivoting=True, mode="economic")
+    r = int((np.abs(np.diag(Rr)) > 1e-10 * abs(Rr[0, 0])).sum())
+    Q = Q[:, :r]
+    Hw = Hm[:, :nw]
+    np.testing.assert_allclose(S, Hw.T @ (Hw - Q @ (Q.T @ Hw)), atol=1e-10 * abs(At).max())
+
+
+def test_full_pencil_eq28_matches_reduced_eq29():
+    # well-conditioned RT_[1] (beta = 1) so that QZ on the full pencil is accurate
+    n, d, K = fegen.rt_quad(4, 1, 1.0)
+    mats = np.broadcast_to(K, (d.shape[0],) + K.shape)
+    H = O.setup(n, d, mats, opts=dict(max_levels=2))
+    L0 = H.levels[0]
+    for i in range(L0.nagg):
+        At, Aww, loc = OL.local_blocks(i, L0.elems, L0.mats, L0.mult, L0.ael, L0.omega, L0.Omega)
+        nw = Aww.shape[0]
+        AO = L0.A[loc][:, loc].toarray()
+        D = np.zeros_like(AO)
+        D[:nw, :nw] = np.eye(nw)
+        lam = sla.eigvals(D @ AO @ D, At)
+        lam = np.real(lam[np.isfinite(lam)])
+        lam = np.sort(lam[np.abs(lam) > 1e-8])
+        _, mu, _ = OL.local_problem(At, Aww, L0.tau)
+        ref = np.sort(1.0 / mu[mu > 1e-12])
+        np.testing.assert_allclose(lam, ref, rtol=1e-7)
+
+
+def _discrete_curl_rt0(N):
+    """curl of each Q1 vertex hat, as RT_[0] nodal normal-component DOFs (fegen numbering)."""
+    h = 1.0 / N
+    nV = (N + 1) * N
+    modes = []
+    for J in range(N + 1):
+        for I in range(N + 1):
+            v = np.zeros(2 * N * (N + 1))
+            if J < N:
+                v[I * N + J] = -1 / h                       # vertical edge above the vertex
+            if J > 0:
+                v[I * N + J - 1] = 1 / h                    # vertical edge below
+            if I < N:
+                v[nV + J * N + I] = 1 / h                   # horizontal edge to the right
+            if I > 0:
+                v[nV + J * N + I - 1] = -1 / h              # horizontal edge to the left
+            modes.append(v)
+    return np.array(modes)
+
+
+def test_weak_approximation_bound_random_and_curl_modes(cfg1):
+    c, mats, H = cfg1
+    L0 = H.levels[0]
+    N = 16
+    # the constructed curl modes are divergence free (beta = 0 form annihilates them)
+    n0, d0, K0 = fegen.rt_quad(N, 0, 0.0, 2)
+    A0 = O.assemble(n0, d0, np.broadcast_to(K0, (d0.shape[0],) + K0.shape))
+    curls = _discrete_curl_rt0(N)
+    assert max(abs(v @ (A0 @ v)) for v in curls) < 1e-12 * max(v @ v for v in curls)
+    blocks = []
+    taumax = 0.0
+    for i in range(L0.nagg):
+        At, Aww, _ = OL.local_blocks(i, L0.elems, L0.mats, L0.mult, L0.ael, L0.omega, L0.Omega)
+        Z, mu, _ = OL.local_problem(At, Aww, L0.tau)
+        disc = mu[mu >= 1 / L0.tau]
+        if len(disc):
+            taumax = max(taumax, 1.0 / disc.min())
+        blocks.append((L0.omega[i], Aww, Z))
+    assert taumax <= L0.tau
+    rng = np.random.default_rng(7)
+    vs = list(rng.standard_normal((5, c["n"]))) + list(curls[::7])
+    for v in vs:
+        lhs = 0.0
+        for w, Aww, Z in blocks:
+            vw = v[w]
+            e = vw - Z @ (Z.T @ (Aww @ vw))
+            lhs += e @ Aww @ e
+        rhs = v @ (L0.A @ v)
+        assert lhs <= taumax * rhs * (1 + 1e-8) + 1e-14 * abs(lhs)
+
+
+# ----------------------------------------------------------------------------- P / coarse
+def test_P_disjoint_support_and_galerkin(cfg1):
+    c, mats, H = cfg1
+    L0, L1 = H.levels[0], H.levels[1]
+    P = L0.P.tocoo()
+    colagg = np.repeat(np.arange(L0.nagg), L0.k)
+    assert np.all(L0.agg[P.row] == colagg[P.col])
+    Ac = (L0.P.T @ L0.A @ L0.P).toarray()
+    A1 = L1.A.toarray()
+    np.testing.assert_allclose(A1, Ac, atol=1e-12 * abs(Ac).max())
+    for cm, Ag, Gg in zip(L1.elems, L1.mats, L1.G):
+        np.testing.assert_allclose(Gg.T @ Gg, Ag, atol=1e-12 * abs(Ag).max())
+    # G_c = G P on the unmerged elements, merged per group
+    for gi, grp in enumerate(L0.cgroups):
+        cm = L1.elems[gi]
+        acc = np.zeros((len(cm), len(cm)))
+        scale = 0.0
+        for t in grp:
+            RTP = L0.P[L0.elems[t]][:, cm].toarray()
+            Gc = L0.G[t] @ RTP
+            acc += Gc.T @ Gc
+            # G_T^T G_T = A_T holds to eps*||A_T||; the product carries ||R_T P||^2 of it
+            scale += np.linalg.norm(L0.mats[t], 2) * np.linalg.norm(RTP, 2) ** 2
+        np.testing.assert_allclose(acc, L1.mats[gi], rtol=0, atol=1e-12 * scale)
+    assert L1.n < L0.n
+
+
+# ----------------------------------------------------------------------------- colouring / cycle
+def test_colouring_greedy_and_conflict_free(cfg1):
+    c, mats, H = cfg1
+    L0 = H.levels[0]
+    nagg = L0.nagg
+    meets = [set(t for t, d in enumerate(L0.elems) if set(d.tolist()) & set(L0.Omega[i].tolist()))
+             for i in range(nagg)]
+    for i in range(nagg):
+        nb = [k for k in range(nagg) if k != i and meets[i] & meets[k]]
+        used = set(L0.colour[k] for k in nb if k < i)
+        mex = 0
+        while mex in used:
+            mex += 1
+        assert L0.colour[i] == mex
+        assert all(L0.colour[k] != L0.colour[i] for k in nb)
+
+
+def _dense_prec(H):
+    n = H.levels[0].n
+    return np.column_stack([O.vcycle(H, e) for e in np.eye(n)])
+
+
+def test_vcycle_symmetric_and_contractive(cfg1):
+    # tight on a well-conditioned three-level RT_[1] hierarchy (beta = 1, forced 3 levels)
+    n, d, K = fegen.rt_quad(8, 1, 1.0)
+    Hw = O.setup(n, d, np.broadcast_to(K, (d.shape[0],) + K.shape),
+                 opts=dict(max_density=1.0, agg_passes=1, agg_passes_coarse=1))
+    assert len(Hw.levels) == 3
+    Binv = _dense_prec(Hw)
+    np.testing.assert_allclose(Binv, Binv.T, rtol=0, atol=1e-12 * abs(Binv).max())
+    A = Hw.levels[0].A.toarray()
+    lam = np.sort(np.real(sla.eigvals(Binv @ A)))
+    assert lam[0] > 0 and lam[-1] <= 1 + 1e-10
+    # cfg1 (kappa(A) ~ 1e10): symmetric to eps*kappa, spectrum in (0, 1]
+    c, mats, H = cfg1
+    Binv = _dense_prec(H)
+    np.testing.assert_allclose(Binv, Binv.T, rtol=0, atol=1e-6 * abs(Binv).max())
+    A = H.levels[0].A.toarray()
+    lam = np.sort(np.real(sla.eigvals(Binv @ A)))
+    assert lam[0] > 0 and lam[-1] <= 1 + 1e-5
+
+
+def test_within_colour_order_is_irrelevant(cfg1):
+    c, mats, H = cfg1
+    L0 = H.levels[0]
+    b = c["b"][0]
+    x1 = O.vcycle(H, b)
+    saved = L0.sweep
+    L0.sweep = sorted(range(L0.nagg), key=lambda i: (L0.colour[i], -i))
+    try:
+        x2 = O.vcycle(H, b)
+    finally:
+        L0.sweep = saved
+    np.testing.assert_allclose(x1, x2, rtol=1e-11, atol=1e-11 * abs(x1).max())
+
+
+def test_two_level_bound_KTG():
+    # Section 2: K_TG <= lambda_max(M_wJ^{-1} M~) tau_max, with K_TG = 1/lambda_min(B^{-1}A)
+    c, mats = _cfg(1, 8)
+    H = O.setup(c["n"], c["elem_dofs"], mats, opts=dict(max_levels=2), c_tau=0.75)
+    L0 = H.levels[0]
+    n = c["n"]
+    A = L0.A.toarray()
+    lam = np.sort(np.real(sla.eigvals(_dense_prec(H) @ A)))
+    KTG = 1.0 / lam[0]
+    Ef = np.eye(n)
+    for i in L0.sweep:
+        Om = L0.Omega[i]
+        R = np.zeros((len(Om), n))
+        R[np.arange(len(Om)), Om] = 1.0
+        Ef = (np.eye(n) - R.T @ np.linalg.solve(A[np.ix_(Om, Om)], R @ A)) @ Ef
+    Eb = np.linalg.solve(A, Ef.T @ A)
+    Mt_inv = (np.eye(n) - Eb @ Ef) @ np.linalg.inv(A)
+    MwJ = np.zeros((n, n))
+    taumax = 0.0
+    for i in range(L0.nagg):
+        w = L0.omega[i]
+        MwJ[np.ix_(w, w)] = A[np.ix_(w, w)]
+        At, Aww, _ = OL.local_blocks(i, L0.elems, L0.mats, L0.mult, L0.ael, L0.omega, L0.Omega)
+        _, mu, _ = OL.local_problem(At, Aww, L0.tau)
+        disc = mu[mu >= 1 / L0.tau]
+        if len(disc):
+            taumax = max(taumax, 1.0 / disc.min())
+    lmax = 1.0 / np.min(np.real(sla.eigvals(Mt_inv @ MwJ)))
+    assert KTG <= lmax * taumax * (1 + 1e-8)
+    assert taumax <= L0.tau
+
+
+# ----------------------------------------------------------------------------- solvers
+def test_pcg_matches_direct_solve(cfg1):
+    c, mats, H = cfg1
+    A = H.levels[0].A
+    b = c["b"][0]
+    x, it, hist = O.pcg(lambda v: A @ v, b, lambda r: O.vcycle(H, r))
+    xd = spla.spsolve(A.tocsc(), b)
+    assert np.linalg.norm(x - xd) <= 1e-6 * np.linalg.norm(xd)
+    assert np.linalg.norm(b - A @ x) <= 1e-8 * np.linalg.norm(b)
+    xf, itf, _ = O.fcg(lambda v: A @ v, b, lambda r: O.vcycle(H, r))
+    assert abs(itf - it) <= 1
+
+
+def test_hierarchy_stop_rules():
+    c, mats = _cfg(2, 16)
+    H = O.setup(c["n"], c["elem_dofs"], mats, c_tau=0.75)
+    assert len(H.levels) <= 3
+    last = H.levels[-1]
+    assert last.coarsest
+    assert (len(H.levels) == 3 or last.n < 10 or last.nnz / last.n ** 2 > 0.25)
+    for a, b in zip(H.levels[:-1], H.levels[1:]):
+        assert b.n < a.n
+
+
+# ----------------------------------------------------------------------------- adjoint
+def test_adjoint_gradient_against_central_differences():
+    # same RT_[1] space and theta distribution as the adjoint workload, with beta = 1 so that
+    # direct solves are accurate enough for central differences (the formula is beta-free)
+    c = fegen.config(5, N=4)
+    n, d, K0 = fegen.rt_quad(4, 1, 1.0, 3)
+    K = np.ascontiguousarray(np.broadcast_to(K0, (d.shape[0],) + K0.shape))
+    theta = c["coef"]
+    b, xs = c["b"][0], c["x_star"]
+
+    def solve_direct(th, rhs):
+        A = O.assemble(n, d, K * th[:, None, None])
+        return spla.spsolve(A.tocsc(), rhs)
+
+    A = O.assemble(n, d, K * theta[:, None, None])
+    H = O.setup(n, d, K * theta[:, None, None], c_tau=0.75)
+
+    def solve(rhs):
+        return O.pcg(lambda v: A @ v, rhs, lambda r: O.vcycle(H, r), rtol=1e-13)[0]
+
+    Lval, x, g = O.adjoint_grad(n, d, K, theta, b, xs, solve)
+    h = 1e-6
+    fd = np.empty(len(theta))
+    for e in range(len(theta)):
+        tp = theta.copy(); tp[e] += h
+        tm = theta.copy(); tm[e] -= h
+        xp = solve_direct(tp, b); xm = solve_direct(tm, b)
+        fd[e] = (0.5 * np.sum((xp - xs) ** 2) - 0.5 * np.sum((xm - xs) ** 2)) / (2 * h)
+    np.testing.assert_allclose(g, fd, rtol=1e-5, atol=1e-5 * np.abs(fd).max())
