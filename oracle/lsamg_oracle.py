@@ -45,7 +45,7 @@ EPS = np.finfo(np.float64).eps
 
 __all__ = [
     "hash32", "assemble", "element_gram", "structural_graph", "mis2", "aggregate_mis2",
-    "aggregate_two_pass", "closure", "local_problem", "Level", "Hierarchy", "setup",
+    "aggregate_two_pass", "closure", "local_problem", "local_problem_pinv", "local_gram_rows", "Level", "Hierarchy", "setup",
     "vcycle", "pcg", "fcg", "elem_grad", "adjoint_grad", "gram_spmv", "greedy_colouring",
     "options_default",
 ]
@@ -301,17 +301,24 @@ def pinv_sym(M):
     return (V[:, keep] / w[keep]) @ V[:, keep].T
 
 
-def local_problem(At, Aww, tau):
-    """Reduced local GEP (Section 2 eq. 2.9) written as S y = mu A_ww y with mu = 1/lambda:
-    S = At_ww - At_wG pinv(At_GG) At_Gw, keep mu < 1/tau_cut (lambda > tau_cut and the
-    +infinity modes ker S).  Basis A_ww-orthonormal, ascending mu, sign fixed so that the
-    largest-magnitude entry of each column is positive.
-    Returns (Z, mu_all, gap) with gap = min_k |mu_k tau - 1|."""
+TIE = 1e-9  # reading: keep mu*tau < 1 - TIE, so exact ties mu = 1/tau (from mesh symmetry) are
+            # discarded deterministically; tau_max <= tau_cut is unaffected
+
+
+def local_problem_pinv(At, Aww, tau):
+    """Reduced local GEP (Section 2 eq. 2.9) in the assembled form S y = mu A_ww y with
+    mu = 1/lambda: S = At_ww - At_wG pinv(At_GG) At_Gw.  Used by the pins on well-conditioned
+    inputs only: the eigh pseudo-inverse loses ~eps*kappa(At_GG)^2, so ill-conditioned blocks
+    go through the least-squares form ``local_problem``.  Returns (Z, mu, gap)."""
     nw = Aww.shape[0]
     Sw = At[:nw, :nw] - At[:nw, nw:] @ pinv_sym(At[nw:, nw:]) @ At[nw:, :nw]
     Sw = 0.5 * (Sw + Sw.T)
     mu, Y = sla.eigh(Sw, Aww)
-    keep = mu < 1.0 / tau
+    return _select(Y, mu, tau)
+
+
+def _select(Y, mu, tau):
+    keep = mu * tau < 1.0 - TIE
     Z = Y[:, keep].copy()
     for j in range(Z.shape[1]):
         k = int(np.argmax(np.abs(Z[:, j])))
@@ -319,6 +326,57 @@ def local_problem(At, Aww, tau):
             Z[:, j] = -Z[:, j]
     gap = float(np.min(np.abs(mu * tau - 1.0))) if len(mu) else np.inf
     return Z, mu, gap
+
+
+def local_gram_rows(i, elems, G, mult, ael, omega, Omega):
+    """Least-squares data of aggregate i (Section 2 eqs. 2.3-2.7), DOFs ordered [omega_i; Gamma_i]:
+    H = W^{1/2} G(R_omega_i, Omega_i) (rows of the elements touching omega_i, each scaled by
+    mult(T)^{-1/2}, eq. 2.6) so that At = H^T H (eq. 2.7), and F = G(R_omega_i, omega_i) so that
+    A_ww = R_w A R_w^T = F^T F (rows not touching omega_i vanish on omega_i)."""
+    w = np.asarray(omega[i], np.int64)
+    loc = np.concatenate([w, np.setdiff1d(Omega[i], w)])
+    pos = {int(g): j for j, g in enumerate(loc)}
+    nw = len(w)
+    blocks = []
+    for t in ael[i]:
+        GT = np.asarray(G[t], float)
+        if GT.size == 0:
+            continue
+        B = np.zeros((GT.shape[0], len(loc)))
+        B[:, [pos[int(g)] for g in elems[t]]] = GT
+        blocks.append((B, float(mult[t])))
+    Hm = np.vstack([B / np.sqrt(m) for B, m in blocks]) if blocks else np.zeros((0, len(loc)))
+    F = np.vstack([B[:, :nw] for B, _ in blocks]) if blocks else np.zeros((0, nw))
+    return Hm, F, loc
+
+
+def local_problem(Hm, F, nw, tau):
+    """Reduced local GEP (Section 2 eq. 2.9) A_ww u = lambda S u, solved as S y = mu A_ww y
+    with mu = 1/lambda, in least-squares form.  With At = H^T H the Schur complement with the
+    Moore-Penrose pseudo-inverse is S = Y^T Y, Y = (I - Q Q^T) H_omega, Q an orthonormal basis of
+    range(H_Gamma) (numerical rank at max(m, n) * eps * sigma_max, NumPy's matrix_rank rule);
+    A_ww = F^T F = R^T R (QR of F).  Then mu are the squared singular values of Y R^{-1} (zeros
+    for ker S, the +infinity modes) and y = R^{-1} v is A_ww-orthonormal.  Keep mu*tau < 1 - TIE,
+    ascending mu, largest-magnitude entry of each column positive.  Returns (Z, mu, gap)."""
+    HG = Hm[:, nw:]
+    Hw = Hm[:, :nw]
+    if HG.shape[1] > 0 and HG.shape[0] > 0:
+        U, sg, _ = np.linalg.svd(HG, full_matrices=False)
+        r = int((sg > max(HG.shape) * EPS * sg[0]).sum()) if sg[0] > 0 else 0
+        Q = U[:, :r]
+        Y = Hw - Q @ (Q.T @ Hw)
+    else:
+        Y = Hw
+    R = np.linalg.qr(F, mode="r")
+    M = sla.solve_triangular(R, Y.T, trans="T", lower=False).T      # Y R^{-1}
+    _, s, Vt = np.linalg.svd(M, full_matrices=True)
+    mu = np.zeros(nw)
+    mu[:len(s)] = s * s
+    order = np.argsort(mu, kind="stable")
+    mu = mu[order]
+    V = Vt.T[:, order]
+    Yv = sla.solve_triangular(R, V, lower=False)
+    return _select(Yv, mu, tau)
 
 
 # -----------------------------------------------------------------------------
@@ -366,6 +424,7 @@ class Level:
     k: np.ndarray = None
     off: np.ndarray = None
     gaps: np.ndarray = None
+    mu: list = None               # local eigenvalues mu (ascending) of every aggregate
     P: sp.csr_matrix = None
     colour: np.ndarray = None
     sweep: list = None            # aggregate order of the forward sweep
@@ -430,12 +489,13 @@ def _coarsen(lev, o, passes):
     agg, nagg = aggregate_two_pass(lev.S, passes)
     eagg, mult, ael, omega, Omega = closure(lev.elems, agg, nagg)
     tau = o["tau_c"] * float(mult.max())
-    Z, gaps = [], []
+    Z, gaps, mus = [], [], []
     for i in range(nagg):
-        At, Aww, _ = local_blocks(i, lev.elems, lev.mats, mult, ael, omega, Omega)
-        Zi, _, gap = local_problem(At, Aww, tau)
+        Hm, F, _ = local_gram_rows(i, lev.elems, lev.G, mult, ael, omega, Omega)
+        Zi, mui, gap = local_problem(Hm, F, len(omega[i]), tau)
         Z.append(Zi)
         gaps.append(gap)
+        mus.append(mui)
     k = np.array([z.shape[1] for z in Z], np.int64)
     nc = int(k.sum())
     if nc == 0 or nc >= lev.n:
@@ -452,6 +512,7 @@ def _coarsen(lev, o, passes):
     lev.agg, lev.nagg, lev.eagg, lev.mult, lev.tau = agg, nagg, eagg, mult, tau
     lev.ael, lev.omega, lev.Omega, lev.Z, lev.k, lev.off, lev.P = ael, omega, Omega, Z, k, off, P
     lev.gaps = np.array(gaps)
+    lev.mu = mus
     # Coarse cover (Section 2 end: A_c = P^T A P = (GP)^T (GP); Remark 5.2: a cover by
     # collections of elements induces a coarser Gram).  Elements whose coarse DOF maps
     # coincide (same set of touching aggregates) are merged into one coarse element with

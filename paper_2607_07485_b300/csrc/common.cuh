@@ -1,0 +1,174 @@
+// Shared device/host utilities of liblsamg: status handling, stream-ordered device
+// buffers, prefix sums, in-CTA sorting networks and CSR transposition.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+#include <utility>
+#include <algorithm>
+
+#include "../../include/lsamg.h"
+
+namespace lsamg {
+
+// ---------------------------------------------------------------------------------
+// Errors: C++ exceptions stay inside the library; the C ABI converts them to codes.
+// ---------------------------------------------------------------------------------
+struct Failure {
+    int code;
+    std::string msg;
+};
+
+[[noreturn]] inline void fail(int code, const std::string &msg) { throw Failure{code, msg}; }
+
+inline void cuda_check(cudaError_t e, const char *what, const char *file, int line) {
+    if (e == cudaSuccess) return;
+    int code = (e == cudaErrorMemoryAllocation) ? LSAMG_OOM : LSAMG_CUDA;
+    char buf[512];
+    snprintf(buf, sizeof buf, "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+    fail(code, buf);
+}
+#define CK(x) ::lsamg::cuda_check((x), #x, __FILE__, __LINE__)
+#define CK_LAUNCH() ::lsamg::cuda_check(cudaGetLastError(), "kernel launch", __FILE__, __LINE__)
+
+inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Stage trace on stderr when the environment variable LSAMG_TRACE is set.
+void trace(const char *fmt, ...);
+
+// ---------------------------------------------------------------------------------
+// Stream-ordered device buffer (cudaMallocAsync / cudaFreeAsync), move-only.
+// ---------------------------------------------------------------------------------
+template <class T>
+struct DBuf {
+    T *p = nullptr;
+    int64_t n = 0;
+    cudaStream_t s = nullptr;
+    DBuf() = default;
+    DBuf(const DBuf &) = delete;
+    DBuf &operator=(const DBuf &) = delete;
+    DBuf(DBuf &&o) noexcept { *this = std::move(o); }
+    DBuf &operator=(DBuf &&o) noexcept {
+        if (this != &o) {
+            release();
+            p = o.p; n = o.n; s = o.s;
+            o.p = nullptr; o.n = 0;
+        }
+        return *this;
+    }
+    ~DBuf() { release(); }
+    void alloc(int64_t count, cudaStream_t st) {
+        release();
+        s = st;
+        n = count;
+        if (count > 0) {
+            cudaError_t e = cudaMallocAsync((void **)&p, (size_t)count * sizeof(T), st);
+            if (e != cudaSuccess) {
+                p = nullptr;
+                n = 0;
+                cudaGetLastError();
+                char buf[160];
+                snprintf(buf, sizeof buf, "device allocation of %.3f GB failed",
+                         (double)count * sizeof(T) / 1e9);
+                fail(e == cudaErrorMemoryAllocation ? LSAMG_OOM : LSAMG_CUDA, buf);
+            }
+        }
+    }
+    void zero(cudaStream_t st) {
+        if (n) CK(cudaMemsetAsync(p, 0, (size_t)n * sizeof(T), st));
+    }
+    void release() {
+        if (p) cudaFreeAsync(p, s);
+        p = nullptr;
+        n = 0;
+    }
+    T *get() const { return p; }
+    int64_t size() const { return n; }
+    int64_t bytes() const { return n * (int64_t)sizeof(T); }
+};
+
+template <class T>
+inline std::vector<T> to_host(const T *d, int64_t n, cudaStream_t s) {
+    std::vector<T> h((size_t)std::max<int64_t>(n, 0));
+    if (n > 0) {
+        CK(cudaMemcpyAsync(h.data(), d, (size_t)n * sizeof(T), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return h;
+}
+
+template <class T>
+inline T read1(const T *d, cudaStream_t s) {
+    T v;
+    CK(cudaMemcpyAsync(&v, d, sizeof(T), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return v;
+}
+
+template <class T>
+inline void upload(DBuf<T> &b, const std::vector<T> &h, cudaStream_t s) {
+    b.alloc((int64_t)h.size(), s);
+    if (!h.empty())
+        CK(cudaMemcpyAsync(b.p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+}
+
+// ---------------------------------------------------------------------------------
+// Device error flag: kernels record the first failure (code, info) with atomicCAS.
+// ---------------------------------------------------------------------------------
+__device__ inline void flag_error(int *err, int code, int info) {
+    if (err && atomicCAS(err, 0, code) == 0) err[1] = info;
+}
+
+// ---------------------------------------------------------------------------------
+// Prefix sums (exclusive, int64 output with the total in out[n]).
+// ---------------------------------------------------------------------------------
+void exclusive_scan_i32(const int32_t *in, int64_t *out, int64_t n, cudaStream_t s);
+void exclusive_scan_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t s);
+
+// ---------------------------------------------------------------------------------
+// Batcher odd-even merge sort network for arbitrary length n (comparators touching
+// positions >= n are dropped, which is valid because the virtual tail is +infinity).
+// Called by all threads of a CTA on shared or global memory.
+// ---------------------------------------------------------------------------------
+template <class K>
+__device__ inline void cta_oem_sort(K *a, int n) {
+    for (int p = 1; p < n; p <<= 1) {
+        for (int k = p; k >= 1; k >>= 1) {
+            const int r0 = k % p;
+            for (int x = threadIdx.x; x + k < n; x += blockDim.x) {
+                if (x < r0) continue;
+                if (((x - r0) & (2 * k - 1)) >= k) continue;
+                if ((x / (2 * p)) != ((x + k) / (2 * p))) continue;
+                K u = a[x], v = a[x + k];
+                if (v < u) { a[x] = v; a[x + k] = u; }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Sort every CSR segment ascending in place and (optionally) count unique values.
+// Segments longer than the shared-memory capacity raise LSAMG_LIMIT through err.
+void seg_sort(int32_t *vals, const int64_t *ptr, int64_t nseg, int64_t *uniq_count, int *err,
+              cudaStream_t s);
+// Compact the sorted segments to their unique values: out[optr[i]..] = unique(vals[ptr[i]..]).
+void seg_unique_compact(const int32_t *vals, const int64_t *ptr, int64_t nseg, const int64_t *optr,
+                        int32_t *out, cudaStream_t s);
+
+// Transpose a CSR map rows -> cols (ptr [nr+1], idx) into cols -> rows with each output
+// list sorted ascending.  Allocates tptr [nc+1] and tidx.
+void csr_transpose(const int64_t *ptr, const int32_t *idx, int64_t nr, int64_t nnz, int64_t nc,
+                   DBuf<int64_t> &tptr, DBuf<int32_t> &tidx, int *err, cudaStream_t s);
+
+// Device-wide sort of 64-bit keys (bitonic network, one launch per stage).
+void sort_u64(uint64_t *keys, int64_t n, cudaStream_t s);
+
+// Small reductions.
+int32_t max_i32(const int32_t *d, int64_t n, cudaStream_t s);
+int64_t sum_i64(const int64_t *d, int64_t n, cudaStream_t s);
+
+constexpr int SEG_SMEM_MAX = 56 * 1024;  // max int32 entries of one segment sorted in smem
+
+}  // namespace lsamg

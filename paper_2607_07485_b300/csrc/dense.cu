@@ -1,0 +1,774 @@
+// Batched variable-size FP64 dense kernels (see dense.cuh).  FP64 arithmetic throughout:
+// these serve the local eigenproblems whose small eigenvalues select the coarse space.
+#include "dense.cuh"
+
+namespace lsamg {
+
+namespace {
+
+constexpr int NB = 32;          // panel width of the blocked Cholesky / TRSM
+constexpr int TT = 64;          // output tile of the update kernels
+constexpr double DEPS = 2.220446049250313e-16;
+
+// ------------------------------------------------------------------------- potrf
+__global__ void k_maxdiag(const double *base, const int64_t *off, const int32_t *ld,
+                          const int32_t *nn, int64_t count, double *md) {
+    int64_t b = blockIdx.x;
+    if (b >= count) return;
+    const double *A = base + off[b];
+    int n = nn[b], L = ld[b];
+    double m = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, fabs(A[i + (int64_t)i * L]));
+    for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __shared__ double w[32];
+    if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r = 0.0;
+        for (int i = 0; i < (int)(blockDim.x + 31) / 32; i++) r = fmax(r, w[i]);
+        md[b] = r;
+    }
+}
+
+__global__ void k_potf2(double *base, const int64_t *off, const int32_t *ld, const int32_t *nn,
+                        int64_t count, int j0, int mode, const double *md, int *err) {
+    int64_t b = blockIdx.x;
+    if (b >= count) return;
+    int n = nn[b];
+    if (j0 >= n) return;
+    int bs = min(NB, n - j0);
+    int L = ld[b];
+    double *A = base + off[b] + (int64_t)j0 + (int64_t)j0 * L;
+    __shared__ double s[NB][NB + 1];
+    __shared__ double piv;
+    for (int t = threadIdx.x; t < bs * bs; t += blockDim.x) {
+        int i = t % bs, j = t / bs;
+        s[i][j] = (i >= j) ? A[i + (int64_t)j * L] : 0.0;
+    }
+    __syncthreads();
+    const double tol = (mode == POTRF_PSD) ? (double)n * DEPS * md[b] : 0.0;
+    for (int k = 0; k < bs; k++) {
+        if (threadIdx.x == 0) {
+            double d = s[k][k];
+            double p;
+            if (mode == POTRF_SPD) {
+                if (!(d > 0.0) || !isfinite(d)) {
+                    flag_error(err, LSAMG_SINGULAR, (int)b);
+                    d = 1.0;
+                }
+                p = sqrt(d);
+            } else {
+                p = (d > tol) ? sqrt(d) : 0.0;
+            }
+            s[k][k] = p;
+            piv = p;
+        }
+        __syncthreads();
+        double p = piv;
+        for (int i = k + 1 + threadIdx.x; i < bs; i += blockDim.x) s[i][k] = (p > 0.0) ? s[i][k] / p : 0.0;
+        __syncthreads();
+        int m = bs - k - 1;
+        for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+            int i = k + 1 + t % m, j = k + 1 + t / m;
+            if (i >= j) s[i][j] -= s[i][k] * s[j][k];
+        }
+        __syncthreads();
+    }
+    for (int t = threadIdx.x; t < bs * bs; t += blockDim.x) {
+        int i = t % bs, j = t / bs;
+        if (i >= j) A[i + (int64_t)j * L] = s[i][j];
+    }
+}
+
+// rows below the diagonal block: A21 <- A21 L11^{-T}
+__global__ void k_potrf_panel(double *base, const int64_t *off, const int32_t *ld,
+                              const int32_t *nn, int64_t count, int j0) {
+    int64_t b = blockIdx.y;
+    if (b >= count) return;
+    int n = nn[b];
+    if (j0 >= n) return;
+    int bs = min(NB, n - j0);
+    int L = ld[b];
+    double *A = base + off[b];
+    __shared__ double l[NB][NB + 1];
+    for (int t = threadIdx.x; t < bs * bs; t += blockDim.x) {
+        int i = t % bs, j = t / bs;
+        l[i][j] = (i >= j) ? A[(j0 + i) + (int64_t)(j0 + j) * L] : 0.0;
+    }
+    __syncthreads();
+    int r = j0 + bs + blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    double x[NB];
+#pragma unroll
+    for (int c = 0; c < NB; c++)
+        if (c < bs) x[c] = A[r + (int64_t)(j0 + c) * L];
+#pragma unroll
+    for (int c = 0; c < NB; c++) {
+        if (c < bs) {
+            double v = x[c];
+#pragma unroll
+            for (int k = 0; k < NB; k++)
+                if (k < c) v -= x[k] * l[c][k];
+            x[c] = (l[c][c] != 0.0) ? v / l[c][c] : 0.0;
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < NB; c++)
+        if (c < bs) A[r + (int64_t)(j0 + c) * L] = x[c];
+}
+
+__device__ __forceinline__ void tri_index(int t, int &ti, int &tj) {
+    int i = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while ((i + 1) * (i + 2) / 2 <= t) i++;
+    while (i * (i + 1) / 2 > t) i--;
+    ti = i;
+    tj = t - i * (i + 1) / 2;
+}
+
+// trailing update A22 -= L21 L21^T on lower tiles
+__global__ void __launch_bounds__(256) k_potrf_update(double *base, const int64_t *off,
+                                                      const int32_t *ld, const int32_t *nn,
+                                                      int64_t count, int j0) {
+    int64_t b = blockIdx.y;
+    if (b >= count) return;
+    int n = nn[b];
+    int bs = min(NB, n - j0);
+    int r0 = j0 + bs;
+    int m = n - r0;
+    if (m <= 0 || bs <= 0) return;
+    int T = (m + TT - 1) / TT;
+    if ((int64_t)blockIdx.x >= (int64_t)T * (T + 1) / 2) return;
+    int ti, tj;
+    tri_index(blockIdx.x, ti, tj);
+    int L = ld[b];
+    double *A = base + off[b];
+    __shared__ double As[NB][TT + 1];
+    __shared__ double Bs[NB][TT + 1];
+    int ib = r0 + ti * TT, jb = r0 + tj * TT;
+    for (int t = threadIdx.x; t < NB * TT; t += blockDim.x) {
+        int rr = t % TT, k = t / TT;
+        int gi = ib + rr, gj = jb + rr;
+        As[k][rr] = (k < bs && gi < n) ? A[gi + (int64_t)(j0 + k) * L] : 0.0;
+        Bs[k][rr] = (k < bs && gj < n) ? A[gj + (int64_t)(j0 + k) * L] : 0.0;
+    }
+    __syncthreads();
+    int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+    double acc[4][4] = {};
+#pragma unroll 8
+    for (int k = 0; k < NB; k++) {
+        double a[4], c[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            a[u] = As[k][ty * 4 + u];
+            c[u] = Bs[k][tx * 4 + u];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+#pragma unroll
+            for (int v = 0; v < 4; v++) acc[u][v] = fma(a[u], c[v], acc[u][v]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; u++)
+#pragma unroll
+        for (int v = 0; v < 4; v++) {
+            int gi = ib + ty * 4 + u, gj = jb + tx * 4 + v;
+            if (gi < n && gj < n && gi >= gj) A[gi + (int64_t)gj * L] -= acc[u][v];
+        }
+}
+
+// ------------------------------------------------------------------------- trsm
+constexpr int SW = 32;  // right-hand-side strip width
+
+__global__ void __launch_bounds__(256) k_trsm(const double *baseL, const int64_t *loff,
+                                              const int32_t *lld, const int32_t *nn,
+                                              double *baseB, const int64_t *boff,
+                                              const int32_t *bld, const int32_t *bcols,
+                                              int64_t count, int trans) {
+    int64_t b = blockIdx.y;
+    if (b >= count) return;
+    int n = nn[b];
+    int ncol = bcols[b];
+    int c0 = blockIdx.x * SW;
+    if (c0 >= ncol || n <= 0) return;
+    int cs = min(SW, ncol - c0);
+    const double *Lm = baseL + loff[b];
+    int LL = lld[b];
+    double *B = baseB + boff[b] + (int64_t)c0 * bld[b];
+    int LB = bld[b];
+    __shared__ double Ls[NB][NB + 1];
+    __shared__ double Xs[NB][SW + 1];
+    __shared__ double acc[NB][SW + 1];
+    int nrb = (n + NB - 1) / NB;
+    for (int step = 0; step < nrb; step++) {
+        int rb = trans ? (nrb - 1 - step) : step;
+        int r0 = rb * NB, rs = min(NB, n - r0);
+        for (int t = threadIdx.x; t < NB * SW; t += blockDim.x) {
+            int i = t % NB, c = t / NB;
+            acc[i][c] = (i < rs && c < cs) ? B[(r0 + i) + (int64_t)c * LB] : 0.0;
+        }
+        __syncthreads();
+        int kb0 = trans ? rb + 1 : 0, kb1 = trans ? nrb : rb;
+        for (int kb = kb0; kb < kb1; kb++) {
+            int k0 = kb * NB, ks = min(NB, n - k0);
+            for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
+                int i = t % NB, k = t / NB;
+                double v = 0.0;
+                if (!trans) {
+                    if (i < rs && k < ks) v = Lm[(r0 + i) + (int64_t)(k0 + k) * LL];  // L[r0+i, k0+k]
+                } else {
+                    if (i < rs && k < ks) v = Lm[(k0 + k) + (int64_t)(r0 + i) * LL];  // L[k0+k, r0+i]
+                }
+                Ls[i][k] = v;
+            }
+            for (int t = threadIdx.x; t < NB * SW; t += blockDim.x) {
+                int k = t % NB, c = t / NB;
+                Xs[k][c] = (k < ks && c < cs) ? B[(k0 + k) + (int64_t)c * LB] : 0.0;
+            }
+            __syncthreads();
+            for (int t = threadIdx.x; t < NB * SW; t += blockDim.x) {
+                int i = t % NB, c = t / NB;
+                double v = acc[i][c];
+#pragma unroll 8
+                for (int k = 0; k < NB; k++) v -= Ls[i][k] * Xs[k][c];
+                acc[i][c] = v;
+            }
+            __syncthreads();
+        }
+        // diagonal block
+        for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
+            int i = t % NB, k = t / NB;
+            Ls[i][k] = (i < rs && k < rs && i >= k) ? Lm[(r0 + i) + (int64_t)(r0 + k) * LL] : 0.0;
+        }
+        __syncthreads();
+        if (threadIdx.x < cs) {
+            int c = threadIdx.x;
+            if (!trans) {
+                for (int i = 0; i < rs; i++) {
+                    double v = acc[i][c];
+                    for (int k = 0; k < i; k++) v -= Ls[i][k] * acc[k][c];
+                    acc[i][c] = (Ls[i][i] != 0.0) ? v / Ls[i][i] : 0.0;
+                }
+            } else {
+                for (int i = rs - 1; i >= 0; i--) {
+                    double v = acc[i][c];
+                    for (int k = i + 1; k < rs; k++) v -= Ls[k][i] * acc[k][c];
+                    acc[i][c] = (Ls[i][i] != 0.0) ? v / Ls[i][i] : 0.0;
+                }
+            }
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < NB * SW; t += blockDim.x) {
+            int i = t % NB, c = t / NB;
+            if (i < rs && c < cs) B[(r0 + i) + (int64_t)c * LB] = acc[i][c];
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------------- syrk (C -= W^T W)
+__global__ void __launch_bounds__(256) k_syrk_tn(double *baseC, const int64_t *coff,
+                                                 const int32_t *cld, const int32_t *cn,
+                                                 const double *baseW, const int64_t *woff,
+                                                 const int32_t *wld, const int32_t *wk,
+                                                 int64_t count, double alpha, int wrow) {
+    int64_t b = blockIdx.y;
+    if (b >= count) return;
+    int n = cn[b], K = wk[b];
+    int T = (n + TT - 1) / TT;
+    if ((int)blockIdx.x >= T * T || K <= 0) return;
+    int ti = blockIdx.x / T, tj = blockIdx.x % T;
+    double *C = baseC + coff[b];
+    int LC = cld[b];
+    const double *W = baseW + woff[b];
+    const int64_t rs = wrow ? (int64_t)wld[b] : 1, cs = wrow ? 1 : (int64_t)wld[b];
+    __shared__ double As[NB][TT + 1];
+    __shared__ double Bs[NB][TT + 1];
+    int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+    double acc[4][4] = {};
+    int ib = ti * TT, jb = tj * TT;
+    for (int k0 = 0; k0 < K; k0 += NB) {
+        for (int t = threadIdx.x; t < NB * TT; t += blockDim.x) {
+            int k = t % NB, rr = t / NB;
+            int gk = k0 + k;
+            As[k][rr] = (gk < K && ib + rr < n) ? W[gk * rs + (int64_t)(ib + rr) * cs] : 0.0;
+            Bs[k][rr] = (gk < K && jb + rr < n) ? W[gk * rs + (int64_t)(jb + rr) * cs] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int k = 0; k < NB; k++) {
+            double a[4], c[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                a[u] = As[k][ty * 4 + u];
+                c[u] = Bs[k][tx * 4 + u];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+#pragma unroll
+                for (int v = 0; v < 4; v++) acc[u][v] = fma(a[u], c[v], acc[u][v]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 4; u++)
+#pragma unroll
+        for (int v = 0; v < 4; v++) {
+            int gi = ib + ty * 4 + u, gj = jb + tx * 4 + v;
+            if (gi < n && gj < n) C[gi + (int64_t)gj * LC] += alpha * acc[u][v];
+        }
+}
+
+// ------------------------------------------------------------------------- transpose
+__global__ void k_transpose(const double *baseS, const int64_t *soff, const int32_t *sld,
+                            const int32_t *sn, double *baseD, const int64_t *doff,
+                            const int32_t *dld, int64_t count) {
+    int64_t b = blockIdx.y;
+    if (b >= count) return;
+    int n = sn[b];
+    int T = (n + 31) / 32;
+    if ((int)blockIdx.x >= T * T) return;
+    int ti = blockIdx.x / T, tj = blockIdx.x % T;
+    const double *S = baseS + soff[b];
+    double *D = baseD + doff[b];
+    int LS = sld[b], LD = dld[b];
+    __shared__ double t[32][33];
+    for (int u = threadIdx.x; u < 1024; u += blockDim.x) {
+        int i = u % 32, j = u / 32;
+        int gi = ti * 32 + i, gj = tj * 32 + j;
+        t[i][j] = (gi < n && gj < n) ? S[gi + (int64_t)gj * LS] : 0.0;
+    }
+    __syncthreads();
+    for (int u = threadIdx.x; u < 1024; u += blockDim.x) {
+        int i = u % 32, j = u / 32;
+        int gi = tj * 32 + i, gj = ti * 32 + j;  // D[gi, gj] = S[gj, gi]
+        if (gi < n && gj < n) D[gi + (int64_t)gj * LD] = t[j][i];
+    }
+}
+
+// ------------------------------------------------------------------------- sytd2
+__device__ double block_sum(double v, double *red) {
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    int nw = (blockDim.x + 31) >> 5;
+    for (int i = 0; i < nw; i++) r += red[i];
+    return r;
+}
+
+__global__ void __launch_bounds__(512) k_sytd2(double *base, const int64_t *off, const int32_t *ld,
+                                               const int32_t *nn, int64_t count, double *dd,
+                                               double *ee, double *tt, const int64_t *toff,
+                                               double *pwork, const int64_t *pwoff) {
+    int64_t b = blockIdx.x;
+    if (b >= count) return;
+    int n = nn[b];
+    int L = ld[b];
+    double *A = base + off[b];
+    double *d = dd + toff[b], *e = ee + toff[b], *tau = tt + toff[b];
+    double *p = pwork + pwoff[b];  // length n
+    __shared__ double red[32];
+    __shared__ double sh_tau, sh_alpha_scale;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    for (int j = 0; j < n - 1; j++) {
+        int m = n - j - 1;                 // length of x = A[j+1:n, j]
+        double *x = A + (j + 1) + (int64_t)j * L;
+        double sig = 0.0;
+        for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) sig += x[i] * x[i];
+        sig = block_sum(sig, red);
+        if (threadIdx.x == 0) {
+            double alpha = x[0];
+            d[j] = A[j + (int64_t)j * L];
+            if (sig == 0.0) {
+                sh_tau = 0.0;
+                e[j] = alpha;
+                sh_alpha_scale = 0.0;
+            } else {
+                double beta = -copysign(sqrt(alpha * alpha + sig), alpha);
+                sh_tau = (beta - alpha) / beta;
+                sh_alpha_scale = 1.0 / (alpha - beta);
+                e[j] = beta;
+            }
+            tau[j] = sh_tau;
+        }
+        __syncthreads();
+        double tj = sh_tau, sc = sh_alpha_scale;
+        if (tj == 0.0) {
+            __syncthreads();
+            continue;
+        }
+        for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) x[i] *= sc;
+        if (threadIdx.x == 0) x[0] = 1.0;  // v[0] = 1 (restored to beta below)
+        __syncthreads();
+        // p = tau * A22 v with A22 = A[j+1:, j+1:] (lower triangle stored)
+        double *A22 = A + (j + 1) + (int64_t)(j + 1) * L;
+        // pass 1: p[c] = sum_{r >= c} A22[r, c] v[r]  (warp per column)
+        for (int c = warp; c < m; c += nwarp) {
+            double s = 0.0;
+            const double *col = A22 + (int64_t)c * L;
+            for (int r = c + lane; r < m; r += 32) s += col[r] * x[r];
+            for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) p[c] = s;
+        }
+        __syncthreads();
+        // pass 2: p[r] += sum_{c < r} A22[r, c] v[c]  (thread per row)
+        for (int r0 = 0; r0 < m; r0 += blockDim.x) {
+            int r = r0 + threadIdx.x;
+            double s = 0.0;
+            int cmax = min(r0 + (int)blockDim.x, m);
+            for (int c = 0; c < cmax; c++)
+                if (c < r && r < m) s += A22[r + (int64_t)c * L] * x[c];
+            if (r < m) p[r] = tj * (p[r] + s);
+        }
+        __syncthreads();
+        double pv = 0.0;
+        for (int i = threadIdx.x; i < m; i += blockDim.x) pv += p[i] * x[i];
+        pv = block_sum(pv, red);
+        double kk = -0.5 * tj * pv;
+        for (int i = threadIdx.x; i < m; i += blockDim.x) p[i] += kk * x[i];  // w
+        __syncthreads();
+        // A22 -= v w^T + w v^T (lower)
+        for (int c = warp; c < m; c += nwarp) {
+            double vc = x[c], wc = p[c];
+            double *col = A22 + (int64_t)c * L;
+            for (int r = c + lane; r < m; r += 32) col[r] -= x[r] * wc + p[r] * vc;
+        }
+        __syncthreads();
+        // keep v in place (v[0] implicit); store beta on the subdiagonal position
+        if (threadIdx.x == 0) x[0] = e[j];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && n > 0) d[n - 1] = A[(n - 1) + (int64_t)(n - 1) * L];
+}
+
+// ------------------------------------------------------------------------- stebz
+__device__ int sturm_count(const double *d, const double *e, int n, double x, double pivmin) {
+    int cnt = 0;
+    double q = d[0] - x;
+    if (fabs(q) < pivmin) q = -pivmin;
+    cnt += q < 0.0;
+    for (int i = 1; i < n; i++) {
+        q = d[i] - x - e[i - 1] * e[i - 1] / q;
+        if (fabs(q) < pivmin) q = -pivmin;
+        cnt += q < 0.0;
+    }
+    return cnt;
+}
+
+__device__ double bisect_index(const double *d, const double *e, int n, int j, double lo, double hi,
+                               double pivmin) {
+    // smallest x with count(x) >= j + 1
+    for (int it = 0; it < 200; it++) {
+        double mid = 0.5 * (lo + hi);
+        if (hi - lo <= 2.0 * DEPS * fmax(fabs(lo), fabs(hi)) + pivmin || mid == lo || mid == hi) break;
+        if (sturm_count(d, e, n, mid, pivmin) >= j + 1)
+            hi = mid;
+        else
+            lo = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+__global__ void k_stebz(const double *dd, const double *ee, const int64_t *toff, const int32_t *nn,
+                        int64_t count, double sigma, int32_t *kout, double *w, double *gap) {
+    int64_t b = blockIdx.x;
+    if (b >= count) return;
+    int n = nn[b];
+    const double *d = dd + toff[b], *e = ee + toff[b];
+    __shared__ double glo, ghi, pivmin;
+    __shared__ int kk;
+    __shared__ double lam_lo, lam_hi;
+    if (threadIdx.x == 0) {
+        double lo = 1e300, hi = -1e300, emax = 0.0;
+        for (int i = 0; i < n; i++) {
+            double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < n - 1 ? fabs(e[i]) : 0.0);
+            lo = fmin(lo, d[i] - r);
+            hi = fmax(hi, d[i] + r);
+            if (i < n - 1) emax = fmax(emax, e[i] * e[i]);
+        }
+        double tn = fmax(fabs(lo), fabs(hi));
+        pivmin = 2.2250738585072014e-308 * fmax(1.0, emax);
+        glo = lo - 2.0 * DEPS * tn * n - pivmin;
+        ghi = hi + 2.0 * DEPS * tn * n + pivmin;
+        kk = (n > 0) ? sturm_count(d, e, n, sigma, pivmin) : 0;
+        kout[b] = kk;
+        lam_lo = -1.0;
+        lam_hi = -1.0;
+    }
+    __syncthreads();
+    int k = kk;
+    // eigenvalues 0..k-1 (kept) and k (first discarded) for the gap
+    for (int j = threadIdx.x; j <= k && j < n; j += blockDim.x) {
+        double lam = bisect_index(d, e, n, j, glo, ghi, pivmin);
+        if (j < k) w[toff[b] + j] = lam;
+        if (j == k - 1) lam_lo = lam;
+        if (j == k) lam_hi = lam;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double g = 1e300;
+        if (k > 0) g = fmin(g, fabs(lam_lo / sigma - 1.0));
+        if (k < n) g = fmin(g, fabs(lam_hi / sigma - 1.0));
+        gap[b] = g;
+    }
+}
+
+// ------------------------------------------------------------------------- stein
+__device__ __forceinline__ double urand(uint32_t a, uint32_t b) {
+    uint32_t x = a * 0x9E3779B1u ^ (b + 0x7F4A7C15u);
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return (double)x * (2.0 / 4294967296.0) - 1.0;
+}
+
+__global__ void __launch_bounds__(256) k_stein(const double *dd, const double *ee,
+                                               const int64_t *toff, const int32_t *nn,
+                                               int64_t count, const double *wv, const int32_t *kk,
+                                               double *baseV, const int64_t *voff,
+                                               const int32_t *vld, double *work,
+                                               const int64_t *workoff) {
+    int64_t b = blockIdx.x;
+    if (b >= count) return;
+    int n = nn[b], k = kk[b];
+    if (k <= 0 || n <= 0) return;
+    const double *d = dd + toff[b], *e = ee + toff[b], *w = wv + toff[b];
+    double *V = baseV + voff[b];
+    int LV = vld[b];
+    double *W = work + workoff[b];
+    double *dg = W, *su = W + n, *su2 = W + 2 * n, *mu = W + 3 * n, *pv = W + 4 * n, *x = W + 5 * n;
+    __shared__ double red[32];
+    __shared__ double tnorm;
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < n; i++)
+            t = fmax(t, fabs(d[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < n - 1 ? fabs(e[i]) : 0.0));
+        tnorm = fmax(t, 1e-300);
+    }
+    __syncthreads();
+    const double ortol = 1e-3 * tnorm, pertol = 10.0 * DEPS * tnorm;
+    int cstart = 0;
+    double lamprev = 0.0;
+    for (int j = 0; j < k; j++) {
+        double lam = w[j];
+        if (j > 0) {
+            if (lam - w[j - 1] > ortol) cstart = j;
+            if (lam - lamprev < pertol) lam = lamprev + pertol;
+        }
+        lamprev = lam;
+        // LU with partial pivoting of T - lam I (serial, O(n))
+        if (threadIdx.x == 0) {
+            for (int i = 0; i < n; i++) {
+                dg[i] = d[i] - lam;
+                su[i] = (i < n - 1) ? e[i] : 0.0;
+                su2[i] = 0.0;
+            }
+            for (int i = 0; i < n - 1; i++) {
+                double sub = e[i];
+                if (fabs(dg[i]) >= fabs(sub)) {
+                    if (dg[i] == 0.0) dg[i] = pertol;
+                    double m = sub / dg[i];
+                    mu[i] = m;
+                    pv[i] = 0.0;
+                    dg[i + 1] -= m * su[i];
+                } else {
+                    double m = dg[i] / sub;
+                    mu[i] = m;
+                    pv[i] = 1.0;
+                    double od = dg[i + 1], os = su[i], os1 = su[i + 1];
+                    dg[i] = sub;
+                    su[i] = od;
+                    su2[i] = os1;
+                    dg[i + 1] = os - m * od;
+                    su[i + 1] = -m * os1;
+                }
+            }
+            if (dg[n - 1] == 0.0) dg[n - 1] = pertol;
+        }
+        for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = urand((uint32_t)j, (uint32_t)i);
+        __syncthreads();
+        for (int it = 0; it < 3; it++) {
+            // scale to unit infinity norm
+            double mx = 0.0;
+            for (int i = threadIdx.x; i < n; i += blockDim.x) mx = fmax(mx, fabs(x[i]));
+            for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            __syncthreads();
+            if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double r = 0.0;
+                for (int i = 0; i < (int)(blockDim.x >> 5); i++) r = fmax(r, red[i]);
+                red[0] = (r > 0.0) ? 1.0 / r : 1.0;
+            }
+            __syncthreads();
+            double inv = red[0];
+            for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] *= inv;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                // forward: apply row interchanges and multipliers
+                for (int i = 0; i < n - 1; i++) {
+                    if (pv[i] != 0.0) {
+                        double t = x[i];
+                        x[i] = x[i + 1];
+                        x[i + 1] = t - mu[i] * x[i];
+                    } else {
+                        x[i + 1] -= mu[i] * x[i];
+                    }
+                }
+                // back substitution with U (diag dg, super su, second super su2)
+                for (int i = n - 1; i >= 0; i--) {
+                    double v = x[i];
+                    if (i + 1 < n) v -= su[i] * x[i + 1];
+                    if (i + 2 < n) v -= su2[i] * x[i + 2];
+                    x[i] = v / dg[i];
+                }
+            }
+            __syncthreads();
+            // re-orthogonalise against earlier members of the cluster (modified Gram-Schmidt)
+            for (int c = cstart; c < j; c++) {
+                double s = 0.0;
+                const double *vc = V + (int64_t)c * LV;
+                for (int i = threadIdx.x; i < n; i += blockDim.x) s += vc[i] * x[i];
+                s = block_sum(s, red);
+                for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] -= s * vc[i];
+                __syncthreads();
+            }
+        }
+        double s = 0.0;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) s += x[i] * x[i];
+        s = block_sum(s, red);
+        double inv = (s > 0.0) ? 1.0 / sqrt(s) : 0.0;
+        double *vj = V + (int64_t)j * LV;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) vj[i] = x[i] * inv;
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------------- ormtr
+__global__ void __launch_bounds__(256) k_ormtr(const double *baseA, const int64_t *aoff,
+                                               const int32_t *ald, const int32_t *nn,
+                                               const double *tt, const int64_t *toff,
+                                               double *baseV, const int64_t *voff,
+                                               const int32_t *vld, const int32_t *vcols,
+                                               int64_t count) {
+    int64_t b = blockIdx.y;
+    if (b >= count) return;
+    int n = nn[b], k = vcols[b];
+    const int lane = threadIdx.x & 31;
+    int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (c >= k) return;
+    const double *A = baseA + aoff[b];
+    int LA = ald[b];
+    const double *tau = tt + toff[b];
+    double *v = baseV + voff[b] + (int64_t)c * vld[b];
+    for (int j = n - 2; j >= 0; j--) {
+        double t = tau[j];
+        if (t == 0.0) continue;
+        int m = n - j - 1;
+        const double *h = A + (j + 1) + (int64_t)j * LA;  // h[0] implicit 1
+        double s = 0.0;
+        for (int r = lane; r < m; r += 32) s += (r == 0 ? 1.0 : h[r]) * v[j + 1 + r];
+        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        s *= t;
+        for (int r = lane; r < m; r += 32) v[j + 1 + r] -= s * (r == 0 ? 1.0 : h[r]);
+        __syncwarp();
+    }
+}
+
+}  // namespace
+
+// ============================================================================= host wrappers
+void potrf_batched(double *base, const MatBatch &A, PotrfMode mode, int *err, cudaStream_t s) {
+    if (A.count == 0 || A.maxn == 0) return;
+    DBuf<double> md;
+    md.alloc(A.count, s);
+    k_maxdiag<<<(unsigned)A.count, 256, 0, s>>>(base, A.off.p, A.ld.p, A.n.p, A.count, md.p);
+    CK_LAUNCH();
+    for (int j0 = 0; j0 < A.maxn; j0 += NB) {
+        k_potf2<<<(unsigned)A.count, 256, 0, s>>>(base, A.off.p, A.ld.p, A.n.p, A.count, j0, mode,
+                                                 md.p, err);
+        CK_LAUNCH();
+        int rem = A.maxn - j0 - NB;
+        if (rem <= 0) break;
+        dim3 gp((unsigned)cdiv(rem, 128), (unsigned)A.count);
+        k_potrf_panel<<<gp, 128, 0, s>>>(base, A.off.p, A.ld.p, A.n.p, A.count, j0);
+        CK_LAUNCH();
+        int64_t T = cdiv(rem, TT);
+        dim3 gu((unsigned)(T * (T + 1) / 2), (unsigned)A.count);
+        k_potrf_update<<<gu, 256, 0, s>>>(base, A.off.p, A.ld.p, A.n.p, A.count, j0);
+        CK_LAUNCH();
+    }
+}
+
+void trsm_batched(const double *base_L, const MatBatch &Lb, double *base_B, const MatBatch &Bb,
+                  bool trans, cudaStream_t s) {
+    if (Bb.count == 0 || Bb.maxm == 0 || Lb.maxn == 0) return;
+    dim3 g((unsigned)cdiv(Bb.maxm, SW), (unsigned)Bb.count);
+    k_trsm<<<g, 256, 0, s>>>(base_L, Lb.off.p, Lb.ld.p, Lb.n.p, base_B, Bb.off.p, Bb.ld.p, Bb.m.p,
+                             Bb.count, trans ? 1 : 0);
+    CK_LAUNCH();
+}
+
+void syrk_tn_batched(double *base_C, const MatBatch &Cb, const double *base_W, const MatBatch &Wb,
+                     double alpha, bool w_rowmajor, cudaStream_t s) {
+    if (Cb.count == 0 || Cb.maxn == 0) return;
+    int64_t T = cdiv(Cb.maxn, TT);
+    dim3 g((unsigned)(T * T), (unsigned)Cb.count);
+    k_syrk_tn<<<g, 256, 0, s>>>(base_C, Cb.off.p, Cb.ld.p, Cb.n.p, base_W, Wb.off.p, Wb.ld.p, Wb.n.p,
+                                Cb.count, alpha, w_rowmajor ? 1 : 0);
+    CK_LAUNCH();
+}
+
+void transpose_batched(const double *base_S, const MatBatch &Sb, double *base_D, const MatBatch &Db,
+                       cudaStream_t s) {
+    if (Sb.count == 0 || Sb.maxn == 0) return;
+    int64_t T = cdiv(Sb.maxn, 32);
+    dim3 g((unsigned)(T * T), (unsigned)Sb.count);
+    k_transpose<<<g, 256, 0, s>>>(base_S, Sb.off.p, Sb.ld.p, Sb.n.p, base_D, Db.off.p, Db.ld.p,
+                                  Sb.count);
+    CK_LAUNCH();
+}
+
+void sytd2_batched(double *base, const MatBatch &Ab, double *d, double *e, double *tau,
+                   const int64_t *toff, cudaStream_t s) {
+    if (Ab.count == 0) return;
+    // per-matrix symv workspace: reuse the toff layout (n entries per matrix)
+    DBuf<double> pw;
+    int64_t tot = read1(toff + Ab.count, s);
+    pw.alloc(std::max<int64_t>(tot, 1), s);
+    k_sytd2<<<(unsigned)Ab.count, 512, 0, s>>>(base, Ab.off.p, Ab.ld.p, Ab.n.p, Ab.count, d, e, tau,
+                                               toff, pw.p, toff);
+    CK_LAUNCH();
+}
+
+void stebz_batched(const double *d, const double *e, const int64_t *toff, const int32_t *n,
+                   int64_t count, double sigma, int32_t *k, double *w, double *gap,
+                   cudaStream_t s) {
+    if (count == 0) return;
+    k_stebz<<<(unsigned)count, 128, 0, s>>>(d, e, toff, n, count, sigma, k, w, gap);
+    CK_LAUNCH();
+}
+
+void stein_batched(const double *d, const double *e, const int64_t *toff, const int32_t *n,
+                   const double *w, const int32_t *k, double *base_V, const MatBatch &Vb,
+                   double *work, const int64_t *workoff, cudaStream_t s) {
+    if (Vb.count == 0) return;
+    k_stein<<<(unsigned)Vb.count, 256, 0, s>>>(d, e, toff, n, Vb.count, w, k, base_V, Vb.off.p,
+                                              Vb.ld.p, work, workoff);
+    CK_LAUNCH();
+}
+
+void ormtr_batched(const double *base_A, const MatBatch &Ab, const double *tau, const int64_t *toff,
+                   double *base_V, const MatBatch &Vb, cudaStream_t s) {
+    if (Vb.count == 0 || Vb.maxm == 0) return;
+    dim3 g((unsigned)cdiv(Vb.maxm, 8), (unsigned)Vb.count);
+    k_ormtr<<<g, 256, 0, s>>>(base_A, Ab.off.p, Ab.ld.p, Ab.n.p, tau, toff, base_V, Vb.off.p,
+                              Vb.ld.p, Vb.m.p, Vb.count);
+    CK_LAUNCH();
+}
+
+}  // namespace lsamg

@@ -1,0 +1,130 @@
+// Internal data model of liblsamg.  Every level is kept in element-block form:
+// a list of (element DOF map, dense Gram block G_T) pairs (Prop. 5.1), plus the
+// aggregation, closure, interpolation and smoother data built on it (Section 2).
+#pragma once
+#include "common.cuh"
+
+namespace lsamg {
+
+struct Level {
+    int64_t n = 0;   // DOFs
+    int64_t ne = 0;  // elements (level 0) or merged coarse elements (levels >= 1)
+    // element maps (CSR) and Gram blocks G_T (row-major m_T x n_T)
+    DBuf<int64_t> eptr;
+    DBuf<int32_t> eidx;
+    DBuf<int64_t> goff;
+    DBuf<int32_t> grows;
+    DBuf<double> G64;
+    DBuf<float> G32;
+    // element blocks A_T = G_T^T G_T (row-major n_T x n_T), kept during set-up only
+    DBuf<int64_t> aoff;
+    DBuf<double> AT;
+    // DOF -> elements
+    DBuf<int64_t> dptr;
+    DBuf<int32_t> didx;
+    int64_t nnz = 0;        // structural nnz of the assembled operator
+    int64_t nnz_e = 0;      // sum of element map lengths
+    int32_t max_nT = 0;     // largest element map
+    // aggregation and closure (Section 2 eqs. 2.2-2.5)
+    int32_t nagg = 0;
+    int32_t maxmult = 0;
+    double tau = 0.0;
+    DBuf<int32_t> agg;      // [n]
+    DBuf<int64_t> eaptr;    // element -> touching aggregates (sorted)
+    DBuf<int32_t> eaidx;
+    DBuf<int32_t> mult;     // [ne]
+    DBuf<int64_t> aeptr;    // aggregate -> elements touching omega_i
+    DBuf<int32_t> aeidx;
+    DBuf<int64_t> wptr;     // omega_i CSR (sorted DOFs)
+    DBuf<int32_t> widx;
+    DBuf<int32_t> posw;     // [n] rank of a DOF inside its aggregate
+    DBuf<int64_t> Optr;     // Omega_i CSR (sorted DOFs)
+    DBuf<int32_t> Oidx;
+    DBuf<int32_t> Olpos;    // omega-first local index of each Omega_i entry
+    DBuf<int64_t> oeptr;    // aggregate -> elements meeting Omega_i
+    DBuf<int32_t> oeidx;
+    DBuf<int64_t> oelocoff; // per (aggregate, element) entry: offset of its local positions
+    DBuf<int32_t> oeloc;    // sorted-Omega local index of each element DOF, -1 if outside
+    std::vector<int32_t> h_nw, h_nO;  // host copies of |omega_i| and |Omega_i|
+    // interpolation P = [R_w^T Z_i]
+    int64_t nc = 0;
+    DBuf<int32_t> k;        // [nagg]
+    DBuf<int64_t> off;      // [nagg+1] coarse DOF offsets
+    DBuf<int64_t> zoff;     // [nagg+1] offsets of Z_i (row-major |omega_i| x k_i)
+    DBuf<double> Z64;
+    DBuf<float> Z32;
+    std::vector<int32_t> h_k;
+    std::vector<double> h_gap;
+    DBuf<int32_t> cgroup;   // [ne] coarse element of each element (-1 if none)
+    // multiplicative Schwarz smoother
+    int32_t ncol = 0;
+    std::vector<int64_t> colptr;  // host: colour c holds colagg[colptr[c]..colptr[c+1])
+    DBuf<int32_t> colagg;
+    DBuf<int32_t> colour;
+    DBuf<int64_t> Loff;     // packed lower-triangular Cholesky factor of A_Omega (row-major)
+    DBuf<double> L64;
+    DBuf<float> L32;
+    // coarsest level: packed lower Cholesky factor of the dense operator
+    bool coarsest = false;
+    DBuf<double> Ld64;
+    DBuf<float> Ld32;
+    // cycle workspaces (allocated for nrhs_ws right-hand sides)
+    int32_t nrhs_ws = 0;
+    int32_t max_grows_cached = 0;   // largest G_T row count (shared-memory staging size)
+    int64_t Omega_total = 0;        // sum of |Omega_i| (Schwarz workspace per right-hand side)
+    DBuf<double> b64, x64, r64, ws64;
+    DBuf<float> b32, x32, r32, ws32;
+};
+
+struct Options {
+    lsamg_options o;
+};
+
+struct Handle {
+    cudaStream_t stream = nullptr;
+    lsamg_options opt{};
+    std::vector<Level> levels;
+    DBuf<int> err;              // device error flag (code, info)
+    DBuf<double> coef;          // level-0 element coefficients (for the adjoint gradient)
+    int64_t n0 = 0, ne0 = 0;
+    int32_t nT0 = 0;
+    lsamg_stats stats{};
+    // solve workspaces (FP64 outer Krylov vectors)
+    int32_t nrhs_ws = 0;
+    DBuf<double> kr, kz, kp, kq, kro, kx, dots;
+};
+
+// ------------------------------------------------------------------- graph.cu
+void check_input(const Level &L, int *err, cudaStream_t s);
+void build_dof_elem(Level &L, int *err, cudaStream_t s);
+void aggregate_level(Level &L, int passes, int *err, cudaStream_t s);
+void closure_level(Level &L, double tau_c, int *err, cudaStream_t s);
+void colour_level(Level &L, int *err, cudaStream_t s);
+int64_t structural_nnz_level0(Level &L, int *err, cudaStream_t s);
+int64_t structural_nnz_coarse(const Level &fine, int *err, cudaStream_t s);
+void check_err(const int *err, cudaStream_t s, const char *where);
+
+// ------------------------------------------------------------------- setup.cu
+void factor_elements(Level &L, int *err, cudaStream_t s);
+void local_spectral(Level &L, const lsamg_options &o, int *err, cudaStream_t s, double *flops);
+void build_coarse(Level &fine, Level &coarse, int *err, cudaStream_t s, double *flops);
+void smoother_setup(Level &L, const lsamg_options &o, int *err, cudaStream_t s, double *flops);
+void coarsest_setup(Level &L, int *err, cudaStream_t s, double *flops);
+
+// ------------------------------------------------------------------- cycle.cu
+void ensure_cycle_ws(Level &L, int nrhs, cudaStream_t s);
+template <class T>
+void vcycle(Handle &H, int l, int nrhs, cudaStream_t s);
+template <class T>
+void gram_spmv(const Level &L, const T *x, T *y, const T *b, int nrhs, cudaStream_t s);
+void elem_grad(const Level &L, const double *coef, const double *lam, const double *x, double *g,
+               cudaStream_t s);
+// FP64 vector helpers used by the Krylov drivers
+void vec_dots(const double *a, const double *b, int64_t n, int nrhs, double *out, cudaStream_t s);
+void vec_axpy(double *y, const double *x, const double *alpha, int64_t n, int nrhs, double sign,
+              cudaStream_t s);
+void vec_xpby(double *p, const double *z, const double *beta, int64_t n, int nrhs, cudaStream_t s);
+template <class A, class B>
+void vec_convert(B *dst, const A *src, int64_t count, cudaStream_t s);
+
+}  // namespace lsamg

@@ -270,10 +270,12 @@ def test_local_gep_residual_and_normalisation():
     L0 = H.levels[0]
     for i in range(L0.nagg):
         At, Aww, _ = OL.local_blocks(i, L0.elems, L0.mats, L0.mult, L0.ael, L0.omega, L0.Omega)
-        Z, mu, gap = OL.local_problem(At, Aww, L0.tau)
+        Hm, F, _ = OL.local_gram_rows(i, L0.elems, L0.G, L0.mult, L0.ael, L0.omega, L0.Omega)
+        Z, mu, gap = OL.local_problem(Hm, F, len(L0.omega[i]), L0.tau)
         nw = Aww.shape[0]
+        np.testing.assert_allclose(F.T @ F, Aww, atol=1e-12 * abs(Aww).max())
         S = At[:nw, :nw] - At[:nw, nw:] @ np.linalg.pinv(At[nw:, nw:], rcond=1e-15) @ At[nw:, :nw]
-        kept = mu[mu < 1 / L0.tau]
+        kept = mu[mu * L0.tau < 1 - OL.TIE]
         np.testing.assert_allclose(Z.T @ Aww @ Z, np.eye(Z.shape[1]), atol=1e-9)
         R = S @ Z - Aww @ Z * kept
         assert np.abs(R).max() <= 1e-10 * abs(S).max() * max(1, np.abs(Z).max())
@@ -313,9 +315,13 @@ def test_full_pencil_eq28_matches_reduced_eq29():
         lam = sla.eigvals(D @ AO @ D, At)
         lam = np.real(lam[np.isfinite(lam)])
         lam = np.sort(lam[np.abs(lam) > 1e-8])
-        _, mu, _ = OL.local_problem(At, Aww, L0.tau)
+        Hm, F, _ = OL.local_gram_rows(i, L0.elems, L0.G, L0.mult, L0.ael, L0.omega, L0.Omega)
+        _, mu, _ = OL.local_problem(Hm, F, nw, L0.tau)
         ref = np.sort(1.0 / mu[mu > 1e-12])
         np.testing.assert_allclose(lam, ref, rtol=1e-7)
+        # the assembled (pseudo-inverse) form gives the same spectrum on this conditioning
+        _, mu2, _ = OL.local_problem_pinv(At, Aww, L0.tau)
+        np.testing.assert_allclose(mu2, mu, atol=1e-10)
 
 
 def _discrete_curl_rt0(N):
@@ -351,8 +357,9 @@ def test_weak_approximation_bound_random_and_curl_modes(cfg1):
     taumax = 0.0
     for i in range(L0.nagg):
         At, Aww, _ = OL.local_blocks(i, L0.elems, L0.mats, L0.mult, L0.ael, L0.omega, L0.Omega)
-        Z, mu, _ = OL.local_problem(At, Aww, L0.tau)
-        disc = mu[mu >= 1 / L0.tau]
+        Hm, F, _ = OL.local_gram_rows(i, L0.elems, L0.G, L0.mult, L0.ael, L0.omega, L0.Omega)
+        Z, mu, _ = OL.local_problem(Hm, F, len(L0.omega[i]), L0.tau)
+        disc = mu[mu * L0.tau >= 1 - OL.TIE]
         if len(disc):
             taumax = max(taumax, 1.0 / disc.min())
         blocks.append((L0.omega[i], Aww, Z))
@@ -474,9 +481,9 @@ def test_two_level_bound_KTG():
     for i in range(L0.nagg):
         w = L0.omega[i]
         MwJ[np.ix_(w, w)] = A[np.ix_(w, w)]
-        At, Aww, _ = OL.local_blocks(i, L0.elems, L0.mats, L0.mult, L0.ael, L0.omega, L0.Omega)
-        _, mu, _ = OL.local_problem(At, Aww, L0.tau)
-        disc = mu[mu >= 1 / L0.tau]
+        Hm, F, _ = OL.local_gram_rows(i, L0.elems, L0.G, L0.mult, L0.ael, L0.omega, L0.Omega)
+        _, mu, _ = OL.local_problem(Hm, F, len(L0.omega[i]), L0.tau)
+        disc = mu[mu * L0.tau >= 1 - OL.TIE]
         if len(disc):
             taumax = max(taumax, 1.0 / disc.min())
     lmax = 1.0 / np.min(np.real(sla.eigvals(Mt_inv @ MwJ)))
@@ -537,3 +544,23 @@ def test_adjoint_gradient_against_central_differences():
         xp = solve_direct(tp, b); xm = solve_direct(tm, b)
         fd[e] = (0.5 * np.sum((xp - xs) ** 2) - 0.5 * np.sum((xm - xs) ** 2)) / (2 * h)
     np.testing.assert_allclose(g, fd, rtol=1e-5, atol=1e-5 * np.abs(fd).max())
+
+
+def test_local_problem_least_squares_form_vs_cholesky_route(cfg1):
+    # eq. 2.9 evaluated two independent ways on the cfg1 data (kappa(A) ~ 1e10): least squares
+    # on the Gram rows (the oracle) and Cholesky of the assembled At_GG / A_ww; the projectors
+    # onto the retained modes agree to ~1e-9, far below the eigh pseudo-inverse form's ~1e-4
+    c, mats, H = cfg1
+    L0 = H.levels[0]
+    for i in range(L0.nagg):
+        At, Aww, _ = OL.local_blocks(i, L0.elems, L0.mats, L0.mult, L0.ael, L0.omega, L0.Omega)
+        nw = Aww.shape[0]
+        S = At[:nw, :nw] - At[:nw, nw:] @ sla.cho_solve(sla.cho_factor(At[nw:, nw:]), At[nw:, :nw])
+        Lw = np.linalg.cholesky(Aww)
+        C = sla.solve_triangular(Lw, sla.solve_triangular(Lw, S, lower=True).T, lower=True)
+        mu, V = np.linalg.eigh(0.5 * (C + C.T))
+        Zc = sla.solve_triangular(Lw.T, V[:, mu * L0.tau < 1 - OL.TIE], lower=False)
+        assert Zc.shape[1] == L0.Z[i].shape[1]
+        Pa = np.linalg.qr(Zc)[0]
+        Pb = np.linalg.qr(L0.Z[i])[0]
+        assert np.linalg.norm(Pa @ Pa.T - Pb @ Pb.T, 2) < 2e-8
