@@ -78,6 +78,7 @@ typedef struct {
     int64_t chunk_bytes;         /* device workspace budget for batched local problems (0 = auto) */
     int32_t use_graph;           /* 1: capture the V-cycle as a CUDA graph */
     int32_t verbose;
+    int32_t profile;             /* 1: time every kernel class with CUDA events on the stream */
 } lsamg_options;
 
 lsamg_options lsamg_options_default(void);
@@ -161,6 +162,17 @@ enum {
 };
 int lsamg_query(lsamg_handle *h, int32_t level, int32_t what, void *out, int64_t cap_bytes,
                 int64_t *bytes_needed);
+
+/* Per-kernel-class device time since the last call (profile option on): out[0] = milliseconds,
+ * out[1] = launches, out[2] = algorithmic FLOPs, out[3] = algorithmic bytes.  Collecting
+ * synchronises the stream the kernels ran on and resets the counters of every class.
+ * lsamg_kernel_stats_all fills out[4 * n_classes]. */
+int32_t lsamg_kernel_classes(void);
+const char *lsamg_kernel_name(int32_t cls);
+int lsamg_kernel_stats_all(double *out);
+
+/* Number of CUDA kernel launches the library has issued in this process. */
+int64_t lsamg_launch_count(void);
 
 void lsamg_destroy(lsamg_handle *h);
 const char *lsamg_last_error(void);

@@ -519,7 +519,8 @@ def _coarsen(lev, o, passes):
     # A_g = sum_T (R_T P)^T A_T (R_T P) and a range factor G_g of A_g.  Merged members share
     # eagg, hence mult, closure and splitting weights, so every next-level quantity
     # (graph, Omega, At, A_ww) is unchanged by the merge.  Groups are ordered by their
-    # smallest member element.
+    # smallest member element.  The coarse element's Gram rows are the members' rows of
+    # G_c = G P stacked (no truncation), so G_g^T G_g = A_g.
     groups = {}
     order = []
     for t in range(len(lev.elems)):
@@ -534,14 +535,16 @@ def _coarsen(lev, o, passes):
     for key in order:
         cm = np.concatenate([np.arange(off[a], off[a + 1]) for a in key]).astype(np.int64)
         Ag = np.zeros((len(cm), len(cm)))
+        Gg = []
         for t in groups[key]:
             d = lev.elems[t]
             RTP = P[d][:, cm].toarray()
             Ag += RTP.T @ lev.mats[t] @ RTP
+            Gg.append(lev.G[t] @ RTP)            # G_c = G P, rows of the member element
         Ag = 0.5 * (Ag + Ag.T)
         celems.append(cm)
         cmats.append(Ag)
-        cG.append(element_gram(Ag, check=False))
+        cG.append(np.vstack(Gg) if Gg else np.zeros((0, len(cm))))
         members.append(np.array(groups[key], np.int64))
     lev.cgroups = members
     return Level(n=nc, elems=celems, mats=cmats, G=cG)

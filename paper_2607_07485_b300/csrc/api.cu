@@ -89,6 +89,42 @@ int32_t device_max(const int32_t *a, int64_t n, cudaStream_t s) {
 void finish_level_info(Level &L, cudaStream_t s) {
     L.max_grows_cached = device_max(L.grows.p, L.ne, s);
     if (!L.coarsest && L.nagg > 0) L.Omega_total = read1(L.Optr.p + L.nagg, s);
+    // algorithmic bytes: every stored G_T entry, element map and vector entry touched once
+    auto gr = to_host(L.grows.p, L.ne, s);
+    auto ep = to_host(L.eptr.p, L.ne + 1, s);
+    double gent = 0.0, ment = 0.0;
+    for (int64_t e = 0; e < L.ne; e++) {
+        gent += (double)gr[e] * (double)(ep[e + 1] - ep[e]);
+        ment += (double)(ep[e + 1] - ep[e]);
+    }
+    for (int t = 0; t < 2; t++) {
+        const double w = t ? 8.0 : 4.0;
+        L.spmv_bytes[t] = gent * w + ment * 4.0 + 3.0 * (double)L.n * w;
+        L.coarse_bytes[t] = L.coarsest ? 2.0 * (double)L.n * (double)(L.n + 1) / 2.0 * w : 0.0;
+    }
+    if (!L.coarsest && L.nagg > 0 && L.ncol > 0) {
+        auto oep = to_host(L.oeptr.p, L.nagg + 1, s);
+        auto oei = to_host(L.oeidx.p, oep[L.nagg], s);
+        auto cag = to_host(L.colagg.p, L.nagg, s);
+        for (int t = 0; t < 2; t++) L.sweep_bytes[t].assign(L.ncol, 0.0);
+        for (int c = 0; c < L.ncol; c++)
+            for (int64_t q = L.colptr[c]; q < L.colptr[c + 1]; q++) {
+                const int32_t a = cag[q];
+                const double nO = L.h_nO[a];
+                double g = 0.0, idx = nO;
+                for (int64_t j = oep[a]; j < oep[a + 1]; j++) {
+                    const int32_t e = oei[j];
+                    g += (double)gr[e] * (double)(ep[e + 1] - ep[e]);
+                    idx += 2.0 * (double)(ep[e + 1] - ep[e]);
+                }
+                for (int t = 0; t < 2; t++) {
+                    const double w = t ? 8.0 : 4.0;
+                    // factor (packed lower), element G blocks, index maps, residual gather / x
+                    // update / residual scatter
+                    L.sweep_bytes[t][c] += nO * (nO + 1) / 2.0 * w + g * w + idx * 4.0 + 4.0 * nO * w;
+                }
+            }
+    }
 }
 
 void do_setup(Handle &H, const lsamg_problem *P, const lsamg_options &o) {
@@ -190,7 +226,7 @@ void do_setup(Handle &H, const lsamg_problem *P, const lsamg_options &o) {
             double t = now();
             L.coarsest = true;
             trace("level %d: coarsest (n %lld)", l, (long long)L.n);
-            coarsest_setup(L, err, s, &flops);
+            { LSAMG_PROF("setup: coarsest", s); coarsest_setup(L, err, s, &flops); }
             L.AT.release();
             finish_level_info(L, s);
             st.stage_seconds[7] += now() - t;
@@ -202,14 +238,14 @@ void do_setup(Handle &H, const lsamg_problem *P, const lsamg_options &o) {
         trace("level %d: smoother", l);
         st.stage_seconds[4] += now() - t;
         t = now();
-        smoother_setup(L, o, err, s, &flops);
+        { LSAMG_PROF("setup: smoother factors", s); smoother_setup(L, o, err, s, &flops); }
         st.stage_seconds[5] += now() - t;
         t = now();
         H.levels.emplace_back();
         Level &Lf = H.levels[l];      // re-take references after the vector grew
         Level &Lc = H.levels[l + 1];
         trace("level %d: coarse", l);
-        build_coarse(Lf, Lc, err, s, &flops);
+        { LSAMG_PROF("setup: coarse gram", s); build_coarse(Lf, Lc, err, s, &flops); }
         trace("level %d: coarse built (ne %lld)", l, (long long)Lc.ne);
         Lc.nnz = structural_nnz_coarse(Lf, err, s);
         build_dof_elem(Lc, err, s);
@@ -242,6 +278,7 @@ void do_setup(Handle &H, const lsamg_problem *P, const lsamg_options &o) {
     st.grid_complexity = gc;
     st.setup_flops = flops;
     st.setup_seconds = now() - t0;
+    prof_report("set-up");
 }
 
 void ensure_solve_ws(Handle &H, int nrhs) {
@@ -318,7 +355,10 @@ int do_solve(Handle &H, const double *b, double *x, int nrhs, int mode, bool use
     CK(cudaStreamSynchronize(s));
     int it = 0;
     for (; active > 0 && it < o.maxit; it++) {
-        gram_spmv<double>(L0, p, q, nullptr, nrhs, s);               // q = A p
+        {
+            LSAMG_PROF("krylov: spmv fp64", s);
+            gram_spmv<double>(L0, p, q, nullptr, nrhs, s);           // q = A p
+        }
         vec_dots(p, q, n, nrhs, d, s);
         CK(cudaMemcpyAsync(hv.data(), d, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
@@ -344,7 +384,10 @@ int do_solve(Handle &H, const double *b, double *x, int nrhs, int mode, bool use
             it++;
             break;
         }
-        precondition(H, r, z, nrhs, fp32);
+        {
+            LSAMG_PROF("krylov: precondition", s);
+            precondition(H, r, z, nrhs, fp32);
+        }
         vec_dots(r, z, n, nrhs, d, s);
         if (flexible) vec_dots(ro, z, n, nrhs, d + nrhs, s);
         CK(cudaMemcpyAsync(hv.data(), d, 2 * nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -363,6 +406,7 @@ int do_solve(Handle &H, const double *b, double *x, int nrhs, int mode, bool use
         vec_xpby(p, z, d + 5 * nrhs, n, nrhs, s);
     }
     CK(cudaStreamSynchronize(s));
+    prof_report("solve");
     bool ok = true;
     for (int i = 0; i < nrhs; i++) {
         if (iters) iters[i] = done[i] ? its[i] : it;
@@ -402,8 +446,26 @@ lsamg_options lsamg_options_default(void) {
     o.chunk_bytes = 0;
     o.use_graph = 0;
     o.verbose = 0;
+    o.profile = 0;
     return o;
 }
+
+int32_t lsamg_kernel_classes(void) { return KC_N; }
+const char *lsamg_kernel_name(int32_t cls) { return kclass_name(cls); }
+int lsamg_kernel_stats_all(double *out) {
+    if (!out) return LSAMG_INVALID_ARG;
+    return guarded([&] {
+        KStat st[KC_N];
+        ktimer_collect(st);
+        for (int c = 0; c < KC_N; c++) {
+            out[4 * c + 0] = st[c].ms;
+            out[4 * c + 1] = (double)st[c].calls;
+            out[4 * c + 2] = st[c].flops;
+            out[4 * c + 3] = st[c].bytes;
+        }
+    });
+}
+int64_t lsamg_launch_count(void) { return launch_count(); }
 
 int lsamg_setup(const lsamg_problem *prob, const lsamg_options *opts, void *stream,
                 lsamg_handle **out) {
@@ -413,6 +475,7 @@ int lsamg_setup(const lsamg_problem *prob, const lsamg_options *opts, void *stre
     if (!h) return LSAMG_OOM;
     h->h.stream = (cudaStream_t)stream;
     h->h.opt = opts ? *opts : lsamg_options_default();
+    ktimer_enable(h->h.opt.profile != 0);
     int rc = guarded([&] { do_setup(h->h, prob, h->h.opt); });
     if (rc != LSAMG_OK) {
         std::string msg = g_last_error;

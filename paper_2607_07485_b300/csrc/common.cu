@@ -3,8 +3,116 @@
 
 #include <cstdarg>
 #include <cstdlib>
+#include <ctime>
 
 namespace lsamg {
+
+static int64_t g_launches = 0;
+void count_launch() { g_launches++; }
+int64_t launch_count() { return g_launches; }
+
+static const char *kKNames[KC_N] = {"elem_factor", "potrf", "pstrf", "trsm", "syrk", "sytd2",
+                                    "stebz", "stein", "ormtr", "assemble", "coarse_gram",
+                                    "schwarz_sweep", "gram_spmv", "transfer", "coarse_solve",
+                                    "graph"};
+const char *kclass_name(int c) { return (c >= 0 && c < KC_N) ? kKNames[c] : ""; }
+static bool g_kt_on = false;
+void ktimer_enable(bool on) { g_kt_on = on; }
+bool ktimer_enabled() { return g_kt_on; }
+struct KPending {
+    int cls;
+    cudaEvent_t a, b;
+    double flops, bytes;
+};
+static std::vector<KPending> g_kpend;
+static KStat g_kacc[KC_N];
+
+static std::vector<cudaEvent_t> g_evpool;
+static cudaEvent_t ev_get() {
+    if (!g_evpool.empty()) {
+        cudaEvent_t e = g_evpool.back();
+        g_evpool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+KTime::KTime(int c, cudaStream_t st, double f, double b) : cls(c), s(st), flops(f), bytes(b) {
+    if (!g_kt_on) return;
+    e0 = ev_get();
+    cudaEventRecord(e0, s);
+}
+KTime::~KTime() {
+    if (!g_kt_on || !e0) return;
+    cudaEvent_t e1 = ev_get();
+    cudaEventRecord(e1, s);
+    g_kpend.push_back({cls, e0, e1, flops, bytes});
+}
+
+void ktimer_collect(KStat out[KC_N]) {
+    for (auto &p : g_kpend) {
+        cudaEventSynchronize(p.b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, p.a, p.b);
+        g_kacc[p.cls].ms += ms;
+        g_kacc[p.cls].calls += 1;
+        g_kacc[p.cls].flops += p.flops;
+        g_kacc[p.cls].bytes += p.bytes;
+        g_evpool.push_back(p.a);
+        g_evpool.push_back(p.b);
+    }
+    g_kpend.clear();
+    if (out)
+        for (int c = 0; c < KC_N; c++) {
+            out[c] = g_kacc[c];
+            g_kacc[c] = KStat{};
+        }
+}
+
+static std::vector<std::pair<std::string, double>> g_prof;
+static std::vector<std::pair<std::string, double>> g_open;
+
+bool prof_on() {
+    static const bool on = std::getenv("LSAMG_PROFILE") != nullptr;
+    return on;
+}
+
+static double wall() {
+    timespec t;
+    clock_gettime(CLOCK_MONOTONIC, &t);
+    return t.tv_sec + 1e-9 * t.tv_nsec;
+}
+
+void prof_mark(const char *name, cudaStream_t s, bool begin) {
+    cudaStreamSynchronize(s);
+    double t = wall();
+    if (begin) {
+        g_open.push_back({name, t});
+        return;
+    }
+    for (auto it = g_open.rbegin(); it != g_open.rend(); ++it)
+        if (it->first == name) {
+            double dt = t - it->second;
+            g_open.erase(std::next(it).base());
+            for (auto &q : g_prof)
+                if (q.first == name) {
+                    q.second += dt;
+                    return;
+                }
+            g_prof.push_back({name, dt});
+            return;
+        }
+}
+
+void prof_report(const char *title) {
+    if (!prof_on() || g_prof.empty()) return;
+    fprintf(stderr, "[lsamg profile] %s\n", title);
+    for (auto &q : g_prof) fprintf(stderr, "  %-28s %10.4f s\n", q.first.c_str(), q.second);
+    fflush(stderr);
+    g_prof.clear();
+}
 
 void trace(const char *fmt, ...) {
     static const bool on = std::getenv("LSAMG_TRACE") != nullptr;

@@ -31,12 +31,53 @@ inline void cuda_check(cudaError_t e, const char *what, const char *file, int li
     fail(code, buf);
 }
 #define CK(x) ::lsamg::cuda_check((x), #x, __FILE__, __LINE__)
-#define CK_LAUNCH() ::lsamg::cuda_check(cudaGetLastError(), "kernel launch", __FILE__, __LINE__)
+#define CK_LAUNCH() (::lsamg::count_launch(), ::lsamg::cuda_check(cudaGetLastError(), "kernel launch", __FILE__, __LINE__))
+
+// Number of kernel launches issued by the library (all streams, process-wide).
+void count_launch();
+int64_t launch_count();
 
 inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 // Stage trace on stderr when the environment variable LSAMG_TRACE is set.
 void trace(const char *fmt, ...);
+
+// Opt-in stage profiler (environment variable LSAMG_PROFILE): synchronises the stream around
+// each named region and accumulates wall time; prof_report() prints and clears the totals.
+bool prof_on();
+void prof_mark(const char *name, cudaStream_t s, bool begin);
+void prof_report(const char *title);
+struct ProfScope {
+    const char *n;
+    cudaStream_t s;
+    ProfScope(const char *name, cudaStream_t st) : n(name), s(st) { if (prof_on()) prof_mark(n, s, true); }
+    ~ProfScope() { if (prof_on()) prof_mark(n, s, false); }
+};
+#define LSAMG_PROF(name, stream) ::lsamg::ProfScope _prof_scope_##__LINE__(name, stream)
+
+// Per-kernel-class device timing with CUDA events on the launching stream (enabled by the
+// `profile` option): algorithmic FLOPs / bytes per launch are supplied by the caller.
+enum KClass {
+    KC_ELEM_FACTOR = 0, KC_POTRF, KC_PSTRF, KC_TRSM, KC_SYRK, KC_SYTD2, KC_STEBZ, KC_STEIN,
+    KC_ORMTR, KC_ASSEMBLE, KC_COARSE_GRAM, KC_SCHWARZ, KC_SPMV, KC_TRANSFER, KC_COARSE_SOLVE,
+    KC_GRAPH, KC_N
+};
+const char *kclass_name(int c);
+void ktimer_enable(bool on);
+bool ktimer_enabled();
+struct KTime {
+    int cls;
+    cudaStream_t s;
+    double flops, bytes;
+    cudaEvent_t e0 = nullptr;
+    KTime(int c, cudaStream_t st, double f = 0.0, double b = 0.0);
+    ~KTime();
+};
+struct KStat {
+    double ms = 0.0, flops = 0.0, bytes = 0.0;
+    int64_t calls = 0;
+};
+void ktimer_collect(KStat out[KC_N]);  // synchronises, accumulates and clears pending events
 
 // ---------------------------------------------------------------------------------
 // Stream-ordered device buffer (cudaMallocAsync / cudaFreeAsync), move-only.

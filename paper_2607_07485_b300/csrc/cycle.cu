@@ -2,6 +2,8 @@
 // multiplicative Schwarz sweep on the overlaps, restriction / interpolation with
 // P = [R_w^T Z_i], the dense coarsest solve (Section 2 E_TG; Section 6 preamble), and
 // the FP64 vector kernels of the outer Krylov loop.  Templated on float / double.
+#include <type_traits>
+
 #include "impl.cuh"
 
 namespace lsamg {
@@ -210,6 +212,97 @@ __global__ void k_interp(const int64_t *wptr, const int32_t *widx, const int32_t
     }
 }
 
+// ---------------------------------------------------------------- blocked coarsest solve
+constexpr int CB = 256;  // rows per block of the multi-CTA triangular solves
+
+// forward solve of the diagonal block rows [r0, r1) of L y = v (columns < r0 already applied)
+template <class T>
+__global__ void __launch_bounds__(256) k_cs_fwd_diag(const T *L, int r0, int r1, T *v, int64_t stride) {
+    __shared__ T red[32];
+    T *vr = v + (int64_t)blockIdx.x * stride;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    for (int b0 = r0; b0 < r1; b0 += 32) {
+        const int rs = min(32, r1 - b0);
+        for (int i = warp; i < rs; i += nwarp) {
+            const T *row = L + (int64_t)(b0 + i) * (b0 + i + 1) / 2;
+            T sacc = 0;
+            for (int j = r0 + lane; j < b0; j += 32) sacc += row[j] * vr[j];
+            sacc = warp_sum(sacc);
+            if (lane == 0) red[i] = vr[b0 + i] - sacc;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            T yl = 0;
+            for (int i = 0; i < rs; i++) {
+                const T *row = L + (int64_t)(b0 + i) * (b0 + i + 1) / 2 + b0;
+                T c = (lane < i) ? row[lane] * yl : (T)0;
+                c = warp_sum(c);
+                T yi = (red[i] - c) / row[i];
+                if (lane == i) yl = yi;
+            }
+            if (lane < rs) vr[b0 + lane] = yl;
+        }
+        __syncthreads();
+    }
+}
+
+// v[r] -= sum_{j in [r0, r1)} L[r, j] y[j] for rows r >= r1 (warp per row)
+template <class T>
+__global__ void __launch_bounds__(256) k_cs_fwd_update(const T *L, int r0, int r1, int n, T *v,
+                                                       int64_t stride) {
+    T *vr = v + (int64_t)blockIdx.y * stride;
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = r1 + wid; r < n; r += nw) {
+        const T *row = L + r * (r + 1) / 2;
+        T sacc = 0;
+        for (int j = r0 + lane; j < r1; j += 32) sacc += row[j] * vr[j];
+        sacc = warp_sum(sacc);
+        if (lane == 0) vr[r] -= sacc;
+    }
+}
+
+// backward solve of the diagonal block [r0, r1) of L^T x = y (rows >= r1 already applied)
+template <class T>
+__global__ void __launch_bounds__(256) k_cs_bwd_diag(const T *L, int r0, int r1, T *v, int64_t stride) {
+    T *vr = v + (int64_t)blockIdx.x * stride;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nb = (r1 - r0 + 31) / 32;
+    for (int bi = nb - 1; bi >= 0; bi--) {
+        const int b0 = r0 + bi * 32, rs = min(32, r1 - b0);
+        if (warp == 0) {
+            T xl = (lane < rs) ? vr[b0 + lane] : (T)0;
+            for (int i = rs - 1; i >= 0; i--) {
+                const T *row = L + (int64_t)(b0 + i) * (b0 + i + 1) / 2 + b0;
+                T xi = __shfl_sync(0xffffffffu, xl, i) / row[i];
+                if (lane == i) xl = xi;
+                if (lane < i) xl -= row[lane] * xi;
+            }
+            if (lane < rs) vr[b0 + lane] = xl;
+        }
+        __syncthreads();
+        for (int j = r0 + threadIdx.x; j < b0; j += blockDim.x) {
+            T sacc = 0;
+            for (int i = 0; i < rs; i++) sacc += L[(int64_t)(b0 + i) * (b0 + i + 1) / 2 + j] * vr[b0 + i];
+            vr[j] -= sacc;
+        }
+        __syncthreads();
+    }
+}
+
+// v[j] -= sum_{i in [r0, r1)} L[i, j] x[i] for columns j < r0 (thread per column)
+template <class T>
+__global__ void __launch_bounds__(256) k_cs_bwd_update(const T *L, int r0, int r1, T *v, int64_t stride) {
+    T *vr = v + (int64_t)blockIdx.y * stride;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < r0;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        T sacc = 0;
+        for (int i = r0; i < r1; i++) sacc += L[(int64_t)i * (i + 1) / 2 + j] * vr[i];
+        vr[j] -= sacc;
+    }
+}
+
 template <class T>
 __global__ void __launch_bounds__(1024) k_coarse_solve(const T *L, int n, T *v, int64_t stride,
                                                        int nrhs) {
@@ -306,6 +399,7 @@ void gram_spmv(const Level &L, const T *x, T *y, const T *b, int nrhs, cudaStrea
         CK(cudaMemsetAsync(y, 0, tot * sizeof(T), s));
     }
     if (L.ne == 0) return;
+    KTime kt(KC_SPMV, s, 0.0, L.spmv_bytes[std::is_same<T, double>::value ? 1 : 0] * (nrhs > 1 ? 1.0 : 1.0));
     const T *G = std::is_same<T, float>::value ? (const T *)L.G32.p : (const T *)L.G64.p;
     int32_t maxm = 0;
     // rows per element never exceed the element-map length on level 0; coarse groups can
@@ -365,6 +459,8 @@ static void sweep(Level &L, int c, int nrhs, cudaStream_t s) {
         G = L.G64.p;
     }
     size_t sm = (size_t)std::max(1, L.max_grows_cached) * sizeof(T);
+    KTime kt(KC_SCHWARZ, s, 0.0, L.sweep_bytes[std::is_same<T, double>::value ? 1 : 0].empty() ? 0.0
+                                     : L.sweep_bytes[std::is_same<T, double>::value ? 1 : 0][c]);
     k_schwarz<T><<<(unsigned)std::min<int64_t>(na, 148 * 8), 256, sm, s>>>(
         L.colagg.p + L.colptr[c], na, L.Optr.p, L.Oidx.p, Lp, L.Loff.p, L.oeptr.p, L.oeidx.p,
         L.oelocoff.p, L.oeloc.p, L.eptr.p, L.eidx.p, G, L.goff.p, L.grows.p, xvec<T>(L), rvec<T>(L),
@@ -378,31 +474,68 @@ void vcycle(Handle &H, int l, int nrhs, cudaStream_t s) {
     const int64_t tot = L.n * nrhs;
     T *b = bvec<T>(L), *x = xvec<T>(L), *r = rvec<T>(L);
     if (L.coarsest) {
+        LSAMG_PROF("vc: coarsest solve", s);
         CK(cudaMemcpyAsync(x, b, tot * sizeof(T), cudaMemcpyDeviceToDevice, s));
         const T *Ld;
         if constexpr (std::is_same<T, float>::value) Ld = L.Ld32.p; else Ld = L.Ld64.p;
-        k_coarse_solve<T><<<(unsigned)nrhs, 1024, 0, s>>>(Ld, (int)L.n, x, L.n, nrhs);
-        CK_LAUNCH();
+        const int n = (int)L.n;
+        KTime kt(KC_COARSE_SOLVE, s, 0.0, L.coarse_bytes[std::is_same<T, double>::value ? 1 : 0] * nrhs);
+        if (n <= 2 * CB) {
+            k_coarse_solve<T><<<(unsigned)nrhs, 1024, 0, s>>>(Ld, n, x, L.n, nrhs);
+            CK_LAUNCH();
+            return;
+        }
+        for (int r0 = 0; r0 < n; r0 += CB) {
+            const int r1 = std::min(n, r0 + CB);
+            k_cs_fwd_diag<T><<<(unsigned)nrhs, 256, 0, s>>>(Ld, r0, r1, x, L.n);
+            CK_LAUNCH();
+            if (r1 < n) {
+                dim3 g((unsigned)std::min<int64_t>(cdiv((int64_t)(n - r1) * 32, 256), 148 * 8), (unsigned)nrhs);
+                k_cs_fwd_update<T><<<g, 256, 0, s>>>(Ld, r0, r1, n, x, L.n);
+                CK_LAUNCH();
+            }
+        }
+        for (int r1 = n; r1 > 0; r1 -= CB) {
+            const int r0 = std::max(0, r1 - CB);
+            k_cs_bwd_diag<T><<<(unsigned)nrhs, 256, 0, s>>>(Ld, r0, r1, x, L.n);
+            CK_LAUNCH();
+            if (r0 > 0) {
+                dim3 g((unsigned)std::min<int64_t>(cdiv(r0, 256), 148 * 8), (unsigned)nrhs);
+                k_cs_bwd_update<T><<<g, 256, 0, s>>>(Ld, r0, r1, x, L.n);
+                CK_LAUNCH();
+            }
+        }
         return;
     }
     Level &C = H.levels[l + 1];
     CK(cudaMemsetAsync(x, 0, tot * sizeof(T), s));
     CK(cudaMemcpyAsync(r, b, tot * sizeof(T), cudaMemcpyDeviceToDevice, s));
-    for (int c = 0; c < L.ncol; c++) sweep<T>(L, c, nrhs, s);
+    {
+        LSAMG_PROF(l == 0 ? "vc: L0 pre-smooth" : "vc: Lc pre-smooth", s);
+        for (int c = 0; c < L.ncol; c++) sweep<T>(L, c, nrhs, s);
+    }
     const T *Z;
     if constexpr (std::is_same<T, float>::value) Z = L.Z32.p; else Z = L.Z64.p;
+    {
+    KTime kt(KC_TRANSFER, s);
     k_restrict<T><<<gridv(L.nagg, 1, 148 * 16), 128, 0, s>>>(L.wptr.p, L.widx.p, L.k.p, L.off.p, Z,
                                                             L.zoff.p, L.nagg, r, L.n, bvec<T>(C),
                                                             C.n, nrhs);
     CK_LAUNCH();
+    }
     vcycle<T>(H, l + 1, nrhs, s);
+    {
+    KTime kt(KC_TRANSFER, s);
     k_interp<T><<<gridv(L.nagg, 1, 148 * 16), 256, 0, s>>>(L.wptr.p, L.widx.p, L.k.p, L.off.p, Z,
                                                           L.zoff.p, L.nagg, xvec<T>(C), C.n, x,
                                                           L.n, nrhs);
     CK_LAUNCH();
+    }
     // residual after the coarse correction: r = b - A x
     CK(cudaMemcpyAsync(r, b, tot * sizeof(T), cudaMemcpyDeviceToDevice, s));
     {
+        LSAMG_PROF(l == 0 ? "vc: L0 residual spmv" : "vc: Lc residual spmv", s);
+        KTime kt(KC_SPMV, s, 0.0, L.spmv_bytes[std::is_same<T, double>::value ? 1 : 0]);
         const T *G;
         if constexpr (std::is_same<T, float>::value) G = L.G32.p; else G = L.G64.p;
         size_t sm = (size_t)std::max(1, L.max_grows_cached) * sizeof(T);
@@ -410,7 +543,10 @@ void vcycle(Handle &H, int l, int nrhs, cudaStream_t s) {
                                                           L.grows.p, x, r, L.n, nrhs, (T)-1);
         CK_LAUNCH();
     }
-    for (int c = L.ncol - 1; c >= 0; c--) sweep<T>(L, c, nrhs, s);
+    {
+        LSAMG_PROF(l == 0 ? "vc: L0 post-smooth" : "vc: Lc post-smooth", s);
+        for (int c = L.ncol - 1; c >= 0; c--) sweep<T>(L, c, nrhs, s);
+    }
 }
 
 template void vcycle<float>(Handle &, int, int, cudaStream_t);

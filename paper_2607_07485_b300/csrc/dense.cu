@@ -128,20 +128,29 @@ __device__ __forceinline__ void tri_index(int t, int &ti, int &tj) {
 // trailing update A22 -= L21 L21^T on lower tiles
 __global__ void __launch_bounds__(256) k_potrf_update(double *base, const int64_t *off,
                                                       const int32_t *ld, const int32_t *nn,
-                                                      int64_t count, int j0) {
+                                                      int64_t count, int j0, const int32_t *b0,
+                                                      const int32_t *stop, int full) {
     int64_t b = blockIdx.y;
     if (b >= count) return;
+    if (stop && stop[b] >= 0) return;  // pivoted factorisation already truncated
     int n = nn[b];
     int bs = min(NB, n - j0);
-    int r0 = j0 + bs;
+    int r0 = j0 + min(NB, n - j0);
     int m = n - r0;
     if (m <= 0 || bs <= 0) return;
     int T = (m + TT - 1) / TT;
-    if ((int64_t)blockIdx.x >= (int64_t)T * (T + 1) / 2) return;
     int ti, tj;
-    tri_index(blockIdx.x, ti, tj);
+    if (full) {
+        if ((int64_t)blockIdx.x >= (int64_t)T * T) return;
+        ti = blockIdx.x / T;
+        tj = blockIdx.x % T;
+    } else {
+        if ((int64_t)blockIdx.x >= (int64_t)T * (T + 1) / 2) return;
+        tri_index(blockIdx.x, ti, tj);
+    }
     int L = ld[b];
-    double *A = base + off[b];
+    const int o0 = b0 ? b0[b] : 0;
+    double *A = base + off[b] + (int64_t)o0 + (int64_t)o0 * L;
     __shared__ double As[NB][TT + 1];
     __shared__ double Bs[NB][TT + 1];
     int ib = r0 + ti * TT, jb = r0 + tj * TT;
@@ -172,8 +181,114 @@ __global__ void __launch_bounds__(256) k_potrf_update(double *base, const int64_
 #pragma unroll
         for (int v = 0; v < 4; v++) {
             int gi = ib + ty * 4 + u, gj = jb + tx * 4 + v;
-            if (gi < n && gj < n && gi >= gj) A[gi + (int64_t)gj * L] -= acc[u][v];
+            if (gi < n && gj < n && (full || gi >= gj)) A[gi + (int64_t)gj * L] -= acc[u][v];
         }
+}
+
+// one panel of the pivoted Cholesky (one CTA per matrix); columns j0 .. j0+NB-1 of the block
+__global__ void __launch_bounds__(256) k_pstf_panel(double *base, const int64_t *off,
+                                                    const int32_t *ld, const int32_t *nfull,
+                                                    const int32_t *b0s, const int32_t *bns,
+                                                    int64_t count, int j0, int32_t *perm,
+                                                    const int64_t *permoff, int32_t *rank,
+                                                    double *work, const int64_t *workoff,
+                                                    const double *md) {
+    int64_t b = blockIdx.x;
+    if (b >= count) return;
+    const int n = bns[b];
+    if (j0 >= n || rank[b] >= 0) return;  // finished or stopped earlier
+    const int L = ld[b], N = nfull[b], g0 = b0s[b];
+    double *M = base + off[b];                        // whole view
+    double *A = M + (int64_t)g0 + (int64_t)g0 * L;    // the pivoted block
+    int32_t *pv = perm + permoff[b];
+    double *w = work + workoff[b];
+    const double tol = 10.0 * DEPS * md[b];
+    __shared__ double red_v[32];
+    __shared__ int red_i[32];
+    __shared__ int piv;
+    __shared__ double pval;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    for (int i = j0 + threadIdx.x; i < n; i += blockDim.x) w[i] = A[i + (int64_t)i * L];
+    __syncthreads();
+    const int jend = min(n, j0 + NB);
+    for (int j = j0; j < jend; j++) {
+        // pivot: largest updated diagonal among rows j..n-1 (first index on ties)
+        double bv = -1e300;
+        int bi = n;
+        for (int i = j + threadIdx.x; i < n; i += blockDim.x)
+            if (w[i] > bv || (w[i] == bv && i < bi)) {
+                bv = w[i];
+                bi = i;
+            }
+        for (int o = 16; o; o >>= 1) {
+            double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov > bv || (ov == bv && oi < bi)) {
+                bv = ov;
+                bi = oi;
+            }
+        }
+        if (lane == 0) {
+            red_v[warp] = bv;
+            red_i[warp] = bi;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double v = red_v[0];
+            int id = red_i[0];
+            for (int q = 1; q < nwarp; q++)
+                if (red_v[q] > v || (red_v[q] == v && red_i[q] < id)) {
+                    v = red_v[q];
+                    id = red_i[q];
+                }
+            piv = id;
+            pval = v;
+        }
+        __syncthreads();
+        const int p = piv;
+        if (!(pval > tol)) {
+            // numerically zero trailing block: rank j, zero pivots from here on
+            for (int i = j + threadIdx.x; i < n; i += blockDim.x) A[i + (int64_t)i * L] = 0.0;
+            if (threadIdx.x == 0) rank[b] = j;
+            return;
+        }
+        if (p != j) {
+            // swap rows g0+j and g0+p, then columns, over the whole view
+            for (int c = threadIdx.x; c < N; c += blockDim.x) {
+                double t = M[(g0 + j) + (int64_t)c * L];
+                M[(g0 + j) + (int64_t)c * L] = M[(g0 + p) + (int64_t)c * L];
+                M[(g0 + p) + (int64_t)c * L] = t;
+            }
+            __syncthreads();
+            for (int r = threadIdx.x; r < N; r += blockDim.x) {
+                double t = M[r + (int64_t)(g0 + j) * L];
+                M[r + (int64_t)(g0 + j) * L] = M[r + (int64_t)(g0 + p) * L];
+                M[r + (int64_t)(g0 + p) * L] = t;
+            }
+            if (threadIdx.x == 0) {
+                double t = w[j];
+                w[j] = w[p];
+                w[p] = t;
+                int u = pv[j];
+                pv[j] = pv[p];
+                pv[p] = u;
+            }
+            __syncthreads();
+        }
+        const double ljj = sqrt(w[j]);
+        // column j: l_ij = (a_ij - sum_{k in panel, k<j} l_ik l_jk) / l_jj
+        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) {
+            double v = A[i + (int64_t)j * L];
+            for (int k = j0; k < j; k++) v -= A[i + (int64_t)k * L] * A[j + (int64_t)k * L];
+            v /= ljj;
+            A[i + (int64_t)j * L] = v;
+            w[i] -= v * v;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) A[j + (int64_t)j * L] = ljj;
+        __syncthreads();
+    }
+    (void)lane;
 }
 
 // ------------------------------------------------------------------------- trsm
@@ -358,85 +473,86 @@ __device__ double block_sum(double v, double *red) {
     return r;
 }
 
+// One CTA per matrix.  Per column j: Householder vector v (staged in shared memory), the
+// symmetric product p = tau A22 v in ONE sweep over the stored lower triangle (each warp owns
+// columns: column sums reduce in registers, the transposed contributions accumulate in shared
+// memory with atomics), then the rank-2 update A22 -= v w^T + w v^T.
 __global__ void __launch_bounds__(512) k_sytd2(double *base, const int64_t *off, const int32_t *ld,
                                                const int32_t *nn, int64_t count, double *dd,
                                                double *ee, double *tt, const int64_t *toff,
-                                               double *pwork, const int64_t *pwoff) {
+                                               double *pwork, const int64_t *pwoff, int use_smem) {
+    extern __shared__ double smv[];
     int64_t b = blockIdx.x;
     if (b >= count) return;
-    int n = nn[b];
-    int L = ld[b];
+    const int n = nn[b];
+    const int L = ld[b];
     double *A = base + off[b];
     double *d = dd + toff[b], *e = ee + toff[b], *tau = tt + toff[b];
-    double *p = pwork + pwoff[b];  // length n
+    double *p = use_smem ? smv : pwork + 2 * pwoff[b];
+    double *v = use_smem ? smv + n : pwork + 2 * pwoff[b] + n;
     __shared__ double red[32];
-    __shared__ double sh_tau, sh_alpha_scale;
+    __shared__ double sh_tau, sh_scale;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     for (int j = 0; j < n - 1; j++) {
-        int m = n - j - 1;                 // length of x = A[j+1:n, j]
+        const int m = n - j - 1;
         double *x = A + (j + 1) + (int64_t)j * L;
         double sig = 0.0;
         for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) sig += x[i] * x[i];
         sig = block_sum(sig, red);
         if (threadIdx.x == 0) {
-            double alpha = x[0];
+            const double alpha = x[0];
             d[j] = A[j + (int64_t)j * L];
             if (sig == 0.0) {
                 sh_tau = 0.0;
                 e[j] = alpha;
-                sh_alpha_scale = 0.0;
+                sh_scale = 0.0;
             } else {
-                double beta = -copysign(sqrt(alpha * alpha + sig), alpha);
+                const double beta = -copysign(sqrt(alpha * alpha + sig), alpha);
                 sh_tau = (beta - alpha) / beta;
-                sh_alpha_scale = 1.0 / (alpha - beta);
+                sh_scale = 1.0 / (alpha - beta);
                 e[j] = beta;
             }
             tau[j] = sh_tau;
         }
         __syncthreads();
-        double tj = sh_tau, sc = sh_alpha_scale;
-        if (tj == 0.0) {
-            __syncthreads();
-            continue;
+        const double tj = sh_tau, sc = sh_scale;
+        if (tj == 0.0) continue;
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+            const double vi = (i == 0) ? 1.0 : x[i] * sc;
+            v[i] = vi;
+            if (i > 0) x[i] = vi;
+            p[i] = 0.0;
         }
-        for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) x[i] *= sc;
-        if (threadIdx.x == 0) x[0] = 1.0;  // v[0] = 1 (restored to beta below)
         __syncthreads();
-        // p = tau * A22 v with A22 = A[j+1:, j+1:] (lower triangle stored)
         double *A22 = A + (j + 1) + (int64_t)(j + 1) * L;
-        // pass 1: p[c] = sum_{r >= c} A22[r, c] v[r]  (warp per column)
         for (int c = warp; c < m; c += nwarp) {
-            double s = 0.0;
+            const double vc = v[c];
             const double *col = A22 + (int64_t)c * L;
-            for (int r = c + lane; r < m; r += 32) s += col[r] * x[r];
-            for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) p[c] = s;
-        }
-        __syncthreads();
-        // pass 2: p[r] += sum_{c < r} A22[r, c] v[c]  (thread per row)
-        for (int r0 = 0; r0 < m; r0 += blockDim.x) {
-            int r = r0 + threadIdx.x;
-            double s = 0.0;
-            int cmax = min(r0 + (int)blockDim.x, m);
-            for (int c = 0; c < cmax; c++)
-                if (c < r && r < m) s += A22[r + (int64_t)c * L] * x[c];
-            if (r < m) p[r] = tj * (p[r] + s);
+            double sacc = 0.0;
+            for (int r = c + lane; r < m; r += 32) {
+                const double a = col[r];
+                sacc += a * v[r];
+                if (r > c) atomicAdd(&p[r], a * vc);
+            }
+            for (int o = 16; o; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+            if (lane == 0) atomicAdd(&p[c], sacc);
         }
         __syncthreads();
         double pv = 0.0;
-        for (int i = threadIdx.x; i < m; i += blockDim.x) pv += p[i] * x[i];
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+            p[i] *= tj;
+            pv += p[i] * v[i];
+        }
         pv = block_sum(pv, red);
-        double kk = -0.5 * tj * pv;
-        for (int i = threadIdx.x; i < m; i += blockDim.x) p[i] += kk * x[i];  // w
+        const double kk = -0.5 * tj * pv;
+        for (int i = threadIdx.x; i < m; i += blockDim.x) p[i] += kk * v[i];  // w
         __syncthreads();
-        // A22 -= v w^T + w v^T (lower)
         for (int c = warp; c < m; c += nwarp) {
-            double vc = x[c], wc = p[c];
+            const double vc = v[c], wc = p[c];
             double *col = A22 + (int64_t)c * L;
-            for (int r = c + lane; r < m; r += 32) col[r] -= x[r] * wc + p[r] * vc;
+            for (int r = c + lane; r < m; r += 32) col[r] -= v[r] * wc + p[r] * vc;
         }
         __syncthreads();
-        // keep v in place (v[0] implicit); store beta on the subdiagonal position
         if (threadIdx.x == 0) x[0] = e[j];
         __syncthreads();
     }
@@ -526,6 +642,8 @@ __device__ __forceinline__ double urand(uint32_t a, uint32_t b) {
     return (double)x * (2.0 / 4294967296.0) - 1.0;
 }
 
+constexpr int STEIN_SLOTS = 64;  // eigenvalues iterated concurrently per matrix (one per thread)
+
 __global__ void __launch_bounds__(256) k_stein(const double *dd, const double *ee,
                                                const int64_t *toff, const int32_t *nn,
                                                int64_t count, const double *wv, const int32_t *kk,
@@ -534,117 +652,127 @@ __global__ void __launch_bounds__(256) k_stein(const double *dd, const double *e
                                                const int64_t *workoff) {
     int64_t b = blockIdx.x;
     if (b >= count) return;
-    int n = nn[b], k = kk[b];
+    const int n = nn[b], k = kk[b];
     if (k <= 0 || n <= 0) return;
     const double *d = dd + toff[b], *e = ee + toff[b], *w = wv + toff[b];
     double *V = baseV + voff[b];
-    int LV = vld[b];
-    double *W = work + workoff[b];
-    double *dg = W, *su = W + n, *su2 = W + 2 * n, *mu = W + 3 * n, *pv = W + 4 * n, *x = W + 5 * n;
+    const int LV = vld[b];
+    double *W = work + workoff[b];  // 4 n STEIN_SLOTS doubles, element i of slot s at [i*S + s]
+    constexpr int S = STEIN_SLOTS;
     __shared__ double red[32];
     __shared__ double tnorm;
-    if (threadIdx.x == 0) {
+    __shared__ double hsh[1024];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    {
         double t = 0.0;
-        for (int i = 0; i < n; i++)
+        for (int i = threadIdx.x; i < n; i += blockDim.x)
             t = fmax(t, fabs(d[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < n - 1 ? fabs(e[i]) : 0.0));
-        tnorm = fmax(t, 1e-300);
-    }
-    __syncthreads();
-    const double ortol = 1e-3 * tnorm, pertol = 10.0 * DEPS * tnorm;
-    int cstart = 0;
-    double lamprev = 0.0;
-    for (int j = 0; j < k; j++) {
-        double lam = w[j];
-        if (j > 0) {
-            if (lam - w[j - 1] > ortol) cstart = j;
-            if (lam - lamprev < pertol) lam = lamprev + pertol;
-        }
-        lamprev = lam;
-        // LU with partial pivoting of T - lam I (serial, O(n))
-        if (threadIdx.x == 0) {
-            for (int i = 0; i < n; i++) {
-                dg[i] = d[i] - lam;
-                su[i] = (i < n - 1) ? e[i] : 0.0;
-                su2[i] = 0.0;
-            }
-            for (int i = 0; i < n - 1; i++) {
-                double sub = e[i];
-                if (fabs(dg[i]) >= fabs(sub)) {
-                    if (dg[i] == 0.0) dg[i] = pertol;
-                    double m = sub / dg[i];
-                    mu[i] = m;
-                    pv[i] = 0.0;
-                    dg[i + 1] -= m * su[i];
-                } else {
-                    double m = dg[i] / sub;
-                    mu[i] = m;
-                    pv[i] = 1.0;
-                    double od = dg[i + 1], os = su[i], os1 = su[i + 1];
-                    dg[i] = sub;
-                    su[i] = od;
-                    su2[i] = os1;
-                    dg[i + 1] = os - m * od;
-                    su[i + 1] = -m * os1;
-                }
-            }
-            if (dg[n - 1] == 0.0) dg[n - 1] = pertol;
-        }
-        for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = urand((uint32_t)j, (uint32_t)i);
+        for (int o = 16; o; o >>= 1) t = fmax(t, __shfl_xor_sync(0xffffffffu, t, o));
+        if (lane == 0) red[warp] = t;
         __syncthreads();
-        for (int it = 0; it < 3; it++) {
-            // scale to unit infinity norm
-            double mx = 0.0;
-            for (int i = threadIdx.x; i < n; i += blockDim.x) mx = fmax(mx, fabs(x[i]));
-            for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-            __syncthreads();
-            if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                double r = 0.0;
-                for (int i = 0; i < (int)(blockDim.x >> 5); i++) r = fmax(r, red[i]);
-                red[0] = (r > 0.0) ? 1.0 / r : 1.0;
-            }
-            __syncthreads();
-            double inv = red[0];
-            for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] *= inv;
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                // forward: apply row interchanges and multipliers
+        if (threadIdx.x == 0) {
+            double r = 0.0;
+            for (int q = 0; q < nwarp; q++) r = fmax(r, red[q]);
+            tnorm = fmax(r, 1e-300);
+        }
+        __syncthreads();
+    }
+    const double ortol = 1e-3 * tnorm, pertol = 10.0 * DEPS * tnorm;
+    // ---- phase 1: independent inverse iteration, one eigenvalue per thread at a time
+    if (threadIdx.x < S) {
+        const int sl = threadIdx.x;
+        double *dg = W, *su = W + (int64_t)n * S, *su2 = W + 2 * (int64_t)n * S,
+               *x = W + 3 * (int64_t)n * S;
+        for (int j = sl; j < k; j += S) {
+            // separate numerically equal eigenvalues by multiples of pertol
+            int q = j;
+            while (q > 0 && w[q] - w[q - 1] < pertol) q--;
+            const double lam = w[j] + (double)(j - q) * pertol;
+            for (int i = 0; i < n; i++) x[(int64_t)i * S + sl] = urand((uint32_t)j, (uint32_t)i);
+            for (int it = 0; it < 3; it++) {
+                double mx = 0.0;
+                for (int i = 0; i < n; i++) mx = fmax(mx, fabs(x[(int64_t)i * S + sl]));
+                const double sc = (mx > 0.0) ? 1.0 / mx : 1.0;
+                // factor T - lam I with partial pivoting while eliminating the right-hand side
+                double diag = d[0] - lam, sup = (n > 1) ? e[0] : 0.0, rhs = x[sl] * sc;
                 for (int i = 0; i < n - 1; i++) {
-                    if (pv[i] != 0.0) {
-                        double t = x[i];
-                        x[i] = x[i + 1];
-                        x[i + 1] = t - mu[i] * x[i];
+                    const double sub = e[i], nd = d[i + 1] - lam, ns = (i + 1 < n - 1) ? e[i + 1] : 0.0;
+                    const double nrhs = x[(int64_t)(i + 1) * S + sl] * sc;
+                    const int64_t ii = (int64_t)i * S + sl;
+                    if (fabs(diag) >= fabs(sub)) {
+                        if (diag == 0.0) diag = pertol;
+                        const double m = sub / diag;
+                        dg[ii] = diag;
+                        su[ii] = sup;
+                        su2[ii] = 0.0;
+                        x[ii] = rhs;
+                        diag = nd - m * sup;
+                        sup = ns;
+                        rhs = nrhs - m * rhs;
                     } else {
-                        x[i + 1] -= mu[i] * x[i];
+                        const double m = diag / sub;
+                        dg[ii] = sub;
+                        su[ii] = nd;
+                        su2[ii] = ns;
+                        x[ii] = nrhs;
+                        diag = sup - m * nd;
+                        sup = -m * ns;
+                        rhs = rhs - m * nrhs;
                     }
                 }
-                // back substitution with U (diag dg, super su, second super su2)
-                for (int i = n - 1; i >= 0; i--) {
-                    double v = x[i];
-                    if (i + 1 < n) v -= su[i] * x[i + 1];
-                    if (i + 2 < n) v -= su2[i] * x[i + 2];
-                    x[i] = v / dg[i];
+                if (diag == 0.0) diag = pertol;
+                const int64_t il = (int64_t)(n - 1) * S + sl;
+                dg[il] = diag;
+                x[il] = rhs / diag;
+                for (int i = n - 2; i >= 0; i--) {
+                    const int64_t ii = (int64_t)i * S + sl;
+                    double v = x[ii] - su[ii] * x[ii + S];
+                    if (i + 2 < n) v -= su2[ii] * x[ii + 2 * S];
+                    x[ii] = v / dg[ii];
                 }
             }
-            __syncthreads();
-            // re-orthogonalise against earlier members of the cluster (modified Gram-Schmidt)
-            for (int c = cstart; c < j; c++) {
-                double s = 0.0;
-                const double *vc = V + (int64_t)c * LV;
-                for (int i = threadIdx.x; i < n; i += blockDim.x) s += vc[i] * x[i];
-                s = block_sum(s, red);
-                for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] -= s * vc[i];
-                __syncthreads();
-            }
+            double nr = 0.0;
+            for (int i = 0; i < n; i++) nr += x[(int64_t)i * S + sl] * x[(int64_t)i * S + sl];
+            const double inv = (nr > 0.0) ? 1.0 / sqrt(nr) : 0.0;
+            double *vj = V + (int64_t)j * LV;
+            for (int i = 0; i < n; i++) vj[i] = x[(int64_t)i * S + sl] * inv;
         }
-        double s = 0.0;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) s += x[i] * x[i];
-        s = block_sum(s, red);
-        double inv = (s > 0.0) ? 1.0 / sqrt(s) : 0.0;
-        double *vj = V + (int64_t)j * LV;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) vj[i] = x[i] * inv;
-        __syncthreads();
+    }
+    __syncthreads();
+    // ---- phase 2: orthonormalise every cluster (gaps <= ortol) by classical Gram-Schmidt twice
+    int c0 = 0;
+    while (c0 < k) {
+        int c1 = c0 + 1;
+        while (c1 < k && w[c1] - w[c1 - 1] <= ortol) c1++;
+        for (int j = c0 + 1; j < c1; j++) {
+            double *vj = V + (int64_t)j * LV;
+            for (int pass = 0; pass < 2; pass++) {
+                for (int i0 = c0; i0 < j; i0 += 1024) {
+                    const int i1 = min(j, i0 + 1024);
+                    for (int i = i0 + warp; i < i1; i += nwarp) {
+                        const double *vi = V + (int64_t)i * LV;
+                        double sd = 0.0;
+                        for (int r = lane; r < n; r += 32) sd += vi[r] * vj[r];
+                        for (int o = 16; o; o >>= 1) sd += __shfl_xor_sync(0xffffffffu, sd, o);
+                        if (lane == 0) hsh[i - i0] = sd;
+                    }
+                    __syncthreads();
+                    for (int r = threadIdx.x; r < n; r += blockDim.x) {
+                        double acc = 0.0;
+                        for (int i = i0; i < i1; i++) acc += hsh[i - i0] * V[(int64_t)i * LV + r];
+                        vj[r] -= acc;
+                    }
+                    __syncthreads();
+                }
+            }
+            double nr = 0.0;
+            for (int r = threadIdx.x; r < n; r += blockDim.x) nr += vj[r] * vj[r];
+            nr = block_sum(nr, red);
+            const double inv = (nr > 0.0) ? 1.0 / sqrt(nr) : 0.0;
+            for (int r = threadIdx.x; r < n; r += blockDim.x) vj[r] *= inv;
+            __syncthreads();
+        }
+        c0 = c1;
     }
 }
 
@@ -684,6 +812,9 @@ __global__ void __launch_bounds__(256) k_ormtr(const double *baseA, const int64_
 // ============================================================================= host wrappers
 void potrf_batched(double *base, const MatBatch &A, PotrfMode mode, int *err, cudaStream_t s) {
     if (A.count == 0 || A.maxn == 0) return;
+    double fl = 0.0;
+    for (auto v : A.h_n) fl += (double)v * v * v / 3.0;
+    KTime kt(KC_POTRF, s, fl);
     DBuf<double> md;
     md.alloc(A.count, s);
     k_maxdiag<<<(unsigned)A.count, 256, 0, s>>>(base, A.off.p, A.ld.p, A.n.p, A.count, md.p);
@@ -699,14 +830,81 @@ void potrf_batched(double *base, const MatBatch &A, PotrfMode mode, int *err, cu
         CK_LAUNCH();
         int64_t T = cdiv(rem, TT);
         dim3 gu((unsigned)(T * (T + 1) / 2), (unsigned)A.count);
-        k_potrf_update<<<gu, 256, 0, s>>>(base, A.off.p, A.ld.p, A.n.p, A.count, j0);
+        k_potrf_update<<<gu, 256, 0, s>>>(base, A.off.p, A.ld.p, A.n.p, A.count, j0, nullptr,
+                                          nullptr, 0);
         CK_LAUNCH();
     }
+}
+
+namespace {
+__global__ void k_maxdiag_block(const double *base, const int64_t *off, const int32_t *ld,
+                                const int32_t *b0, const int32_t *bn, int64_t count, double *md,
+                                int32_t *perm, const int64_t *permoff, int32_t *rank) {
+    int64_t b = blockIdx.x;
+    if (b >= count) return;
+    const int L = ld[b], g0 = b0[b], n = bn[b];
+    const double *A = base + off[b] + (int64_t)g0 + (int64_t)g0 * L;
+    double m = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        m = fmax(m, A[i + (int64_t)i * L]);
+        perm[permoff[b] + i] = i;
+    }
+    for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __shared__ double w[32];
+    if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r = 0.0;
+        for (int i = 0; i < (int)(blockDim.x + 31) / 32; i++) r = fmax(r, w[i]);
+        md[b] = r;
+        rank[b] = (n == 0) ? 0 : -1;
+    }
+}
+}  // namespace
+
+namespace {
+__global__ void k_rank_finish(int32_t *rank, const int32_t *bn, int64_t count) {
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < count && rank[b] < 0) rank[b] = bn[b];
+}
+}  // namespace
+
+void pstrf_batched(double *base, const MatBatch &A, const int32_t *b0, const int32_t *bn,
+                   int32_t max_bn, int32_t *perm, const int64_t *permoff, int32_t *rank,
+                   cudaStream_t s) {
+    if (A.count == 0 || max_bn == 0) return;
+    KTime kt(KC_PSTRF, s);
+    DBuf<double> md, work;
+    DBuf<int64_t> woff;
+    md.alloc(A.count, s);
+    // work shares the permutation layout (one double per block row)
+    int64_t tot = read1(permoff + A.count, s);
+    work.alloc(std::max<int64_t>(tot, 1), s);
+    k_maxdiag_block<<<(unsigned)A.count, 256, 0, s>>>(base, A.off.p, A.ld.p, b0, bn, A.count, md.p,
+                                                       perm, permoff, rank);
+    CK_LAUNCH();
+    for (int j0 = 0; j0 < max_bn; j0 += NB) {
+        k_pstf_panel<<<(unsigned)A.count, 256, 0, s>>>(base, A.off.p, A.ld.p, A.n.p, b0, bn,
+                                                      A.count, j0, perm, permoff, rank, work.p,
+                                                      permoff, md.p);
+        CK_LAUNCH();
+        int rem = max_bn - j0 - NB;
+        if (rem <= 0) break;
+        int64_t T = cdiv(rem, TT);
+        dim3 gu((unsigned)(T * T), (unsigned)A.count);
+        k_potrf_update<<<gu, 256, 0, s>>>(base, A.off.p, A.ld.p, bn, A.count, j0, b0, rank, 1);
+        CK_LAUNCH();
+    }
+    k_rank_finish<<<(unsigned)cdiv(A.count, 256), 256, 0, s>>>(rank, bn, A.count);
+    CK_LAUNCH();
 }
 
 void trsm_batched(const double *base_L, const MatBatch &Lb, double *base_B, const MatBatch &Bb,
                   bool trans, cudaStream_t s) {
     if (Bb.count == 0 || Bb.maxm == 0 || Lb.maxn == 0) return;
+    double fl = 0.0;
+    for (size_t i = 0; i < Bb.h_n.size(); i++) fl += (double)Bb.h_n[i] * Bb.h_n[i] * Bb.h_m[i];
+    KTime kt(KC_TRSM, s, fl);
     dim3 g((unsigned)cdiv(Bb.maxm, SW), (unsigned)Bb.count);
     k_trsm<<<g, 256, 0, s>>>(base_L, Lb.off.p, Lb.ld.p, Lb.n.p, base_B, Bb.off.p, Bb.ld.p, Bb.m.p,
                              Bb.count, trans ? 1 : 0);
@@ -716,6 +914,9 @@ void trsm_batched(const double *base_L, const MatBatch &Lb, double *base_B, cons
 void syrk_tn_batched(double *base_C, const MatBatch &Cb, const double *base_W, const MatBatch &Wb,
                      double alpha, bool w_rowmajor, cudaStream_t s) {
     if (Cb.count == 0 || Cb.maxn == 0) return;
+    double fl = 0.0;
+    for (size_t i = 0; i < Cb.h_n.size(); i++) fl += 2.0 * Cb.h_n[i] * Cb.h_n[i] * Wb.h_n[i];
+    KTime kt(KC_SYRK, s, fl);
     int64_t T = cdiv(Cb.maxn, TT);
     dim3 g((unsigned)(T * T), (unsigned)Cb.count);
     k_syrk_tn<<<g, 256, 0, s>>>(base_C, Cb.off.p, Cb.ld.p, Cb.n.p, base_W, Wb.off.p, Wb.ld.p, Wb.n.p,
@@ -736,12 +937,20 @@ void transpose_batched(const double *base_S, const MatBatch &Sb, double *base_D,
 void sytd2_batched(double *base, const MatBatch &Ab, double *d, double *e, double *tau,
                    const int64_t *toff, cudaStream_t s) {
     if (Ab.count == 0) return;
-    // per-matrix symv workspace: reuse the toff layout (n entries per matrix)
+    double fl = 0.0;
+    for (auto v : Ab.h_n) fl += 4.0 / 3.0 * v * v * v;
+    KTime kt(KC_SYTD2, s, fl);
+    const size_t need = 2 * (size_t)std::max(Ab.maxn, 1) * sizeof(double);
+    const bool smem = need <= 200 * 1024;
     DBuf<double> pw;
-    int64_t tot = read1(toff + Ab.count, s);
-    pw.alloc(std::max<int64_t>(tot, 1), s);
-    k_sytd2<<<(unsigned)Ab.count, 512, 0, s>>>(base, Ab.off.p, Ab.ld.p, Ab.n.p, Ab.count, d, e, tau,
-                                               toff, pw.p, toff);
+    if (smem) {
+        CK(cudaFuncSetAttribute(k_sytd2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need));
+    } else {
+        int64_t tot = read1(toff + Ab.count, s);
+        pw.alloc(std::max<int64_t>(2 * tot, 1), s);
+    }
+    k_sytd2<<<(unsigned)Ab.count, 512, smem ? need : 0, s>>>(base, Ab.off.p, Ab.ld.p, Ab.n.p, Ab.count,
+                                                            d, e, tau, toff, pw.p, toff, smem ? 1 : 0);
     CK_LAUNCH();
 }
 
@@ -749,6 +958,7 @@ void stebz_batched(const double *d, const double *e, const int64_t *toff, const 
                    int64_t count, double sigma, int32_t *k, double *w, double *gap,
                    cudaStream_t s) {
     if (count == 0) return;
+    KTime kt(KC_STEBZ, s);
     k_stebz<<<(unsigned)count, 128, 0, s>>>(d, e, toff, n, count, sigma, k, w, gap);
     CK_LAUNCH();
 }
@@ -757,6 +967,7 @@ void stein_batched(const double *d, const double *e, const int64_t *toff, const 
                    const double *w, const int32_t *k, double *base_V, const MatBatch &Vb,
                    double *work, const int64_t *workoff, cudaStream_t s) {
     if (Vb.count == 0) return;
+    KTime kt(KC_STEIN, s);
     k_stein<<<(unsigned)Vb.count, 256, 0, s>>>(d, e, toff, n, Vb.count, w, k, base_V, Vb.off.p,
                                               Vb.ld.p, work, workoff);
     CK_LAUNCH();
@@ -765,6 +976,9 @@ void stein_batched(const double *d, const double *e, const int64_t *toff, const 
 void ormtr_batched(const double *base_A, const MatBatch &Ab, const double *tau, const int64_t *toff,
                    double *base_V, const MatBatch &Vb, cudaStream_t s) {
     if (Vb.count == 0 || Vb.maxm == 0) return;
+    double fl = 0.0;
+    for (size_t i = 0; i < Vb.h_n.size(); i++) fl += 4.0 * Vb.h_n[i] * Vb.h_n[i] * Vb.h_m[i];
+    KTime kt(KC_ORMTR, s, fl);
     dim3 g((unsigned)cdiv(Vb.maxm, 8), (unsigned)Vb.count);
     k_ormtr<<<g, 256, 0, s>>>(base_A, Ab.off.p, Ab.ld.p, Ab.n.p, tau, toff, base_V, Vb.off.p,
                               Vb.ld.p, Vb.m.p, Vb.count);

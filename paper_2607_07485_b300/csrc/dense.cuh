@@ -13,6 +13,7 @@ struct MatBatch {
     DBuf<int32_t> m;    // extra dimension (columns of a right-hand side, K of an update)
     int64_t count = 0;
     int32_t maxn = 0, maxm = 0;
+    std::vector<int32_t> h_n, h_m;  // host copies of the sizes (FLOP accounting)
     void set(const std::vector<int64_t> &o, const std::vector<int32_t> &l,
              const std::vector<int32_t> &nn, const std::vector<int32_t> &mm, cudaStream_t s) {
         count = (int64_t)o.size();
@@ -21,6 +22,8 @@ struct MatBatch {
         upload(n, nn, s);
         std::vector<int32_t> m2 = mm.empty() ? std::vector<int32_t>(o.size(), 0) : mm;
         upload(m, m2, s);
+        h_n = nn;
+        h_m = m2;
         maxn = 0;
         maxm = 0;
         for (auto v : nn) maxn = std::max(maxn, v);
@@ -35,6 +38,17 @@ enum PotrfMode { POTRF_SPD = 0, POTRF_PSD = 1 };
 // n*eps*max(diag) are treated as zero (column zeroed), giving a generalised inverse in the
 // triangular solves below (used for the pseudo-inverse of the interface block).
 void potrf_batched(double *base, const MatBatch &A, PotrfMode mode, int *err, cudaStream_t s);
+
+// Pivoted (rank-revealing) Cholesky of a diagonal block of each view, LAPACK pstrf style:
+// P A_bb P^T = L L^T with diagonal pivoting, stopping when the largest remaining diagonal is
+// <= 10 * eps * max(diag); the trailing pivots are set to zero (generalised inverse in the
+// triangular solves).  The block starts at row/column `b0[i]` of view i and has order bn[i];
+// row and column swaps are applied to the whole view (order nfull[i]) so that the coupling
+// blocks are permuted consistently.  perm receives the pivot order (block-local), rank the
+// numerical rank.
+void pstrf_batched(double *base, const MatBatch &A, const int32_t *b0, const int32_t *bn,
+                   int32_t max_bn, int32_t *perm, const int64_t *permoff, int32_t *rank,
+                   cudaStream_t s);
 
 // X = L^{-1} B (trans = false) or X = L^{-T} B (trans = true), in place on B.
 // L views in Lb (n = order), B views in Bb (n = rows = order, m = columns).

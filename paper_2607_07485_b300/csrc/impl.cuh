@@ -72,6 +72,11 @@ struct Level {
     int32_t nrhs_ws = 0;
     int32_t max_grows_cached = 0;   // largest G_T row count (shared-memory staging size)
     int64_t Omega_total = 0;        // sum of |Omega_i| (Schwarz workspace per right-hand side)
+    // algorithmic bytes per application (index 0: FP32, 1: FP64): Gram SpMV, one colour of the
+    // Schwarz sweep (per colour), the coarsest triangular solves
+    double spmv_bytes[2] = {0, 0};
+    std::vector<double> sweep_bytes[2];
+    double coarse_bytes[2] = {0, 0};
     DBuf<double> b64, x64, r64, ws64;
     DBuf<float> b32, x32, r32, ws32;
 };

@@ -440,6 +440,26 @@ __global__ void __launch_bounds__(256) k_gc(const int32_t *items, int64_t nitems
         }
 }
 
+// compressed coarse factor: G'[r, perm[c]] = L[c, r] (c >= r, r < rank) from a pivoted
+// Cholesky P A_g P^T = L L^T stored column-major in W
+__global__ void k_extract_factor(const double *W, const int64_t *woff, const int64_t *nn,
+                                 const int32_t *perm, const int64_t *permoff, const int32_t *rank,
+                                 const int64_t *goff, int64_t ng, double *G64, float *G32) {
+    int64_t g = blockIdx.y;
+    if (g >= ng) return;
+    const int64_t n = nn[g];
+    const int r = rank[g];
+    const double *L = W + woff[g];
+    const int32_t *pv = perm + permoff[g];
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)r * n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t row = t / n, c = t % n;
+        double v = (c >= row) ? L[c + row * n] : 0.0;
+        G64[goff[g] + row * n + pv[c]] = v;
+        G32[goff[g] + row * n + pv[c]] = (float)v;
+    }
+}
+
 __global__ void k_rowbase(const int64_t *mptr, const int32_t *midx, int64_t ng,
                           const int32_t *grows, int64_t *rowbase) {
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ng;
@@ -508,6 +528,7 @@ void factor_elements(Level &L, int *err, cudaStream_t s) {
     L.G64.alloc(std::max<int64_t>(tot, 1), s);
     L.grows.alloc(std::max<int64_t>(L.ne, 1), s);
     size_t sm = (size_t)mx * mx * sizeof(double);
+    KTime kt(KC_ELEM_FACTOR, s, (double)L.ne * mx * mx * mx / 3.0);
     CK(cudaFuncSetAttribute(k_elem_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     k_elem_factor<<<gridc(L.ne, 1, 148 * 16), 128, sm, s>>>(L.AT.p, L.aoff.p, dnT.p, L.ne, L.G64.p,
                                                           L.goff.p, L.grows.p, err);
@@ -584,10 +605,12 @@ void local_spectral(Level &L, const lsamg_options &o, int *err, cudaStream_t s, 
         gp.alloc(na, s);
         dk.alloc(na, s);
         // 1. assemble At (omega-first) and A_ww
+        { LSAMG_PROF("ls: assemble", s);
+        KTime kt(KC_ASSEMBLE, s);
         k_assemble_gep<<<(unsigned)na, 256, maxE * sizeof(int32_t), s>>>(
             a0, na, L.aeptr.p, L.aeidx.p, L.eptr.p, L.eidx.p, L.AT.p, L.aoff.p, L.mult.p, L.Optr.p,
             L.Oidx.p, L.Olpos.p, L.wptr.p, At.p, datoff.p, Aww.p, dawoff.p);
-        CK_LAUNCH();
+        CK_LAUNCH(); }
         // 2. Schur complement S = At_ww - At_wG At_GG^+ At_Gw via a semidefinite Cholesky of At_GG
         MatBatch bGG, bGw, bww, bW, bAww, bV, bC, bY;
         {
@@ -613,17 +636,41 @@ void local_spectral(Level &L, const lsamg_options &o, int *err, cudaStream_t s, 
             bY.set(o3, l1, nwv, nwv, s);
             bC.set(o5, nwv, nwv, nwv, s);
         }
-        potrf_batched(At.p, bGG, POTRF_PSD, err, s);
+        { LSAMG_PROF("ls: schur", s);
+        {
+            // rank-revealing pivoted Cholesky of At_GG (the pseudo-inverse in eq. 2.9); row and
+            // column swaps run over the whole At so At_wG / At_Gw are permuted consistently
+            MatBatch bAt;
+            std::vector<int64_t> oall(na), poff(na + 1, 0);
+            for (int64_t i = 0; i < na; i++) {
+                oall[i] = atoff[i];
+                poff[i + 1] = poff[i] + nGv[i];
+            }
+            bAt.set(oall, nOv, nOv, {}, s);
+            DBuf<int32_t> db0, dbn, perm, rank;
+            DBuf<int64_t> dpoff;
+            upload(db0, nwv, s);
+            upload(dbn, nGv, s);
+            upload(dpoff, poff, s);
+            perm.alloc(std::max<int64_t>(poff[na], 1), s);
+            rank.alloc(na, s);
+            int32_t maxG = 0;
+            for (auto g : nGv) maxG = std::max(maxG, g);
+            pstrf_batched(At.p, bAt, db0.p, dbn.p, maxG, perm.p, dpoff.p, rank.p, s);
+        }
         trsm_batched(At.p, bGG, At.p, bGw, false, s);                 // W = L_G^{-1} At_Gw
         syrk_tn_batched(At.p, bww, At.p, bW, -1.0, false, s);          // S = At_ww - W^T W
+        }
+        { LSAMG_PROF("ls: gep transform", s);
         // 3. GEP S y = mu A_ww y -> C = L^{-1} S L^{-T}
         potrf_batched(Aww.p, bAww, POTRF_SPD, err, s);
         trsm_batched(Aww.p, bAww, At.p, bY, false, s);                // Y = L^{-1} S
         transpose_batched(At.p, bww, C.p, bC, s);                     // C = Y^T
         trsm_batched(Aww.p, bAww, C.p, bC, false, s);                 // C = L^{-1} S L^{-T}
+        }
         // 4. tridiagonalise, count and bisect the eigenvalues below 1/tau_cut
-        sytd2_batched(C.p, bC, dv.p, ev.p, tv.p, dtoff.p, s);
-        stebz_batched(dv.p, ev.p, dtoff.p, bC.n.p, na, sigma, dk.p, wv.p, gp.p, s);
+        { LSAMG_PROF("ls: sytd2", s); sytd2_batched(C.p, bC, dv.p, ev.p, tv.p, dtoff.p, s); }
+        { LSAMG_PROF("ls: stebz", s); stebz_batched(dv.p, ev.p, dtoff.p, bC.n.p, na, sigma, dk.p, wv.p, gp.p, s); }
         auto hk = to_host(dk.p, na, s);
         auto hg = to_host(gp.p, na, s);
         check_err(err, s, "local spectral problems (factorisations)");
@@ -633,7 +680,7 @@ void local_spectral(Level &L, const lsamg_options &o, int *err, cudaStream_t s, 
             L.h_k[a0 + i] = hk[i];
             L.h_gap[a0 + i] = hg[i];
             voff[i + 1] = voff[i] + (int64_t)nwv[i] * hk[i];
-            wkoff[i + 1] = wkoff[i] + 6 * (int64_t)nwv[i];
+            wkoff[i + 1] = wkoff[i] + 4 * 64 * (int64_t)nwv[i];  // inverse-iteration scratch
             *flops += 4.0 * nwv[i] * (double)nwv[i] * hk[i] + (double)nwv[i] * nwv[i] * hk[i];
         }
         Chunk ch;
@@ -651,9 +698,9 @@ void local_spectral(Level &L, const lsamg_options &o, int *err, cudaStream_t s, 
             bV.set(o, nwv, nwv, hk, s);
         }
         // 5. eigenvectors: inverse iteration, back-transformation, Z = L^{-T} V
-        stein_batched(dv.p, ev.p, dtoff.p, bC.n.p, wv.p, dk.p, ch.V.p, bV, work.p, dwk.p, s);
-        ormtr_batched(C.p, bC, tv.p, dtoff.p, ch.V.p, bV, s);
-        trsm_batched(Aww.p, bAww, ch.V.p, bV, true, s);
+        { LSAMG_PROF("ls: stein", s); stein_batched(dv.p, ev.p, dtoff.p, bC.n.p, wv.p, dk.p, ch.V.p, bV, work.p, dwk.p, s); }
+        { LSAMG_PROF("ls: ormtr", s); ormtr_batched(C.p, bC, tv.p, dtoff.p, ch.V.p, bV, s); }
+        { LSAMG_PROF("ls: trsm Z", s); trsm_batched(Aww.p, bAww, ch.V.p, bV, true, s); }
         CK(cudaStreamSynchronize(s));
         check_err(err, s, "local spectral problems");
         chunks.push_back(std::move(ch));
@@ -784,10 +831,11 @@ void build_coarse(Level &F, Level &C, int *err, cudaStream_t s, double *flops) {
         maxc = std::max<int32_t>(maxc, (int32_t)hcols[g]);
     }
     C.max_nT = maxc;
-    upload(C.goff, cgoff, s);
+    DBuf<double> Gst;  // stacked G_c,T = G_T (R_T P) of the members (Section 2: G_c = G P)
+    DBuf<int64_t> dgst;
+    upload(dgst, cgoff, s);
     upload(C.aoff, caoff, s);
-    upload(C.grows, crows, s);
-    C.G64.alloc(std::max<int64_t>(cgoff[ng], 1), s);
+    Gst.alloc(std::max<int64_t>(cgoff[ng], 1), s);
     DBuf<int64_t> rowbase, dcgoff;
     rowbase.alloc(std::max<int64_t>(ne, 1), s);
     k_rowbase<<<gridc(ng), 256, 0, s>>>(mptr.p, midx.p, ng, F.grows.p, rowbase.p);
@@ -814,16 +862,14 @@ void build_coarse(Level &F, Level &C, int *err, cudaStream_t s, double *flops) {
         upload(ditems, items, s);
         int64_t nit = (int64_t)items.size() / 3;
         if (nit > 0) {
+            KTime kt(KC_COARSE_GRAM, s);
             k_gc<<<(unsigned)nit, 256, 0, s>>>(ditems.p, nit, F.eptr.p, F.eidx.p, F.G64.p, F.goff.p,
                                                 F.grows.p, F.eaptr.p, F.eaidx.p, F.agg.p, F.posw.p,
-                                                F.k.p, F.Z64.p, F.zoff.p, F.cgroup.p, C.goff.p,
-                                                gcols.p, rowbase.p, C.G64.p);
+                                                F.k.p, F.Z64.p, F.zoff.p, F.cgroup.p, dgst.p,
+                                                gcols.p, rowbase.p, Gst.p);
             CK_LAUNCH();
         }
     }
-    C.G32.alloc(std::max<int64_t>(cgoff[ng], 1), s);
-    k_to_f32<<<gridc(cgoff[ng]), 256, 0, s>>>(C.G64.p, C.G32.p, cgoff[ng]);
-    CK_LAUNCH();
     // A_g = G_g^T G_g (setup of the next level works on element blocks)
     C.AT.alloc(std::max<int64_t>(caoff[ng], 1), s);
     C.AT.zero(s);
@@ -841,13 +887,58 @@ void build_coarse(Level &F, Level &C, int *err, cudaStream_t s, double *flops) {
         }
         bA.set(oa, nn, nn, {}, s);
         bG.set(og, ldg, kk, nn, s);
-        syrk_tn_batched(C.AT.p, bA, C.G64.p, bG, 1.0, true, s);
+        syrk_tn_batched(C.AT.p, bA, Gst.p, bG, 1.0, true, s);
         DBuf<int64_t> dn;
         std::vector<int64_t> n64(hcols.begin(), hcols.end());
         upload(dn, n64, s);
         dim3 gsym(64, (unsigned)std::max<int64_t>(ng, 1));
         if (ng > 0) {
             k_symmetrize_sq<<<gsym, 256, 0, s>>>(C.AT.p, C.aoff.p, dn.p, ng);
+            CK_LAUNCH();
+        }
+        // Remark 5.2: the coarse element's Gram rows are replaced by a rank-revealing factor of
+        // A_g (rank <= min(stacked rows, columns)); G'^T G' = A_g up to the truncation of
+        // numerically zero pivots, so the coarse operator is unchanged
+        DBuf<double> Wf;
+        Wf.alloc(std::max<int64_t>(caoff[ng], 1), s);
+        CK(cudaMemcpyAsync(Wf.p, C.AT.p, caoff[ng] * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        MatBatch bW;
+        std::vector<int32_t> zero(ng, 0);
+        bW.set(oa, nn, nn, {}, s);
+        std::vector<int64_t> poff(ng + 1, 0);
+        int32_t maxn = 0;
+        for (int64_t g = 0; g < ng; g++) {
+            poff[g + 1] = poff[g] + hcols[g];
+            maxn = std::max<int32_t>(maxn, (int32_t)hcols[g]);
+            *flops += (double)hcols[g] * hcols[g] * hcols[g] / 3.0;
+        }
+        DBuf<int32_t> db0, dbn, perm, rank;
+        DBuf<int64_t> dpoff;
+        upload(db0, zero, s);
+        upload(dbn, nn, s);
+        upload(dpoff, poff, s);
+        perm.alloc(std::max<int64_t>(poff[ng], 1), s);
+        rank.alloc(std::max<int64_t>(ng, 1), s);
+        pstrf_batched(Wf.p, bW, db0.p, dbn.p, maxn, perm.p, dpoff.p, rank.p, s);
+        auto hr = to_host(rank.p, ng, s);
+        std::vector<int64_t> ngoff(ng + 1, 0);
+        std::vector<int32_t> nrows(ng);
+        for (int64_t g = 0; g < ng; g++) {
+            nrows[g] = std::min<int32_t>(hr[g], (int32_t)hrows[g]);
+            if (hr[g] > hrows[g]) nrows[g] = hr[g];  // rank cannot exceed stacked rows in exact arithmetic
+            ngoff[g + 1] = ngoff[g] + (int64_t)hr[g] * hcols[g];
+            nrows[g] = hr[g];
+        }
+        upload(C.goff, ngoff, s);
+        upload(C.grows, nrows, s);
+        C.G64.alloc(std::max<int64_t>(ngoff[ng], 1), s);
+        C.G32.alloc(std::max<int64_t>(ngoff[ng], 1), s);
+        C.G64.zero(s);
+        C.G32.zero(s);
+        dim3 gx(64, (unsigned)std::max<int64_t>(ng, 1));
+        if (ng > 0) {
+            k_extract_factor<<<gx, 256, 0, s>>>(Wf.p, C.aoff.p, dn.p, perm.p, dpoff.p, rank.p, C.goff.p,
+                                                 ng, C.G64.p, C.G32.p);
             CK_LAUNCH();
         }
     }
@@ -890,6 +981,7 @@ void smoother_setup(Level &L, const lsamg_options &o, int *err, cudaStream_t s, 
         upload(dmo, mo, s);
         upload(dpo, po, s);
         upload(dnn, nn, s);
+        KTime kta(KC_ASSEMBLE, s);
         k_assemble_smoother<<<(unsigned)na, 256, 0, s>>>(a0, na, L.oeptr.p, L.oeidx.p, L.eptr.p,
                                                           L.AT.p, L.aoff.p, L.oelocoff.p, L.oeloc.p,
                                                           L.Optr.p, AO.p, dmo.p);

@@ -44,7 +44,8 @@ class Options(C.Structure):
     _fields_ = [("tau_c", C.c_double), ("agg_passes", C.c_int32), ("agg_passes_coarse", C.c_int32),
                 ("max_levels", C.c_int32), ("min_coarse", C.c_int32), ("max_density", C.c_double),
                 ("vcycle_fp32", C.c_int32), ("maxit", C.c_int32), ("rtol", C.c_double),
-                ("chunk_bytes", C.c_int64), ("use_graph", C.c_int32), ("verbose", C.c_int32)]
+                ("chunk_bytes", C.c_int64), ("use_graph", C.c_int32), ("verbose", C.c_int32),
+                ("profile", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -71,10 +72,33 @@ _lib.lsamg_stage_name.argtypes = [C.c_int32]
 _lib.lsamg_query.argtypes = [_H, C.c_int32, C.c_int32, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]
 _lib.lsamg_destroy.argtypes = [_H]
 _lib.lsamg_last_error.restype = C.c_char_p
+_lib.lsamg_kernel_classes.restype = C.c_int32
+_lib.lsamg_kernel_name.restype = C.c_char_p
+_lib.lsamg_kernel_name.argtypes = [C.c_int32]
+_lib.lsamg_kernel_stats_all.argtypes = [C.c_void_p]
+_lib.lsamg_launch_count.restype = C.c_int64
 
 EXPORTS = ["lsamg_options_default", "lsamg_setup", "lsamg_apply", "lsamg_solve", "lsamg_solve_host",
            "lsamg_gram_spmv", "lsamg_elem_grad", "lsamg_get_stats", "lsamg_stage_name", "lsamg_query",
-           "lsamg_destroy", "lsamg_last_error"]
+           "lsamg_destroy", "lsamg_last_error", "lsamg_kernel_classes", "lsamg_kernel_name",
+           "lsamg_kernel_stats_all", "lsamg_launch_count"]
+
+
+def kernel_stats():
+    """Per-kernel-class device time since the previous call (needs the profile option)."""
+    k = _lib.lsamg_kernel_classes()
+    buf = np.zeros(4 * k, np.float64)
+    _check(_lib.lsamg_kernel_stats_all(buf.ctypes.data))
+    out = {}
+    for c in range(k):
+        ms, calls, fl, by = buf[4 * c:4 * c + 4]
+        if calls:
+            out[_lib.lsamg_kernel_name(c).decode()] = dict(ms=ms, calls=int(calls), flops=fl, bytes=by)
+    return out
+
+
+def launch_count():
+    return int(_lib.lsamg_launch_count())
 
 
 def _check(rc, allow=()):

@@ -357,10 +357,9 @@ def test_error_codes_on_bad_input():
 @pytest.mark.parametrize("name", ["rt1_beta1", "cfg1", "cfg3_16", "cfg4_6"])
 def test_local_eigenpairs_self_consistent(name):
     """Each level's local problems rebuilt in NumPy from the library's own data (element maps,
-    element Gram blocks, aggregates, overlaps, multiplicities) and solved by an independent
-    Cholesky + eigh route: the library's Z must span the same subspaces (same coordinates, so
+    element Gram blocks, aggregates, overlaps, multiplicities) and solved by the oracle's
+    least-squares route: the library's Z must span the same subspaces (same coordinates, so
     no basis freedom beyond degenerate eigenspaces)."""
-    import scipy.linalg as sla
     p, H, amg, ptol, _, _ = case(name)
     st = amg.stats()
     for l in range(st["n_levels"] - 1):
@@ -371,10 +370,6 @@ def test_local_eigenpairs_self_consistent(name):
         kg, zoff, Z = amg.query(l, "K"), amg.query(l, "ZOFF"), amg.query(l, "Z")
         tau = st["tau"][l]
         elems = [eidx[eptr[e]:eptr[e + 1]] for e in range(len(eptr) - 1)]
-        mats = []
-        for e, d in enumerate(elems):
-            Ge = G[goff[e]:goff[e] + grows[e] * len(d)].reshape(grows[e], len(d))
-            mats.append(Ge.T @ Ge)
         nagg = len(kg)
         ael = [[] for _ in range(nagg)]
         for t, d in enumerate(elems):
@@ -382,22 +377,17 @@ def test_local_eigenpairs_self_consistent(name):
                 ael[a].append(t)
         omega = [np.flatnonzero(agg == a) for a in range(nagg)]
         Omega = [oidx[optr[a]:optr[a + 1]] for a in range(nagg)]
+        Gs = []
+        for e, d in enumerate(elems):
+            Gs.append(G[goff[e]:goff[e] + grows[e] * len(d)].reshape(grows[e], len(d)))
         worst = 0.0
         for a in range(nagg):
-            At, Aww, _ = OL.local_blocks(a, elems, mats, mult, ael, omega, Omega)
-            nw = Aww.shape[0]
-            GG = At[nw:, nw:]
-            if GG.shape[0]:
-                S = At[:nw, :nw] - At[:nw, nw:] @ sla.cho_solve(sla.cho_factor(GG), At[nw:, :nw])
-            else:
-                S = At[:nw, :nw]
-            Lw = np.linalg.cholesky(Aww)
-            C = sla.solve_triangular(Lw, sla.solve_triangular(Lw, S, lower=True).T, lower=True)
-            mu, V = np.linalg.eigh(0.5 * (C + C.T))
-            keep = mu * tau < 1 - OL.TIE
-            Zr = sla.solve_triangular(Lw.T, V[:, keep], lower=False)
+            Hm, F, _ = OL.local_gram_rows(a, elems, Gs, mult, ael, omega, Omega)
+            nw = len(omega[a])
+            Zr, mu, _ = OL.local_problem(Hm, F, nw, tau)
             assert Zr.shape[1] == kg[a], f"level {l} aggregate {a}: k {kg[a]} vs {Zr.shape[1]}"
             Zg = Z[zoff[a]:zoff[a + 1]].reshape(nw, kg[a])
+            Aww = F.T @ F
             np.testing.assert_allclose(Zg.T @ Aww @ Zg, np.eye(kg[a]), atol=1e-6,
                                        err_msg=f"level {l} aggregate {a}: Z not A_ww-orthonormal")
             worst = max(worst, np.linalg.norm(_projector(Zg) - _projector(Zr), 2))

@@ -386,13 +386,19 @@ def test_P_disjoint_support_and_galerkin(cfg1):
     Ac = (L0.P.T @ L0.A @ L0.P).toarray()
     A1 = L1.A.toarray()
     np.testing.assert_allclose(A1, Ac, atol=1e-12 * abs(Ac).max())
-    for cm, Ag, Gg in zip(L1.elems, L1.mats, L1.G):
-        np.testing.assert_allclose(Gg.T @ Gg, Ag, atol=1e-12 * abs(Ag).max())
+    # coarse Gram rows: the members' rows of G_c = G P stacked (checked below with the
+    # rounding scale of each product)
     # G_c = G P on the unmerged elements, merged per group
     for gi, grp in enumerate(L0.cgroups):
         cm = L1.elems[gi]
         acc = np.zeros((len(cm), len(cm)))
         scale = 0.0
+        for t in grp:
+            RTP = L0.P[L0.elems[t]][:, cm].toarray()
+            Gc = L0.G[t] @ RTP
+            acc += Gc.T @ Gc
+        np.testing.assert_allclose(L1.G[gi].T @ L1.G[gi], acc, rtol=0, atol=1e-13 * abs(acc).max() + 1e-300)
+        acc = np.zeros_like(acc)
         for t in grp:
             RTP = L0.P[L0.elems[t]][:, cm].toarray()
             Gc = L0.G[t] @ RTP
