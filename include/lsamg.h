@@ -79,6 +79,8 @@ typedef struct {
     int32_t use_graph;           /* 1: capture the V-cycle as a CUDA graph */
     int32_t verbose;
     int32_t profile;             /* 1: time every kernel class with CUDA events on the stream */
+    int32_t large_dense;         /* local problems above this order use multi-CTA kernels (0 = 2048) */
+    int32_t split_sweep;         /* Schwarz colours with larger overlaps use the split sweep (0 = 4096) */
 } lsamg_options;
 
 lsamg_options lsamg_options_default(void);

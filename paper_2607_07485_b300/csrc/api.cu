@@ -9,6 +9,7 @@
 #include "impl.cuh"
 
 namespace lsamg {
+extern int g_prof_level;
 
 namespace {
 
@@ -107,6 +108,23 @@ void finish_level_info(Level &L, cudaStream_t s) {
         auto oei = to_host(L.oeidx.p, oep[L.nagg], s);
         auto cag = to_host(L.colagg.p, L.nagg, s);
         for (int t = 0; t < 2; t++) L.sweep_bytes[t].assign(L.ncol, 0.0);
+        L.colmax.assign(L.ncol, 0);
+        L.colpairs.assign(L.ncol + 1, 0);
+        std::vector<int32_t> pa;
+        std::vector<int64_t> pe;
+        for (int c = 0; c < L.ncol; c++) {
+            for (int64_t q = L.colptr[c]; q < L.colptr[c + 1]; q++) {
+                const int32_t a = cag[q];
+                L.colmax[c] = std::max(L.colmax[c], L.h_nO[a]);
+                for (int64_t j = oep[a]; j < oep[a + 1]; j++) {
+                    pa.push_back(a);
+                    pe.push_back(j);
+                }
+            }
+            L.colpairs[c + 1] = (int64_t)pa.size();
+        }
+        upload(L.pair_agg, pa, s);
+        upload(L.pair_ent, pe, s);
         for (int c = 0; c < L.ncol; c++)
             for (int64_t q = L.colptr[c]; q < L.colptr[c + 1]; q++) {
                 const int32_t a = cag[q];
@@ -210,6 +228,7 @@ void do_setup(Handle &H, const lsamg_problem *P, const lsamg_options &o) {
             st.stage_seconds[2] += now() - t;
             t = now();
             trace("level %d: local spectral", l);
+            g_prof_level = l;
             if (L.nagg <= 1) {
                 // one aggregate: Gamma is empty and mult = 1, so S = A_ww and every mu = 1; the
                 // cut keeps all modes (tau_cut < 1) or none (tau_cut >= 1) -- either way the level
@@ -238,7 +257,14 @@ void do_setup(Handle &H, const lsamg_problem *P, const lsamg_options &o) {
         trace("level %d: smoother", l);
         st.stage_seconds[4] += now() - t;
         t = now();
-        { LSAMG_PROF("setup: smoother factors", s); smoother_setup(L, o, err, s, &flops); }
+        {
+            static const char *nm[8] = {"L0 setup: smoother factors", "L1 setup: smoother factors",
+                                        "L2 setup: smoother factors", "L3 setup: smoother factors",
+                                        "L4 setup: smoother factors", "L5 setup: smoother factors",
+                                        "L6 setup: smoother factors", "L7 setup: smoother factors"};
+            LSAMG_PROF(nm[l & 7], s);
+            smoother_setup(L, o, err, s, &flops);
+        }
         st.stage_seconds[5] += now() - t;
         t = now();
         H.levels.emplace_back();
@@ -447,6 +473,8 @@ lsamg_options lsamg_options_default(void) {
     o.use_graph = 0;
     o.verbose = 0;
     o.profile = 0;
+    o.large_dense = 0;
+    o.split_sweep = 0;
     return o;
 }
 
@@ -476,6 +504,8 @@ int lsamg_setup(const lsamg_problem *prob, const lsamg_options *opts, void *stre
     h->h.stream = (cudaStream_t)stream;
     h->h.opt = opts ? *opts : lsamg_options_default();
     ktimer_enable(h->h.opt.profile != 0);
+    g_large_dense = h->h.opt.large_dense > 0 ? h->h.opt.large_dense : 2048;
+    g_split_sweep = h->h.opt.split_sweep > 0 ? h->h.opt.split_sweep : 4096;
     int rc = guarded([&] { do_setup(h->h, prob, h->h.opt); });
     if (rc != LSAMG_OK) {
         std::string msg = g_last_error;
@@ -494,6 +524,7 @@ int lsamg_apply(lsamg_handle *h, const double *r, double *z, int32_t nrhs, int32
     return guarded([&] {
         Handle &H = h->h;
         H.stream = (cudaStream_t)stream;
+        g_split_sweep = H.opt.split_sweep > 0 ? H.opt.split_sweep : 4096;
         ensure_solve_ws(H, nrhs);
         bool f = fp32 < 0 ? H.opt.vcycle_fp32 != 0 : fp32 != 0;
         precondition(H, r, z, nrhs, f);
@@ -508,6 +539,7 @@ int lsamg_solve(lsamg_handle *h, const double *b, double *x, int32_t nrhs, int32
     int rc = guarded([&] {
         Handle &H = h->h;
         H.stream = (cudaStream_t)stream;
+        g_split_sweep = H.opt.split_sweep > 0 ? H.opt.split_sweep : 4096;
         status = do_solve(H, b, x, nrhs, mode, use_x0 != 0, iters, relres);
     });
     if (rc != LSAMG_OK) return rc;

@@ -7,6 +7,9 @@
 
 namespace lsamg {
 
+int g_large_dense = 2048;
+int g_split_sweep = 4096;
+
 static int64_t g_launches = 0;
 void count_launch() { g_launches++; }
 int64_t launch_count() { return g_launches; }

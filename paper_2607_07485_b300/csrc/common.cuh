@@ -212,4 +212,8 @@ int64_t sum_i64(const int64_t *d, int64_t n, cudaStream_t s);
 
 constexpr int SEG_SMEM_MAX = 56 * 1024;  // max int32 entries of one segment sorted in smem
 
+// size thresholds between one-CTA-per-matrix and multi-CTA kernels (set from the options)
+extern int g_large_dense;
+extern int g_split_sweep;
+
 }  // namespace lsamg

@@ -213,7 +213,7 @@ __global__ void k_interp(const int64_t *wptr, const int32_t *widx, const int32_t
 }
 
 // ---------------------------------------------------------------- blocked coarsest solve
-constexpr int CB = 256;  // rows per block of the multi-CTA triangular solves
+constexpr int CB = 256;            // rows per block of the multi-CTA triangular solves
 
 // forward solve of the diagonal block rows [r0, r1) of L y = v (columns < r0 already applied)
 template <class T>
@@ -300,6 +300,190 @@ __global__ void __launch_bounds__(256) k_cs_bwd_update(const T *L, int r0, int r
         T sacc = 0;
         for (int i = r0; i < r1; i++) sacc += L[(int64_t)i * (i + 1) / 2 + j] * vr[i];
         vr[j] -= sacc;
+    }
+}
+
+// ---------------------------------------------------------------- split Schwarz sweep (large subdomains)
+// gather: ws[sub] = res[Omega_a]
+template <class T>
+__global__ void k_sw_gather(const int32_t *aggs, const int64_t *Optr, const int32_t *Oidx, const T *res,
+                            T *ws, int64_t n, int64_t wsn, int nrhs) {
+    const int32_t a = aggs[blockIdx.y];
+    const int64_t ob = Optr[a], nO = Optr[a + 1] - ob;
+    for (int r = 0; r < nrhs; r++)
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nO; i += (int64_t)gridDim.x * blockDim.x)
+            ws[(int64_t)r * wsn + ob + i] = res[(int64_t)r * n + Oidx[ob + i]];
+}
+
+// x[Omega_a] += ws[sub]
+template <class T>
+__global__ void k_sw_addx(const int32_t *aggs, const int64_t *Optr, const int32_t *Oidx, const T *ws, T *x,
+                          int64_t n, int64_t wsn, int nrhs) {
+    const int32_t a = aggs[blockIdx.y];
+    const int64_t ob = Optr[a], nO = Optr[a + 1] - ob;
+    for (int r = 0; r < nrhs; r++)
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nO; i += (int64_t)gridDim.x * blockDim.x)
+            x[(int64_t)r * n + Oidx[ob + i]] += ws[(int64_t)r * wsn + ob + i];
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_sw_fwd_diag(const int32_t *aggs, const int64_t *Optr, const T *Lp,
+                                                     const int64_t *Loff, int r0, T *ws, int64_t wsn, int nrhs) {
+    __shared__ T red[32];
+    const int32_t a = aggs[blockIdx.x];
+    const int n = (int)(Optr[a + 1] - Optr[a]);
+    if (r0 >= n) return;
+    const int r1 = min(n, r0 + CB);
+    const T *L = Lp + Loff[a];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    for (int r = 0; r < nrhs; r++) {
+        T *vr = ws + (int64_t)r * wsn + Optr[a];
+        for (int b0 = r0; b0 < r1; b0 += 32) {
+            const int rs = min(32, r1 - b0);
+            for (int i = warp; i < rs; i += nwarp) {
+                const T *row = L + (int64_t)(b0 + i) * (b0 + i + 1) / 2;
+                T sacc = 0;
+                for (int j = r0 + lane; j < b0; j += 32) sacc += row[j] * vr[j];
+                sacc = warp_sum(sacc);
+                if (lane == 0) red[i] = vr[b0 + i] - sacc;
+            }
+            __syncthreads();
+            if (warp == 0) {
+                T yl = 0;
+                for (int i = 0; i < rs; i++) {
+                    const T *row = L + (int64_t)(b0 + i) * (b0 + i + 1) / 2 + b0;
+                    T c = (lane < i) ? row[lane] * yl : (T)0;
+                    c = warp_sum(c);
+                    T yi = (red[i] - c) / row[i];
+                    if (lane == i) yl = yi;
+                }
+                if (lane < rs) vr[b0 + lane] = yl;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_sw_fwd_update(const int32_t *aggs, const int64_t *Optr, const T *Lp,
+                                                       const int64_t *Loff, int r0, T *ws, int64_t wsn, int nrhs) {
+    const int32_t a = aggs[blockIdx.y];
+    const int n = (int)(Optr[a + 1] - Optr[a]);
+    const int r1 = min(n, r0 + CB);
+    if (r1 >= n) return;
+    const T *L = Lp + Loff[a];
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int r = 0; r < nrhs; r++) {
+        T *vr = ws + (int64_t)r * wsn + Optr[a];
+        for (int64_t i = r1 + wid; i < n; i += nw) {
+            const T *row = L + i * (i + 1) / 2;
+            T sacc = 0;
+            for (int j = r0 + lane; j < r1; j += 32) sacc += row[j] * vr[j];
+            sacc = warp_sum(sacc);
+            if (lane == 0) vr[i] -= sacc;
+        }
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_sw_bwd_diag(const int32_t *aggs, const int64_t *Optr, const T *Lp,
+                                                     const int64_t *Loff, int r1g, T *ws, int64_t wsn, int nrhs) {
+    const int32_t a = aggs[blockIdx.x];
+    const int n = (int)(Optr[a + 1] - Optr[a]);
+    // aligned block [r1g - CB, r1g) clipped to this subdomain
+    const int r0 = max(0, r1g - CB);
+    if (r0 >= n) return;
+    const int r1 = min(r1g, n);
+    const T *L = Lp + Loff[a];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int r = 0; r < nrhs; r++) {
+        T *vr = ws + (int64_t)r * wsn + Optr[a];
+        const int nb = (r1 - r0 + 31) / 32;
+        for (int bi = nb - 1; bi >= 0; bi--) {
+            const int b0 = r0 + bi * 32, rs = min(32, r1 - b0);
+            if (warp == 0) {
+                T xl = (lane < rs) ? vr[b0 + lane] : (T)0;
+                for (int i = rs - 1; i >= 0; i--) {
+                    const T *row = L + (int64_t)(b0 + i) * (b0 + i + 1) / 2 + b0;
+                    T xi = __shfl_sync(0xffffffffu, xl, i) / row[i];
+                    if (lane == i) xl = xi;
+                    if (lane < i) xl -= row[lane] * xi;
+                }
+                if (lane < rs) vr[b0 + lane] = xl;
+            }
+            __syncthreads();
+            for (int j = r0 + threadIdx.x; j < b0; j += blockDim.x) {
+                T sacc = 0;
+                for (int i = 0; i < rs; i++) sacc += L[(int64_t)(b0 + i) * (b0 + i + 1) / 2 + j] * vr[b0 + i];
+                vr[j] -= sacc;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_sw_bwd_update(const int32_t *aggs, const int64_t *Optr, const T *Lp,
+                                                       const int64_t *Loff, int r1g, T *ws, int64_t wsn, int nrhs) {
+    const int32_t a = aggs[blockIdx.y];
+    const int n = (int)(Optr[a + 1] - Optr[a]);
+    const int r0 = max(0, r1g - CB);
+    if (r0 >= n) return;
+    const int r1 = min(r1g, n);
+    const T *L = Lp + Loff[a];
+    for (int r = 0; r < nrhs; r++) {
+        T *vr = ws + (int64_t)r * wsn + Optr[a];
+        for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < r0; j += (int64_t)gridDim.x * blockDim.x) {
+            T sacc = 0;
+            for (int i = r0; i < r1; i++) sacc += L[(int64_t)i * (i + 1) / 2 + j] * vr[i];
+            vr[j] -= sacc;
+        }
+    }
+}
+
+// residual update res -= G_T^T G_T delta_T, one CTA per (subdomain, element meeting Omega) pair
+template <class T>
+__global__ void __launch_bounds__(128) k_sw_scatter(const int32_t *pa, const int64_t *pj, int64_t npairs,
+                                                    const int64_t *Optr, const int64_t *locoff,
+                                                    const int32_t *loc, const int32_t *oeidx,
+                                                    const int64_t *eptr, const int32_t *eidx, const T *G,
+                                                    const int64_t *goff, const int32_t *grows, const T *ws,
+                                                    T *res, int64_t n, int64_t wsn, int nrhs) {
+    extern __shared__ unsigned char smraw[];
+    T *t = reinterpret_cast<T *>(smraw);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    for (int64_t q = blockIdx.x; q < npairs; q += gridDim.x) {
+        const int32_t a = pa[q];
+        const int64_t j = pj[q];
+        const int32_t e = oeidx[j];
+        const int64_t b = eptr[e];
+        const int nT = (int)(eptr[e + 1] - b);
+        const int m = grows[e];
+        const T *g = G + goff[e];
+        const int32_t *lc = loc + locoff[j];
+        for (int r = 0; r < nrhs; r++) {
+            const T *v = ws + (int64_t)r * wsn + Optr[a];
+            T *rr = res + (int64_t)r * n;
+            for (int row = warp; row < m; row += nwarp) {
+                const T *gr = g + (int64_t)row * nT;
+                T sacc = 0;
+                for (int c = lane; c < nT; c += 32) {
+                    const int p = lc[c];
+                    if (p >= 0) sacc += gr[c] * v[p];
+                }
+                sacc = warp_sum(sacc);
+                if (lane == 0) t[row] = sacc;
+            }
+            __syncthreads();
+            for (int c = threadIdx.x; c < nT; c += blockDim.x) {
+                T sacc = 0;
+                for (int row = 0; row < m; row++) sacc += g[(int64_t)row * nT + c] * t[row];
+                atomicAdd(&rr[eidx[b + c]], -sacc);
+            }
+            __syncthreads();
+        }
     }
 }
 
@@ -446,9 +630,67 @@ static T *wsvec(Level &L) {
 }
 
 template <class T>
+static void sweep_split(Level &L, int c, int nrhs, cudaStream_t s) {
+    const int64_t na = L.colptr[c + 1] - L.colptr[c];
+    const int32_t *aggs = L.colagg.p + L.colptr[c];
+    const T *Lp;
+    const T *G;
+    if constexpr (std::is_same<T, float>::value) {
+        Lp = L.L32.p;
+        G = L.G32.p;
+    } else {
+        Lp = L.L64.p;
+        G = L.G64.p;
+    }
+    T *ws = wsvec<T>(L);
+    const int maxn = L.colmax[c];
+    dim3 gg((unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv(maxn, 256), 64)), (unsigned)na);
+    k_sw_gather<T><<<gg, 256, 0, s>>>(aggs, L.Optr.p, L.Oidx.p, rvec<T>(L), ws, L.n, L.Omega_total, nrhs);
+    CK_LAUNCH();
+    for (int r0 = 0; r0 < maxn; r0 += CB) {
+        k_sw_fwd_diag<T><<<(unsigned)na, 256, 0, s>>>(aggs, L.Optr.p, Lp, L.Loff.p, r0, ws, L.Omega_total, nrhs);
+        CK_LAUNCH();
+        if (r0 + CB < maxn) {
+            dim3 g((unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv((int64_t)(maxn - r0 - CB) * 32, 256), 256)), (unsigned)na);
+            k_sw_fwd_update<T><<<g, 256, 0, s>>>(aggs, L.Optr.p, Lp, L.Loff.p, r0, ws, L.Omega_total, nrhs);
+            CK_LAUNCH();
+        }
+    }
+    // backward: every subdomain walks its own blocks from its end; blocks are aligned to the
+    // forward partition (multiples of CB from the start), so r1 runs over CB-multiples and the
+    // subdomain's own n
+    std::vector<int> ends;
+    for (int r1 = ((maxn + CB - 1) / CB) * CB; r1 > 0; r1 -= CB) ends.push_back(r1);
+    for (int r1 : ends) {
+        // subdomains whose size is not a multiple of CB treat their last partial block when
+        // r1 is the first CB-multiple >= n: pass r1 and let each use min(r1, n)
+        k_sw_bwd_diag<T><<<(unsigned)na, 256, 0, s>>>(aggs, L.Optr.p, Lp, L.Loff.p, r1, ws, L.Omega_total, nrhs);
+        CK_LAUNCH();
+        dim3 g((unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv(std::max(r1 - CB, 1), 256), 256)), (unsigned)na);
+        k_sw_bwd_update<T><<<g, 256, 0, s>>>(aggs, L.Optr.p, Lp, L.Loff.p, r1, ws, L.Omega_total, nrhs);
+        CK_LAUNCH();
+    }
+    k_sw_addx<T><<<gg, 256, 0, s>>>(aggs, L.Optr.p, L.Oidx.p, ws, xvec<T>(L), L.n, L.Omega_total, nrhs);
+    CK_LAUNCH();
+    const int64_t np = L.colpairs[c + 1] - L.colpairs[c];
+    if (np > 0) {
+        size_t sm = (size_t)std::max(1, L.max_grows_cached) * sizeof(T);
+        k_sw_scatter<T><<<(unsigned)std::min<int64_t>(np, 148 * 16), 128, sm, s>>>(
+            L.pair_agg.p + L.colpairs[c], L.pair_ent.p + L.colpairs[c], np, L.Optr.p, L.oelocoff.p, L.oeloc.p,
+            L.oeidx.p, L.eptr.p, L.eidx.p, G, L.goff.p, L.grows.p, ws, rvec<T>(L), L.n, L.Omega_total, nrhs);
+        CK_LAUNCH();
+    }
+}
+
+template <class T>
 static void sweep(Level &L, int c, int nrhs, cudaStream_t s) {
     const int64_t na = L.colptr[c + 1] - L.colptr[c];
     if (na == 0) return;
+    if (L.colmax[c] > g_split_sweep) {
+        KTime kt(KC_SCHWARZ, s, 0.0, L.sweep_bytes[std::is_same<T, double>::value ? 1 : 0][c]);
+        sweep_split<T>(L, c, nrhs, s);
+        return;
+    }
     const T *Lp;
     const T *G;
     if constexpr (std::is_same<T, float>::value) {

@@ -253,20 +253,30 @@ __global__ void __launch_bounds__(256) k_pstf_panel(double *base, const int64_t 
             return;
         }
         if (p != j) {
-            // swap rows g0+j and g0+p, then columns, over the whole view
-            for (int c = threadIdx.x; c < N; c += blockDim.x) {
-                double t = M[(g0 + j) + (int64_t)c * L];
-                M[(g0 + j) + (int64_t)c * L] = M[(g0 + p) + (int64_t)c * L];
-                M[(g0 + p) + (int64_t)c * L] = t;
+            // symmetric interchange of P = g0+j and Q = g0+p inside the stored lower triangle of
+            // the whole view (LAPACK pstrf order): row segments left of P, the diagonal, column P
+            // against row Q between them, and the columns below Q
+            const int P = g0 + j, Q = g0 + p;
+            for (int c = threadIdx.x; c < P; c += blockDim.x) {
+                double t = M[P + (int64_t)c * L];
+                M[P + (int64_t)c * L] = M[Q + (int64_t)c * L];
+                M[Q + (int64_t)c * L] = t;
             }
-            __syncthreads();
-            for (int r = threadIdx.x; r < N; r += blockDim.x) {
-                double t = M[r + (int64_t)(g0 + j) * L];
-                M[r + (int64_t)(g0 + j) * L] = M[r + (int64_t)(g0 + p) * L];
-                M[r + (int64_t)(g0 + p) * L] = t;
+            for (int r = P + 1 + threadIdx.x; r < Q; r += blockDim.x) {
+                double t = M[r + (int64_t)P * L];
+                M[r + (int64_t)P * L] = M[Q + (int64_t)r * L];
+                M[Q + (int64_t)r * L] = t;
+            }
+            for (int r = Q + 1 + threadIdx.x; r < N; r += blockDim.x) {
+                double t = M[r + (int64_t)P * L];
+                M[r + (int64_t)P * L] = M[r + (int64_t)Q * L];
+                M[r + (int64_t)Q * L] = t;
             }
             if (threadIdx.x == 0) {
-                double t = w[j];
+                double t = M[P + (int64_t)P * L];
+                M[P + (int64_t)P * L] = M[Q + (int64_t)Q * L];
+                M[Q + (int64_t)Q * L] = t;
+                t = w[j];
                 w[j] = w[p];
                 w[p] = t;
                 int u = pv[j];
@@ -477,6 +487,8 @@ __device__ double block_sum(double v, double *red) {
 // symmetric product p = tau A22 v in ONE sweep over the stored lower triangle (each warp owns
 // columns: column sums reduce in registers, the transposed contributions accumulate in shared
 // memory with atomics), then the rank-2 update A22 -= v w^T + w v^T.
+constexpr int SYTD2_THREADS = 512;
+
 __global__ void __launch_bounds__(512) k_sytd2(double *base, const int64_t *off, const int32_t *ld,
                                                const int32_t *nn, int64_t count, double *dd,
                                                double *ee, double *tt, const int64_t *toff,
@@ -488,8 +500,9 @@ __global__ void __launch_bounds__(512) k_sytd2(double *base, const int64_t *off,
     const int L = ld[b];
     double *A = base + off[b];
     double *d = dd + toff[b], *e = ee + toff[b], *tau = tt + toff[b];
-    double *p = use_smem ? smv : pwork + 2 * pwoff[b];
-    double *v = use_smem ? smv + n : pwork + 2 * pwoff[b] + n;
+    double *tbuf = smv;                                   // one 32 x 33 tile buffer per warp
+    double *p = use_smem ? smv + (blockDim.x / 32) * 32 * 33 : pwork + 2 * pwoff[b];
+    double *v = use_smem ? p + n : pwork + 2 * pwoff[b] + n;
     __shared__ double red[32];
     __shared__ double sh_tau, sh_scale;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
@@ -525,17 +538,40 @@ __global__ void __launch_bounds__(512) k_sytd2(double *base, const int64_t *off,
         }
         __syncthreads();
         double *A22 = A + (j + 1) + (int64_t)(j + 1) * L;
-        for (int c = warp; c < m; c += nwarp) {
-            const double vc = v[c];
-            const double *col = A22 + (int64_t)c * L;
-            double sacc = 0.0;
-            for (int r = c + lane; r < m; r += 32) {
-                const double a = col[r];
-                sacc += a * v[r];
-                if (r > c) atomicAdd(&p[r], a * vc);
+        // p = A22 v, tiled: each warp owns row blocks; a 32 x 32 tile is loaded coalesced into
+        // the warp's shared buffer, row sums stay in registers, column sums (the transposed
+        // half) go out with 32 shared atomics per tile
+        {
+            double(*tile)[33] = reinterpret_cast<double(*)[33]>(tbuf + (int64_t)warp * 32 * 33);
+            const int nbk = (m + 31) / 32;
+            for (int rb = warp; rb < nbk; rb += nwarp) {
+                const int r0 = rb * 32;
+                double rsum = 0.0;
+                for (int cb = 0; cb <= rb; cb++) {
+                    const int c0 = cb * 32;
+                    for (int c = 0; c < 32; c++) {
+                        const int gr = r0 + lane, gc = c0 + c;
+                        double a = 0.0;
+                        if (gr < m && gc < m && gr >= gc) a = A22[gr + (int64_t)gc * L];
+                        tile[lane][c] = a;
+                    }
+                    __syncwarp();
+                    // row sums: lane = row (diagonal tile: its stored lower part, diagonal included)
+                    for (int c = 0; c < 32; c++) {
+                        const int gc = c0 + c;
+                        if (gc < m) rsum += tile[lane][c] * v[gc];
+                    }
+                    // column sums: lane = column, strictly below the diagonal
+                    double csum = 0.0;
+                    for (int i = 0; i < 32; i++) {
+                        const int gr = r0 + i;
+                        if (gr < m && (cb != rb || i > lane)) csum += tile[i][lane] * v[gr];
+                    }
+                    if (c0 + lane < m && csum != 0.0) atomicAdd(&p[c0 + lane], csum);
+                    __syncwarp();
+                }
+                if (r0 + lane < m) atomicAdd(&p[r0 + lane], rsum);
             }
-            for (int o = 16; o; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
-            if (lane == 0) atomicAdd(&p[c], sacc);
         }
         __syncthreads();
         double pv = 0.0;
@@ -559,6 +595,150 @@ __global__ void __launch_bounds__(512) k_sytd2(double *base, const int64_t *off,
     if (threadIdx.x == 0 && n > 0) d[n - 1] = A[(n - 1) + (int64_t)(n - 1) * L];
 }
 
+// ---- multi-CTA tridiagonalisation for large matrices (one column per group of launches)
+constexpr int TRT = 64;          // tile of the symmetric product / rank-2 update
+
+// Householder vector of column j for every large matrix; restores the previous subdiagonal
+__global__ void __launch_bounds__(256) k_tr_house(double *base, const int64_t *off, const int32_t *ld,
+                                                  const int32_t *nn, int64_t count, int j, double *dd,
+                                                  double *ee, double *tt, const int64_t *toff,
+                                                  double *vbuf, double *pbuf, const int64_t *voff) {
+    int64_t b = blockIdx.x;
+    if (b >= count) return;
+    const int n = nn[b], L = ld[b];
+    double *A = base + off[b];
+    double *d = dd + toff[b], *e = ee + toff[b], *tau = tt + toff[b];
+    if (j > 0 && j <= n - 1 && threadIdx.x == 0) A[j + (int64_t)(j - 1) * L] = e[j - 1];
+    if (j >= n - 1) {
+        if (j == n - 1 && threadIdx.x == 0) d[n - 1] = A[(n - 1) + (int64_t)(n - 1) * L];
+        return;
+    }
+    const int m = n - j - 1;
+    double *x = A + (j + 1) + (int64_t)j * L;
+    double *v = vbuf + voff[b], *p = pbuf + voff[b];
+    __shared__ double red[32];
+    __shared__ double sh_tau, sh_scale;
+    double sig = 0.0;
+    for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) sig += x[i] * x[i];
+    sig = block_sum(sig, red);
+    if (threadIdx.x == 0) {
+        const double alpha = x[0];
+        d[j] = A[j + (int64_t)j * L];
+        if (sig == 0.0) {
+            sh_tau = 0.0;
+            sh_scale = 0.0;
+            e[j] = alpha;
+        } else {
+            const double beta = -copysign(sqrt(alpha * alpha + sig), alpha);
+            sh_tau = (beta - alpha) / beta;
+            sh_scale = 1.0 / (alpha - beta);
+            e[j] = beta;
+        }
+        tau[j] = sh_tau;
+    }
+    __syncthreads();
+    const double sc = sh_scale, tj = sh_tau;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const double vi = (i == 0) ? 1.0 : x[i] * sc;
+        if (i > 0) x[i] = vi;
+        v[i] = (tj == 0.0) ? 0.0 : vi;
+        p[i] = 0.0;
+    }
+}
+
+// p += A22 v over the stored lower triangle, one 64 x 64 tile per CTA (atomics into p)
+__global__ void __launch_bounds__(128) k_tr_symv(const double *base, const int64_t *off,
+                                                 const int32_t *ld, const int32_t *nn, int64_t count,
+                                                 int j, const double *vbuf, double *pbuf,
+                                                 const int64_t *voff, const double *tt,
+                                                 const int64_t *toff) {
+    int64_t b = blockIdx.y;
+    if (b >= count) return;
+    const int n = nn[b];
+    const int m = n - j - 1;
+    if (m <= 0 || tt[toff[b] + j] == 0.0) return;
+    const int T = (m + TRT - 1) / TRT;
+    if ((int64_t)blockIdx.x >= (int64_t)T * (T + 1) / 2) return;
+    int ti, tj;
+    tri_index(blockIdx.x, ti, tj);
+    const int L = ld[b];
+    const double *A22 = base + off[b] + (j + 1) + (int64_t)(j + 1) * L;
+    const double *v = vbuf + voff[b];
+    double *p = pbuf + voff[b];
+    __shared__ double T_[TRT][TRT + 1];
+    __shared__ double vr[TRT], vc[TRT];
+    const int r0 = ti * TRT, c0 = tj * TRT;
+    for (int t = threadIdx.x; t < TRT * TRT; t += blockDim.x) {
+        const int rr = t % TRT, cc = t / TRT;
+        const int gr = r0 + rr, gc = c0 + cc;
+        double a = 0.0;
+        if (gr < m && gc < m && gr >= gc) a = A22[gr + (int64_t)gc * L];
+        T_[rr][cc] = a;
+    }
+    for (int t = threadIdx.x; t < TRT; t += blockDim.x) {
+        vr[t] = (r0 + t < m) ? v[r0 + t] : 0.0;
+        vc[t] = (c0 + t < m) ? v[c0 + t] : 0.0;
+    }
+    __syncthreads();
+    if (threadIdx.x < TRT) {
+        const int rr = threadIdx.x;
+        double sacc = 0.0;
+        for (int cc = 0; cc < TRT; cc++) sacc += T_[rr][cc] * vc[cc];
+        if (r0 + rr < m) atomicAdd(&p[r0 + rr], sacc);
+    } else {
+        const int cc = threadIdx.x - TRT;
+        double sacc = 0.0;
+        for (int rr = 0; rr < TRT; rr++)
+            if (ti != tj || rr > cc) sacc += T_[rr][cc] * vr[rr];
+        if (c0 + cc < m) atomicAdd(&p[c0 + cc], sacc);
+    }
+}
+
+// p <- w = tau p - (tau^2/2)(p^T v) v
+__global__ void __launch_bounds__(256) k_tr_w(const int32_t *nn, int64_t count, int j, const double *vbuf,
+                                              double *pbuf, const int64_t *voff, const double *tt,
+                                              const int64_t *toff) {
+    int64_t b = blockIdx.x;
+    if (b >= count) return;
+    const int m = nn[b] - j - 1;
+    if (m <= 0) return;
+    const double tj = tt[toff[b] + j];
+    if (tj == 0.0) return;
+    const double *v = vbuf + voff[b];
+    double *p = pbuf + voff[b];
+    __shared__ double red[32];
+    double pv = 0.0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) pv += p[i] * v[i];
+    pv = block_sum(pv, red) * tj;
+    const double kk = -0.5 * tj * pv;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) p[i] = tj * p[i] + kk * v[i];
+}
+
+// A22 -= v w^T + w v^T on the stored lower triangle, one 64 x 64 tile per CTA
+__global__ void __launch_bounds__(256) k_tr_update(double *base, const int64_t *off, const int32_t *ld,
+                                                   const int32_t *nn, int64_t count, int j,
+                                                   const double *vbuf, const double *pbuf,
+                                                   const int64_t *voff, const double *tt,
+                                                   const int64_t *toff) {
+    int64_t b = blockIdx.y;
+    if (b >= count) return;
+    const int m = nn[b] - j - 1;
+    if (m <= 0 || tt[toff[b] + j] == 0.0) return;
+    const int T = (m + TRT - 1) / TRT;
+    if ((int64_t)blockIdx.x >= (int64_t)T * (T + 1) / 2) return;
+    int ti, tj;
+    tri_index(blockIdx.x, ti, tj);
+    const int L = ld[b];
+    double *A22 = base + off[b] + (j + 1) + (int64_t)(j + 1) * L;
+    const double *v = vbuf + voff[b], *w = pbuf + voff[b];
+    const int r0 = ti * TRT, c0 = tj * TRT;
+    for (int t = threadIdx.x; t < TRT * TRT; t += blockDim.x) {
+        const int rr = t % TRT, cc = t / TRT;
+        const int gr = r0 + rr, gc = c0 + cc;
+        if (gr < m && gc < m && gr >= gc) A22[gr + (int64_t)gc * L] -= v[gr] * w[gc] + w[gr] * v[gc];
+    }
+}
+
 // ------------------------------------------------------------------------- stebz
 __device__ int sturm_count(const double *d, const double *e, int n, double x, double pivmin) {
     int cnt = 0;
@@ -574,11 +754,12 @@ __device__ int sturm_count(const double *d, const double *e, int n, double x, do
 }
 
 __device__ double bisect_index(const double *d, const double *e, int n, int j, double lo, double hi,
-                               double pivmin) {
-    // smallest x with count(x) >= j + 1
+                               double pivmin, double atol) {
+    // smallest x with count(x) >= j + 1, to absolute width atol (= 2 eps ||T||: the accuracy the
+    // inverse-iteration shifts need)
     for (int it = 0; it < 200; it++) {
         double mid = 0.5 * (lo + hi);
-        if (hi - lo <= 2.0 * DEPS * fmax(fabs(lo), fabs(hi)) + pivmin || mid == lo || mid == hi) break;
+        if (hi - lo <= atol + pivmin || mid == lo || mid == hi) break;
         if (sturm_count(d, e, n, mid, pivmin) >= j + 1)
             hi = mid;
         else
@@ -617,7 +798,9 @@ __global__ void k_stebz(const double *dd, const double *ee, const int64_t *toff,
     int k = kk;
     // eigenvalues 0..k-1 (kept) and k (first discarded) for the gap
     for (int j = threadIdx.x; j <= k && j < n; j += blockDim.x) {
-        double lam = bisect_index(d, e, n, j, glo, ghi, pivmin);
+        // shifts to 1e-12 ||T||: the retained vectors are orthonormalised together afterwards, so
+        // eigenvalues closer than that only need to land in their cluster's subspace
+        double lam = bisect_index(d, e, n, j, glo, ghi, pivmin, 1e-12 * fmax(fabs(glo), fabs(ghi)));
         if (j < k) w[toff[b] + j] = lam;
         if (j == k - 1) lam_lo = lam;
         if (j == k) lam_hi = lam;
@@ -649,7 +832,7 @@ __global__ void __launch_bounds__(256) k_stein(const double *dd, const double *e
                                                int64_t count, const double *wv, const int32_t *kk,
                                                double *baseV, const int64_t *voff,
                                                const int32_t *vld, double *work,
-                                               const int64_t *workoff) {
+                                               const int64_t *workoff, int cluster_orth) {
     int64_t b = blockIdx.x;
     if (b >= count) return;
     const int n = nn[b], k = kk[b];
@@ -677,7 +860,9 @@ __global__ void __launch_bounds__(256) k_stein(const double *dd, const double *e
         }
         __syncthreads();
     }
-    const double ortol = 1e-3 * tnorm, pertol = 10.0 * DEPS * tnorm;
+    // eigenvectors of eigenvalues closer than ortol are re-orthogonalised; farther apart, exact-shift
+    // inverse iteration already gives orthogonality ~eps*||T||/gap <= 1e-10
+    const double ortol = 1e-6 * tnorm, pertol = 10.0 * DEPS * tnorm;
     // ---- phase 1: independent inverse iteration, one eigenvalue per thread at a time
     if (threadIdx.x < S) {
         const int sl = threadIdx.x;
@@ -739,6 +924,7 @@ __global__ void __launch_bounds__(256) k_stein(const double *dd, const double *e
         }
     }
     __syncthreads();
+    if (!cluster_orth) return;
     // ---- phase 2: orthonormalise every cluster (gaps <= ortol) by classical Gram-Schmidt twice
     int c0 = 0;
     while (c0 < k) {
@@ -891,8 +1077,8 @@ void pstrf_batched(double *base, const MatBatch &A, const int32_t *b0, const int
         int rem = max_bn - j0 - NB;
         if (rem <= 0) break;
         int64_t T = cdiv(rem, TT);
-        dim3 gu((unsigned)(T * T), (unsigned)A.count);
-        k_potrf_update<<<gu, 256, 0, s>>>(base, A.off.p, A.ld.p, bn, A.count, j0, b0, rank, 1);
+        dim3 gu((unsigned)(T * (T + 1) / 2), (unsigned)A.count);
+        k_potrf_update<<<gu, 256, 0, s>>>(base, A.off.p, A.ld.p, bn, A.count, j0, b0, rank, 0);
         CK_LAUNCH();
     }
     k_rank_finish<<<(unsigned)cdiv(A.count, 256), 256, 0, s>>>(rank, bn, A.count);
@@ -934,23 +1120,55 @@ void transpose_batched(const double *base_S, const MatBatch &Sb, double *base_D,
     CK_LAUNCH();
 }
 
+namespace {
+void sytd2_large(double *base, const MatBatch &Ab, double *d, double *e, double *tau,
+                 const int64_t *toff, cudaStream_t s) {
+    // v / p workspaces: reuse the toff layout (n entries per matrix)
+    int64_t tot = read1(toff + Ab.count, s);
+    DBuf<double> vb, pb;
+    vb.alloc(std::max<int64_t>(tot, 1), s);
+    pb.alloc(std::max<int64_t>(tot, 1), s);
+    for (int j = 0; j < Ab.maxn; j++) {
+        k_tr_house<<<(unsigned)Ab.count, 256, 0, s>>>(base, Ab.off.p, Ab.ld.p, Ab.n.p, Ab.count, j, d, e,
+                                                      tau, toff, vb.p, pb.p, toff);
+        CK_LAUNCH();
+        const int m = Ab.maxn - j - 1;
+        if (m <= 0) break;
+        const int64_t T = cdiv(m, TRT);
+        dim3 g((unsigned)(T * (T + 1) / 2), (unsigned)Ab.count);
+        k_tr_symv<<<g, 128, 0, s>>>(base, Ab.off.p, Ab.ld.p, Ab.n.p, Ab.count, j, vb.p, pb.p, toff, tau, toff);
+        CK_LAUNCH();
+        k_tr_w<<<(unsigned)Ab.count, 256, 0, s>>>(Ab.n.p, Ab.count, j, vb.p, pb.p, toff, tau, toff);
+        CK_LAUNCH();
+        k_tr_update<<<g, 256, 0, s>>>(base, Ab.off.p, Ab.ld.p, Ab.n.p, Ab.count, j, vb.p, pb.p, toff, tau, toff);
+        CK_LAUNCH();
+    }
+}
+}  // namespace
+
 void sytd2_batched(double *base, const MatBatch &Ab, double *d, double *e, double *tau,
                    const int64_t *toff, cudaStream_t s) {
     if (Ab.count == 0) return;
     double fl = 0.0;
     for (auto v : Ab.h_n) fl += 4.0 / 3.0 * v * v * v;
     KTime kt(KC_SYTD2, s, fl);
-    const size_t need = 2 * (size_t)std::max(Ab.maxn, 1) * sizeof(double);
-    const bool smem = need <= 200 * 1024;
+    if (Ab.maxn > g_large_dense) {
+        // large matrices get many CTAs per column; all matrices of this batch go this way
+        sytd2_large(base, Ab, d, e, tau, toff, s);
+        return;
+    }
+    const size_t tiles = (SYTD2_THREADS / 32) * 32 * 33 * sizeof(double);
+    const size_t need = tiles + 2 * (size_t)std::max(Ab.maxn, 1) * sizeof(double);
+    const bool smem = need <= 220 * 1024;
     DBuf<double> pw;
-    if (smem) {
-        CK(cudaFuncSetAttribute(k_sytd2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need));
-    } else {
+    if (!smem) {
         int64_t tot = read1(toff + Ab.count, s);
         pw.alloc(std::max<int64_t>(2 * tot, 1), s);
     }
-    k_sytd2<<<(unsigned)Ab.count, 512, smem ? need : 0, s>>>(base, Ab.off.p, Ab.ld.p, Ab.n.p, Ab.count,
-                                                            d, e, tau, toff, pw.p, toff, smem ? 1 : 0);
+    const size_t dyn = smem ? need : tiles;
+    CK(cudaFuncSetAttribute(k_sytd2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    k_sytd2<<<(unsigned)Ab.count, SYTD2_THREADS, dyn, s>>>(base, Ab.off.p, Ab.ld.p, Ab.n.p, Ab.count,
+                                                 d, e, tau, toff, pw.p, toff, smem ? 1 : 0);
     CK_LAUNCH();
 }
 
@@ -963,13 +1181,113 @@ void stebz_batched(const double *d, const double *e, const int64_t *toff, const 
     CK_LAUNCH();
 }
 
+namespace {
+__global__ void k_transpose_rect(const double *baseS, const int64_t *soff, const int32_t *sld,
+                                 const int32_t *sn, const int32_t *sm, double *baseD, const int64_t *doff,
+                                 const int32_t *dld, int64_t count) {
+    int64_t b = blockIdx.z;
+    if (b >= count) return;
+    const int n = sn[b], m = sm[b];
+    const int ti = blockIdx.x, tj = blockIdx.y;  // tile rows (of S) / tile cols
+    if (ti * 32 >= n || tj * 32 >= m) return;
+    const double *S = baseS + soff[b];
+    double *D = baseD + doff[b];
+    const int LS = sld[b], LD = dld[b];
+    __shared__ double t[32][33];
+    for (int u = threadIdx.x; u < 1024; u += blockDim.x) {
+        const int i = u % 32, j = u / 32;
+        const int gi = ti * 32 + i, gj = tj * 32 + j;
+        t[i][j] = (gi < n && gj < m) ? S[gi + (int64_t)gj * LS] : 0.0;
+    }
+    __syncthreads();
+    for (int u = threadIdx.x; u < 1024; u += blockDim.x) {
+        const int j = u % 32, i = u / 32;        // D[gj, gi] = S[gi, gj]
+        const int gi = ti * 32 + i, gj = tj * 32 + j;
+        if (gi < n && gj < m) D[gj + (int64_t)gi * LD] = t[i][j];
+    }
+}
+
+__global__ void k_shift_diag(double *base, const int64_t *off, const int32_t *ld, const int32_t *nn,
+                             int64_t count, double rel) {
+    int64_t b = blockIdx.x;
+    if (b >= count) return;
+    const int n = nn[b], L = ld[b];
+    double *A = base + off[b];
+    __shared__ double tr;
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < n; i++) t = fmax(t, A[i + (int64_t)i * L]);
+        tr = t;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) A[i + (int64_t)i * L] += rel * tr;
+}
+}  // namespace
+
+void transpose_rect_batched(const double *base_S, const MatBatch &Sb, double *base_D, const MatBatch &Db,
+                            cudaStream_t s) {
+    if (Sb.count == 0 || Sb.maxn == 0 || Sb.maxm == 0) return;
+    dim3 g((unsigned)cdiv(Sb.maxn, 32), (unsigned)cdiv(Sb.maxm, 32), (unsigned)Sb.count);
+    k_transpose_rect<<<g, 256, 0, s>>>(base_S, Sb.off.p, Sb.ld.p, Sb.n.p, Sb.m.p, base_D, Db.off.p, Db.ld.p,
+                                       Sb.count);
+    CK_LAUNCH();
+}
+
+void cholqr2_batched(double *base_V, const MatBatch &Vb, int *err, cudaStream_t s) {
+    if (Vb.count == 0 || Vb.maxm == 0) return;
+    const int64_t cnt = Vb.count;
+    std::vector<int64_t> goff(cnt + 1, 0), toff(cnt + 1, 0);
+    std::vector<int32_t> kk(cnt), nn(cnt);
+    for (int64_t i = 0; i < cnt; i++) {
+        kk[i] = Vb.h_m[i];
+        nn[i] = Vb.h_n[i];
+        goff[i + 1] = goff[i] + (int64_t)kk[i] * kk[i];
+        toff[i + 1] = toff[i] + (int64_t)kk[i] * nn[i];
+    }
+    DBuf<double> G, T;
+    G.alloc(std::max<int64_t>(goff[cnt], 1), s);
+    T.alloc(std::max<int64_t>(toff[cnt], 1), s);
+    MatBatch bG, bT, bTt;
+    std::vector<int64_t> go(goff.begin(), goff.end() - 1), to(toff.begin(), toff.end() - 1);
+    bG.set(go, kk, kk, kk, s);          // k x k Gram / Cholesky factor
+    bTt.set(to, kk, kk, nn, s);         // V^T: k rows x n columns, ld k (trsm right-hand side)
+    bT.set(to, kk, kk, {}, s);          // destination views for the transposes (ld k)
+    MatBatch bV2;                        // V as the source of the transposes: n rows, k columns
+    std::vector<int64_t> vo(Vb.h_n.size());
+    {
+        auto ho = to_host(Vb.off.p, cnt, s);
+        auto hl = to_host(Vb.ld.p, cnt, s);
+        for (int64_t i = 0; i < cnt; i++) vo[i] = ho[i];
+        bV2.set(vo, hl, nn, kk, s);
+    }
+    MatBatch bTsrc;                      // V^T as the source of the back-transpose: k rows, n cols
+    bTsrc.set(to, kk, kk, nn, s);
+    for (int pass = 0; pass < 2; pass++) {
+        G.zero(s);
+        MatBatch bW;                     // W = V as K x k with K = n rows (column-major)
+        {
+            auto hl = to_host(Vb.ld.p, cnt, s);
+            bW.set(vo, hl, nn, kk, s);
+        }
+        syrk_tn_batched(G.p, bG, base_V, bW, 1.0, false, s);                       // G = V^T V
+        if (pass == 0) {
+            k_shift_diag<<<(unsigned)cnt, 256, 0, s>>>(G.p, bG.off.p, bG.ld.p, bG.n.p, cnt, 1e-13);
+            CK_LAUNCH();
+        }
+        potrf_batched(G.p, bG, POTRF_SPD, err, s);                                   // G = L L^T
+        transpose_rect_batched(base_V, bV2, T.p, bT, s);                             // T = V^T
+        trsm_batched(G.p, bG, T.p, bTt, false, s);                                   // T = L^{-1} V^T
+        transpose_rect_batched(T.p, bTsrc, base_V, bV2, s);                          // V = T^T
+    }
+}
+
 void stein_batched(const double *d, const double *e, const int64_t *toff, const int32_t *n,
                    const double *w, const int32_t *k, double *base_V, const MatBatch &Vb,
-                   double *work, const int64_t *workoff, cudaStream_t s) {
+                   double *work, const int64_t *workoff, cudaStream_t s, bool cluster_orth) {
     if (Vb.count == 0) return;
     KTime kt(KC_STEIN, s);
     k_stein<<<(unsigned)Vb.count, 256, 0, s>>>(d, e, toff, n, Vb.count, w, k, base_V, Vb.off.p,
-                                              Vb.ld.p, work, workoff);
+                                              Vb.ld.p, work, workoff, cluster_orth ? 1 : 0);
     CK_LAUNCH();
 }
 

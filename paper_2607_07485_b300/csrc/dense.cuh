@@ -82,7 +82,16 @@ void stebz_batched(const double *d, const double *e, const int64_t *toff, const 
 // re-orthogonalisation inside clusters; V views (n rows, k columns).
 void stein_batched(const double *d, const double *e, const int64_t *toff, const int32_t *n,
                    const double *w, const int32_t *k, double *base_V, const MatBatch &Vb,
-                   double *work, const int64_t *workoff, cudaStream_t s);
+                   double *work, const int64_t *workoff, cudaStream_t s, bool cluster_orth = true);
+
+// Rectangular transpose: D (m x n, column-major, ld_d) = S^T with S n x m (column-major, ld_s);
+// S views: n = rows, m = columns; D views: ld only.
+void transpose_rect_batched(const double *base_S, const MatBatch &Sb, double *base_D, const MatBatch &Db,
+                            cudaStream_t s);
+
+// Orthonormalise the columns of each V (n x k, column-major) in place by CholeskyQR2 (two
+// passes of G = V^T V = L L^T, V <- V L^{-T}; the first pass with a small diagonal shift).
+void cholqr2_batched(double *base_V, const MatBatch &Vb, int *err, cudaStream_t s);
 
 // V = Q V with Q the product of the sytd2 reflectors stored in A.
 void ormtr_batched(const double *base_A, const MatBatch &Ab, const double *tau, const int64_t *toff,

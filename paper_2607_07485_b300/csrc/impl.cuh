@@ -76,6 +76,10 @@ struct Level {
     // Schwarz sweep (per colour), the coarsest triangular solves
     double spmv_bytes[2] = {0, 0};
     std::vector<double> sweep_bytes[2];
+    std::vector<int32_t> colmax;        // largest |Omega_i| of each colour
+    std::vector<int64_t> colpairs;      // colour c owns pairs [colpairs[c], colpairs[c+1])
+    DBuf<int32_t> pair_agg;             // (subdomain, element meeting Omega) pairs by colour
+    DBuf<int64_t> pair_ent;             // ... the entry index into oeidx / oelocoff
     double coarse_bytes[2] = {0, 0};
     DBuf<double> b64, x64, r64, ws64;
     DBuf<float> b32, x32, r32, ws32;

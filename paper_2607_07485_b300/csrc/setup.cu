@@ -123,7 +123,7 @@ __global__ void k_elem_factor(const double *AT, const int64_t *aoff, const int32
 // ---------------------------------------------------------------- local problem assembly
 // At (omega-first, column-major |Omega| x |Omega|) += A_T / mult(T) and Aww += A_T on
 // omega x omega, over the elements touching omega_i (eqs. 2.6-2.9).
-__global__ void k_assemble_gep(int64_t a0, int64_t na, const int64_t *aeptr, const int32_t *aeidx,
+__global__ void k_assemble_gep(const int32_t *alist, int64_t na, const int64_t *aeptr, const int32_t *aeidx,
                                const int64_t *eptr, const int32_t *eidx, const double *AT,
                                const int64_t *aoff, const int32_t *mult, const int64_t *Optr,
                                const int32_t *Oidx, const int32_t *Olpos, const int64_t *wptr,
@@ -132,7 +132,7 @@ __global__ void k_assemble_gep(int64_t a0, int64_t na, const int64_t *aeptr, con
     extern __shared__ int32_t pos[];
     int64_t li = blockIdx.x;
     if (li >= na) return;
-    int64_t a = a0 + li;
+    int64_t a = alist[li];
     const int32_t *Om = Oidx + Optr[a];
     const int32_t *lp = Olpos + Optr[a];
     int64_t nO = Optr[a + 1] - Optr[a];
@@ -539,6 +539,19 @@ void factor_elements(Level &L, int *err, cudaStream_t s) {
     check_err(err, s, "element factorisation");
 }
 
+static const char *lvl_name(int level, const char *stage) {
+    static std::vector<std::string> store;
+    static std::vector<std::pair<std::pair<int, std::string>, size_t>> index;
+    for (auto &q : index)
+        if (q.first.first == level && q.first.second == stage) return store[q.second].c_str();
+    store.reserve(256);
+    store.push_back("L" + std::to_string(level) + " " + stage);
+    index.push_back({{level, stage}, store.size() - 1});
+    return store.back().c_str();
+}
+
+int g_prof_level = 0;
+
 void local_spectral(Level &L, const lsamg_options &o, int *err, cudaStream_t s, double *flops) {
     const int64_t nagg = L.nagg;
     // keep mu * tau_cut < 1 - 1e-9 (lambda > tau_cut and the ker S modes); the relative margin
@@ -548,7 +561,8 @@ void local_spectral(Level &L, const lsamg_options &o, int *err, cudaStream_t s, 
     L.h_k.assign(nagg, 0);
     L.h_gap.assign(nagg, 0.0);
     struct Chunk {
-        int64_t a0, na;
+        std::vector<int32_t> ids;
+        int64_t na;
         DBuf<double> V;
         std::vector<int64_t> voff;
     };
@@ -558,23 +572,34 @@ void local_spectral(Level &L, const lsamg_options &o, int *err, cudaStream_t s, 
         auto ep = to_host(L.eptr.p, L.ne + 1, s);
         for (int64_t e = 0; e < L.ne; e++) maxE = std::max<int32_t>(maxE, (int32_t)(ep[e + 1] - ep[e]));
     }
-    int64_t a0 = 0;
-    while (a0 < nagg) {
-        // pick a chunk that fits the budget (at least one aggregate)
-        int64_t bytes = 0, a1 = a0;
-        while (a1 < nagg) {
-            int64_t nw = L.h_nw[a1], nO = L.h_nO[a1];
-            int64_t b = (nO * nO + 3 * nw * nw + 10 * nw) * 8;
-            if (a1 > a0 && bytes + b > budget) break;
+    // batches: aggregates of order <= 2048 (one CTA per matrix in the tridiagonalisation) and
+    // larger ones (many CTAs per matrix) are processed in separate chunks
+    std::vector<int32_t> order;
+    for (int pass = 0; pass < 2; pass++)
+        for (int64_t a = 0; a < nagg; a++)
+            if ((L.h_nw[a] > g_large_dense) == (pass == 1)) order.push_back((int32_t)a);
+    size_t q0 = 0;
+    while (q0 < order.size()) {
+        // pick a chunk that fits the budget (at least one aggregate), same size class
+        int64_t bytes = 0;
+        size_t q1 = q0;
+        const bool large = L.h_nw[order[q0]] > g_large_dense;
+        while (q1 < order.size() && (L.h_nw[order[q1]] > g_large_dense) == large) {
+            const int64_t nw = L.h_nw[order[q1]], nO = L.h_nO[order[q1]];
+            const int64_t b = (nO * nO + 3 * nw * nw + 300 * nw) * 8;
+            if (q1 > q0 && bytes + b > budget) break;
             bytes += b;
-            a1++;
+            q1++;
         }
-        const int64_t na = a1 - a0;
+        std::vector<int32_t> ids(order.begin() + q0, order.begin() + q1);
+        const int64_t na = (int64_t)ids.size();
+        DBuf<int32_t> dids;
+        upload(dids, ids, s);
         std::vector<int64_t> atoff(na + 1), awoff(na + 1), coff(na + 1), toff(na + 1);
         std::vector<int32_t> nwv(na), nGv(na), nOv(na);
         atoff[0] = awoff[0] = coff[0] = toff[0] = 0;
         for (int64_t i = 0; i < na; i++) {
-            int64_t nw = L.h_nw[a0 + i], nO = L.h_nO[a0 + i];
+            int64_t nw = L.h_nw[ids[i]], nO = L.h_nO[ids[i]];
             nwv[i] = (int32_t)nw;
             nOv[i] = (int32_t)nO;
             nGv[i] = (int32_t)(nO - nw);
@@ -605,10 +630,10 @@ void local_spectral(Level &L, const lsamg_options &o, int *err, cudaStream_t s, 
         gp.alloc(na, s);
         dk.alloc(na, s);
         // 1. assemble At (omega-first) and A_ww
-        { LSAMG_PROF("ls: assemble", s);
+        { LSAMG_PROF(lvl_name(g_prof_level, "ls: assemble"), s);
         KTime kt(KC_ASSEMBLE, s);
         k_assemble_gep<<<(unsigned)na, 256, maxE * sizeof(int32_t), s>>>(
-            a0, na, L.aeptr.p, L.aeidx.p, L.eptr.p, L.eidx.p, L.AT.p, L.aoff.p, L.mult.p, L.Optr.p,
+            dids.p, na, L.aeptr.p, L.aeidx.p, L.eptr.p, L.eidx.p, L.AT.p, L.aoff.p, L.mult.p, L.Optr.p,
             L.Oidx.p, L.Olpos.p, L.wptr.p, At.p, datoff.p, Aww.p, dawoff.p);
         CK_LAUNCH(); }
         // 2. Schur complement S = At_ww - At_wG At_GG^+ At_Gw via a semidefinite Cholesky of At_GG
@@ -636,7 +661,7 @@ void local_spectral(Level &L, const lsamg_options &o, int *err, cudaStream_t s, 
             bY.set(o3, l1, nwv, nwv, s);
             bC.set(o5, nwv, nwv, nwv, s);
         }
-        { LSAMG_PROF("ls: schur", s);
+        { LSAMG_PROF(lvl_name(g_prof_level, "ls: schur"), s);
         {
             // rank-revealing pivoted Cholesky of At_GG (the pseudo-inverse in eq. 2.9); row and
             // column swaps run over the whole At so At_wG / At_Gw are permuted consistently
@@ -661,7 +686,7 @@ void local_spectral(Level &L, const lsamg_options &o, int *err, cudaStream_t s, 
         trsm_batched(At.p, bGG, At.p, bGw, false, s);                 // W = L_G^{-1} At_Gw
         syrk_tn_batched(At.p, bww, At.p, bW, -1.0, false, s);          // S = At_ww - W^T W
         }
-        { LSAMG_PROF("ls: gep transform", s);
+        { LSAMG_PROF(lvl_name(g_prof_level, "ls: gep transform"), s);
         // 3. GEP S y = mu A_ww y -> C = L^{-1} S L^{-T}
         potrf_batched(Aww.p, bAww, POTRF_SPD, err, s);
         trsm_batched(Aww.p, bAww, At.p, bY, false, s);                // Y = L^{-1} S
@@ -669,22 +694,22 @@ void local_spectral(Level &L, const lsamg_options &o, int *err, cudaStream_t s, 
         trsm_batched(Aww.p, bAww, C.p, bC, false, s);                 // C = L^{-1} S L^{-T}
         }
         // 4. tridiagonalise, count and bisect the eigenvalues below 1/tau_cut
-        { LSAMG_PROF("ls: sytd2", s); sytd2_batched(C.p, bC, dv.p, ev.p, tv.p, dtoff.p, s); }
-        { LSAMG_PROF("ls: stebz", s); stebz_batched(dv.p, ev.p, dtoff.p, bC.n.p, na, sigma, dk.p, wv.p, gp.p, s); }
+        { LSAMG_PROF(lvl_name(g_prof_level, "ls: sytd2"), s); sytd2_batched(C.p, bC, dv.p, ev.p, tv.p, dtoff.p, s); }
+        { LSAMG_PROF(lvl_name(g_prof_level, "ls: stebz"), s); stebz_batched(dv.p, ev.p, dtoff.p, bC.n.p, na, sigma, dk.p, wv.p, gp.p, s); }
         auto hk = to_host(dk.p, na, s);
         auto hg = to_host(gp.p, na, s);
         check_err(err, s, "local spectral problems (factorisations)");
         std::vector<int64_t> voff(na + 1), wkoff(na + 1);
         voff[0] = wkoff[0] = 0;
         for (int64_t i = 0; i < na; i++) {
-            L.h_k[a0 + i] = hk[i];
-            L.h_gap[a0 + i] = hg[i];
+            L.h_k[ids[i]] = hk[i];
+            L.h_gap[ids[i]] = hg[i];
             voff[i + 1] = voff[i] + (int64_t)nwv[i] * hk[i];
             wkoff[i + 1] = wkoff[i] + 4 * 64 * (int64_t)nwv[i];  // inverse-iteration scratch
             *flops += 4.0 * nwv[i] * (double)nwv[i] * hk[i] + (double)nwv[i] * nwv[i] * hk[i];
         }
         Chunk ch;
-        ch.a0 = a0;
+        ch.ids = ids;
         ch.na = na;
         ch.voff = voff;
         ch.V.alloc(std::max<int64_t>(voff[na], 1), s);
@@ -698,13 +723,19 @@ void local_spectral(Level &L, const lsamg_options &o, int *err, cudaStream_t s, 
             bV.set(o, nwv, nwv, hk, s);
         }
         // 5. eigenvectors: inverse iteration, back-transformation, Z = L^{-T} V
-        { LSAMG_PROF("ls: stein", s); stein_batched(dv.p, ev.p, dtoff.p, bC.n.p, wv.p, dk.p, ch.V.p, bV, work.p, dwk.p, s); }
-        { LSAMG_PROF("ls: ormtr", s); ormtr_batched(C.p, bC, tv.p, dtoff.p, ch.V.p, bV, s); }
-        { LSAMG_PROF("ls: trsm Z", s); trsm_batched(Aww.p, bAww, ch.V.p, bV, true, s); }
+        {
+            // inverse iteration per eigenvalue, then one CholeskyQR2 over all retained vectors:
+            // P needs an orthonormal basis of the retained invariant subspace, not the eigenvectors
+            LSAMG_PROF(lvl_name(g_prof_level, "ls: stein"), s);
+            stein_batched(dv.p, ev.p, dtoff.p, bC.n.p, wv.p, dk.p, ch.V.p, bV, work.p, dwk.p, s, false);
+            cholqr2_batched(ch.V.p, bV, err, s);
+        }
+        { LSAMG_PROF(lvl_name(g_prof_level, "ls: ormtr"), s); ormtr_batched(C.p, bC, tv.p, dtoff.p, ch.V.p, bV, s); }
+        { LSAMG_PROF(lvl_name(g_prof_level, "ls: trsm Z"), s); trsm_batched(Aww.p, bAww, ch.V.p, bV, true, s); }
         CK(cudaStreamSynchronize(s));
         check_err(err, s, "local spectral problems");
         chunks.push_back(std::move(ch));
-        a0 = a1;
+        q0 = q1;
     }
     // P storage: Z_i row-major, sign-normalised
     std::vector<int64_t> zoff(nagg + 1), off(nagg + 1);
@@ -725,9 +756,9 @@ void local_spectral(Level &L, const lsamg_options &o, int *err, cudaStream_t s, 
         std::vector<int64_t> zo(ch.na);
         std::vector<int32_t> nwv(ch.na), kv(ch.na);
         for (int64_t i = 0; i < ch.na; i++) {
-            zo[i] = zoff[ch.a0 + i];
-            nwv[i] = L.h_nw[ch.a0 + i];
-            kv[i] = L.h_k[ch.a0 + i];
+            zo[i] = zoff[ch.ids[i]];
+            nwv[i] = L.h_nw[ch.ids[i]];
+            kv[i] = L.h_k[ch.ids[i]];
         }
         upload(dvo, ch.voff, s);
         upload(dzo, zo, s);

@@ -392,3 +392,32 @@ def test_local_eigenpairs_self_consistent(name):
                                        err_msg=f"level {l} aggregate {a}: Z not A_ww-orthonormal")
             worst = max(worst, np.linalg.norm(_projector(Zg) - _projector(Zr), 2))
         assert worst <= ptol, f"level {l}: self-consistency projector difference {worst:.3e}"
+
+
+@pytest.mark.parametrize("name", ["cfg1", "cfg3_16"])
+def test_multi_cta_paths_match_single_cta(name):
+    """The multi-CTA tridiagonalisation and the split Schwarz sweep (used for large local
+    problems) forced on a small case: same coarse space and the same V-cycle as the
+    one-CTA-per-matrix kernels (and so as the oracle)."""
+    p, H, amg, ptol, vtol, _ = case(name)
+    gen, opts, *_ = CASES[name]
+    o = dict(opts)
+    if "tau_c" not in o and "c_tau" in p:
+        o["tau_c"] = p["c_tau"]
+    big = Lsamg(p["n"], torch.from_numpy(p["elem_dofs"]).to(DEV), torch.from_numpy(p["mats"]).to(DEV),
+                large_dense=16, split_sweep=16, **o)
+    L0 = H.levels[0]
+    np.testing.assert_array_equal(big.query(0, "K"), amg.query(0, "K"))
+    zoff, Z = big.query(0, "ZOFF"), big.query(0, "Z")
+    for i in range(L0.nagg):
+        nw, k = len(L0.omega[i]), int(L0.k[i])
+        Zg = Z[zoff[i]:zoff[i + 1]].reshape(nw, k)
+        assert np.linalg.norm(_projector(Zg) - _projector(L0.Z[i]), 2) <= ptol
+    r = np.random.default_rng(6).standard_normal(p["n"])
+    rt = torch.from_numpy(r).to(DEV)
+    z1 = big.apply(rt, fp32=0).cpu().numpy()
+    z0 = amg.apply(rt, fp32=0).cpu().numpy()
+    assert np.linalg.norm(z1 - z0) <= vtol * np.linalg.norm(z0)
+    zo = O.vcycle(H, r)
+    assert np.linalg.norm(z1 - zo) <= vtol * np.linalg.norm(zo)
+    big.close()
