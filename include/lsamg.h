@@ -80,7 +80,10 @@ typedef struct {
     int32_t verbose;
     int32_t profile;             /* 1: time every kernel class with CUDA events on the stream */
     int32_t large_dense;         /* local problems above this order use multi-CTA kernels (0 = 2048) */
-    int32_t split_sweep;         /* Schwarz colours with larger overlaps use the split sweep (0 = 4096) */
+    int32_t split_sweep;         /* Schwarz colours whose largest overlap exceeds this use the blocked
+                                    many-CTA sweep, smaller ones one CTA per subdomain (0 = 128) */
+    int32_t sweep_block;         /* rows per diagonal block of the blocked triangular solves of the
+                                    Schwarz and coarsest factors, 1..64 (0 = 64); fixed at setup */
 } lsamg_options;
 
 lsamg_options lsamg_options_default(void);

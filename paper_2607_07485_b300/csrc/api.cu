@@ -137,9 +137,9 @@ void finish_level_info(Level &L, cudaStream_t s) {
                 }
                 for (int t = 0; t < 2; t++) {
                     const double w = t ? 8.0 : 4.0;
-                    // factor (packed lower), element G blocks, index maps, residual gather / x
-                    // update / residual scatter
-                    L.sweep_bytes[t][c] += nO * (nO + 1) / 2.0 * w + g * w + idx * 4.0 + 4.0 * nO * w;
+                    // packed factor read by both substitutions, element G blocks, index maps,
+                    // residual gather / x update / residual scatter
+                    L.sweep_bytes[t][c] += nO * (nO + 1) * w + g * w + idx * 4.0 + 4.0 * nO * w;
                 }
             }
     }
@@ -154,6 +154,7 @@ void do_setup(Handle &H, const lsamg_problem *P, const lsamg_options &o) {
         fail(LSAMG_INVALID_ARG, "invalid problem description");
     if (P->n_dofs >= (1ll << 30)) fail(LSAMG_LIMIT, "more than 2^30 DOFs");
     if (o.max_levels < 1 || o.max_levels > 8) fail(LSAMG_INVALID_ARG, "max_levels must be in 1..8");
+    if (o.sweep_block < 0 || o.sweep_block > 64) fail(LSAMG_INVALID_ARG, "sweep_block must be in 0..64");
     H.err.alloc(2, s);
     H.err.zero(s);
     int *err = H.err.p;
@@ -455,6 +456,11 @@ struct lsamg_handle {
     Handle h;
 };
 
+static void set_sweep_globals(const lsamg_options &o) {
+    g_split_sweep = o.split_sweep > 0 ? o.split_sweep : 128;
+    g_sweep_block = o.sweep_block > 0 ? std::min(o.sweep_block, 64) : 64;
+}
+
 extern "C" {
 
 lsamg_options lsamg_options_default(void) {
@@ -475,6 +481,7 @@ lsamg_options lsamg_options_default(void) {
     o.profile = 0;
     o.large_dense = 0;
     o.split_sweep = 0;
+    o.sweep_block = 0;
     return o;
 }
 
@@ -505,7 +512,7 @@ int lsamg_setup(const lsamg_problem *prob, const lsamg_options *opts, void *stre
     h->h.opt = opts ? *opts : lsamg_options_default();
     ktimer_enable(h->h.opt.profile != 0);
     g_large_dense = h->h.opt.large_dense > 0 ? h->h.opt.large_dense : 2048;
-    g_split_sweep = h->h.opt.split_sweep > 0 ? h->h.opt.split_sweep : 4096;
+    set_sweep_globals(h->h.opt);
     int rc = guarded([&] { do_setup(h->h, prob, h->h.opt); });
     if (rc != LSAMG_OK) {
         std::string msg = g_last_error;
@@ -524,7 +531,7 @@ int lsamg_apply(lsamg_handle *h, const double *r, double *z, int32_t nrhs, int32
     return guarded([&] {
         Handle &H = h->h;
         H.stream = (cudaStream_t)stream;
-        g_split_sweep = H.opt.split_sweep > 0 ? H.opt.split_sweep : 4096;
+        set_sweep_globals(H.opt);
         ensure_solve_ws(H, nrhs);
         bool f = fp32 < 0 ? H.opt.vcycle_fp32 != 0 : fp32 != 0;
         precondition(H, r, z, nrhs, f);
@@ -539,7 +546,7 @@ int lsamg_solve(lsamg_handle *h, const double *b, double *x, int32_t nrhs, int32
     int rc = guarded([&] {
         Handle &H = h->h;
         H.stream = (cudaStream_t)stream;
-        g_split_sweep = H.opt.split_sweep > 0 ? H.opt.split_sweep : 4096;
+        set_sweep_globals(H.opt);
         status = do_solve(H, b, x, nrhs, mode, use_x0 != 0, iters, relres);
     });
     if (rc != LSAMG_OK) return rc;

@@ -8,7 +8,8 @@
 namespace lsamg {
 
 int g_large_dense = 2048;
-int g_split_sweep = 4096;
+int g_split_sweep = 128;
+int g_sweep_block = 64;
 
 static int64_t g_launches = 0;
 void count_launch() { g_launches++; }

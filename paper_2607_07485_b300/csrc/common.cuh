@@ -215,5 +215,6 @@ constexpr int SEG_SMEM_MAX = 56 * 1024;  // max int32 entries of one segment sor
 // size thresholds between one-CTA-per-matrix and multi-CTA kernels (set from the options)
 extern int g_large_dense;
 extern int g_split_sweep;
+extern int g_sweep_block;
 
 }  // namespace lsamg

@@ -174,132 +174,384 @@ __global__ void __launch_bounds__(256) k_schwarz(const int32_t *aggs, int64_t na
 }
 
 // ---------------------------------------------------------------- transfers
+// rc[off_a + j] = sum_p Z_a[p, j] res[omega_a[p]] (P^T r, P = blockdiag R_omega^T Z_a).  One CTA
+// per aggregate: the 8 warps take interleaved rows of Z_a (coalesced, 4 rows in flight), lanes
+// take columns in chunks of 128, and the warps' partial sums are added in shared memory.
 template <class T>
-__global__ void k_restrict(const int64_t *wptr, const int32_t *widx, const int32_t *k,
-                           const int64_t *off, const T *Z, const int64_t *zoff, int64_t nagg,
-                           const T *res, int64_t n, T *rc, int64_t nc, int nrhs) {
-    for (int64_t a = blockIdx.x; a < nagg; a += gridDim.x) {
-        const int ka = k[a];
-        const int64_t wb = wptr[a];
-        const int nw = (int)(wptr[a + 1] - wb);
-        const T *z = Z + zoff[a];
-        for (int r = 0; r < nrhs; r++)
-            for (int j = threadIdx.x; j < ka; j += blockDim.x) {
-                T s = 0;
-                for (int p = 0; p < nw; p++) s += z[(int64_t)p * ka + j] * res[(int64_t)r * n + widx[wb + p]];
-                rc[(int64_t)r * nc + off[a] + j] = s;
-            }
-    }
-}
-
-template <class T>
-__global__ void k_interp(const int64_t *wptr, const int32_t *widx, const int32_t *k,
-                         const int64_t *off, const T *Z, const int64_t *zoff, int64_t nagg,
-                         const T *ec, int64_t nc, T *x, int64_t n, int nrhs) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    for (int64_t a = blockIdx.x; a < nagg; a += gridDim.x) {
-        const int ka = k[a];
-        const int64_t wb = wptr[a];
-        const int nw = (int)(wptr[a + 1] - wb);
-        const T *z = Z + zoff[a];
-        for (int r = 0; r < nrhs; r++)
-            for (int p = warp; p < nw; p += nwarp) {
-                T s = 0;
-                for (int j = lane; j < ka; j += 32) s += z[(int64_t)p * ka + j] * ec[(int64_t)r * nc + off[a] + j];
-                s = warp_sum(s);
-                if (lane == 0) x[(int64_t)r * n + widx[wb + p]] += s;
-            }
-    }
-}
-
-// ---------------------------------------------------------------- blocked coarsest solve
-constexpr int CB = 256;            // rows per block of the multi-CTA triangular solves
-
-// forward solve of the diagonal block rows [r0, r1) of L y = v (columns < r0 already applied)
-template <class T>
-__global__ void __launch_bounds__(256) k_cs_fwd_diag(const T *L, int r0, int r1, T *v, int64_t stride) {
-    __shared__ T red[32];
-    T *vr = v + (int64_t)blockIdx.x * stride;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    for (int b0 = r0; b0 < r1; b0 += 32) {
-        const int rs = min(32, r1 - b0);
-        for (int i = warp; i < rs; i += nwarp) {
-            const T *row = L + (int64_t)(b0 + i) * (b0 + i + 1) / 2;
-            T sacc = 0;
-            for (int j = r0 + lane; j < b0; j += 32) sacc += row[j] * vr[j];
-            sacc = warp_sum(sacc);
-            if (lane == 0) red[i] = vr[b0 + i] - sacc;
-        }
-        __syncthreads();
-        if (warp == 0) {
-            T yl = 0;
-            for (int i = 0; i < rs; i++) {
-                const T *row = L + (int64_t)(b0 + i) * (b0 + i + 1) / 2 + b0;
-                T c = (lane < i) ? row[lane] * yl : (T)0;
-                c = warp_sum(c);
-                T yi = (red[i] - c) / row[i];
-                if (lane == i) yl = yi;
-            }
-            if (lane < rs) vr[b0 + lane] = yl;
-        }
-        __syncthreads();
-    }
-}
-
-// v[r] -= sum_{j in [r0, r1)} L[r, j] y[j] for rows r >= r1 (warp per row)
-template <class T>
-__global__ void __launch_bounds__(256) k_cs_fwd_update(const T *L, int r0, int r1, int n, T *v,
-                                                       int64_t stride) {
-    T *vr = v + (int64_t)blockIdx.y * stride;
-    const int lane = threadIdx.x & 31;
-    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t r = r1 + wid; r < n; r += nw) {
-        const T *row = L + r * (r + 1) / 2;
-        T sacc = 0;
-        for (int j = r0 + lane; j < r1; j += 32) sacc += row[j] * vr[j];
-        sacc = warp_sum(sacc);
-        if (lane == 0) vr[r] -= sacc;
-    }
-}
-
-// backward solve of the diagonal block [r0, r1) of L^T x = y (rows >= r1 already applied)
-template <class T>
-__global__ void __launch_bounds__(256) k_cs_bwd_diag(const T *L, int r0, int r1, T *v, int64_t stride) {
-    T *vr = v + (int64_t)blockIdx.x * stride;
+__global__ void __launch_bounds__(256) k_restrict(const int64_t *wptr, const int32_t *widx, const int32_t *k,
+                                                  const int64_t *off, const T *Z, const int64_t *zoff,
+                                                  int64_t nagg, const T *res, int64_t n, T *rc, int64_t nc,
+                                                  int nrhs) {
+    __shared__ T red[8][128];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nb = (r1 - r0 + 31) / 32;
-    for (int bi = nb - 1; bi >= 0; bi--) {
-        const int b0 = r0 + bi * 32, rs = min(32, r1 - b0);
-        if (warp == 0) {
-            T xl = (lane < rs) ? vr[b0 + lane] : (T)0;
-            for (int i = rs - 1; i >= 0; i--) {
-                const T *row = L + (int64_t)(b0 + i) * (b0 + i + 1) / 2 + b0;
-                T xi = __shfl_sync(0xffffffffu, xl, i) / row[i];
-                if (lane == i) xl = xi;
-                if (lane < i) xl -= row[lane] * xi;
+    for (int64_t a = blockIdx.x; a < nagg; a += gridDim.x) {
+        const int ka = k[a];
+        const int64_t wb = wptr[a];
+        const int nw = (int)(wptr[a + 1] - wb);
+        const T *z = Z + zoff[a];
+        for (int r = 0; r < nrhs; r++) {
+            const T *rr = res + (int64_t)r * n;
+            for (int j0 = 0; j0 < ka; j0 += 128) {
+                T acc[4] = {0, 0, 0, 0};
+#pragma unroll 4
+                for (int p = warp; p < nw; p += 8) {
+                    const T rp = rr[widx[wb + p]];
+                    const T *zr = z + (int64_t)p * ka + j0;
+#pragma unroll
+                    for (int u = 0; u < 4; u++) {
+                        const int j = lane + 32 * u;
+                        if (j0 + j < ka) acc[u] += zr[j] * rp;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; u++) red[warp][lane + 32 * u] = acc[u];
+                __syncthreads();
+                if (threadIdx.x < 128 && j0 + (int)threadIdx.x < ka) {
+                    T sum = 0;
+#pragma unroll
+                    for (int w = 0; w < 8; w++) sum += red[w][threadIdx.x];
+                    rc[(int64_t)r * nc + off[a] + j0 + threadIdx.x] = sum;
+                }
+                __syncthreads();
             }
-            if (lane < rs) vr[b0 + lane] = xl;
         }
-        __syncthreads();
-        for (int j = r0 + threadIdx.x; j < b0; j += blockDim.x) {
-            T sacc = 0;
-            for (int i = 0; i < rs; i++) sacc += L[(int64_t)(b0 + i) * (b0 + i + 1) / 2 + j] * vr[b0 + i];
-            vr[j] -= sacc;
-        }
-        __syncthreads();
     }
 }
 
-// v[j] -= sum_{i in [r0, r1)} L[i, j] x[i] for columns j < r0 (thread per column)
+// x[omega_a[p]] += sum_j Z_a[p, j] ec[off_a + j] (x += P e_c).  One CTA per aggregate, the coarse
+// values staged in shared memory, a warp per row of Z_a (4 rows in flight).
 template <class T>
-__global__ void __launch_bounds__(256) k_cs_bwd_update(const T *L, int r0, int r1, T *v, int64_t stride) {
-    T *vr = v + (int64_t)blockIdx.y * stride;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < r0;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        T sacc = 0;
-        for (int i = r0; i < r1; i++) sacc += L[(int64_t)i * (i + 1) / 2 + j] * vr[i];
-        vr[j] -= sacc;
+__global__ void __launch_bounds__(256) k_interp(const int64_t *wptr, const int32_t *widx, const int32_t *k,
+                                                const int64_t *off, const T *Z, const int64_t *zoff,
+                                                int64_t nagg, const T *ec, int64_t nc, T *x, int64_t n,
+                                                int nrhs) {
+    extern __shared__ unsigned char smraw[];
+    T *e = reinterpret_cast<T *>(smraw);   // [max k]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t a = blockIdx.x; a < nagg; a += gridDim.x) {
+        const int ka = k[a];
+        const int64_t wb = wptr[a];
+        const int nw = (int)(wptr[a + 1] - wb);
+        const T *z = Z + zoff[a];
+        for (int r = 0; r < nrhs; r++) {
+            __syncthreads();
+            for (int j = threadIdx.x; j < ka; j += blockDim.x) e[j] = ec[(int64_t)r * nc + off[a] + j];
+            __syncthreads();
+            T *xr = x + (int64_t)r * n;
+#pragma unroll 4
+            for (int p = warp; p < nw; p += 8) {
+                const T *zr = z + (int64_t)p * ka;
+                T sum = 0;
+                for (int j = lane; j < ka; j += 32) sum += zr[j] * e[j];
+                sum = warp_sum(sum);
+                if (lane == 0) xr[widx[wb + p]] += sum;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- blocked triangular solves
+// In-place solve of L L^T v = v for several independent packed lower row-major factors (row i
+// at offset i(i+1)/2): the subdomains of one Schwarz colour, or the coarsest matrix.  Rows are
+// cut into blocks of cb <= TRI_CB rows whose diagonal blocks are inverted once at set-up
+// (Dinv, FP64 packed lower row-major, block b of system a at Doff[a] + b cb(cb+1)/2; the
+// product with it is formed in FP64 in the FP32 cycle too, since an explicit inverse of an
+// ill-conditioned block rounded to FP32 loses its small components to cancellation).  Every launch
+// advances all systems by one block: CTA 0 of a system finishes the next diagonal block (its
+// update by the block just solved, then the product with the inverted diagonal block; all of
+// its loads are issued on entry), CTAs 1.. apply the block just solved to the rest of the
+// system with coalesced loads, many in flight per thread.
+constexpr int TRI_CB = 64;      // largest block
+constexpr int TRI_RG = 8;       // right-hand sides per pass through shared memory
+constexpr int TRI_RPW = TRI_CB / 8;   // block rows per warp in CTA 0
+constexpr int TRI_NU = TRI_CB / 32;   // block columns per lane
+constexpr int TRI_ROWS = 64;    // rows per forward update CTA (8 per warp)
+constexpr int TRI_COLS = 128;   // columns per backward update CTA (2 row halves per column)
+
+__host__ __device__ inline int64_t tri_block_words(int cb) { return (int64_t)cb * (cb + 1) / 2; }
+
+// Forward substitution L y = v.  Block k = rows [k cb, (k+1) cb) already holds y_k; finish block
+// k+1.  k = -1 starts every system (solves block 0).
+template <class T>
+__global__ void __launch_bounds__(256) k_tri_fwd(const int32_t *sys, const int64_t *Optr, const T *Lp,
+                                                 const int64_t *Loff, const double *Dp, const int64_t *Doff,
+                                                 int k, int cb, T *ws, int64_t wsn, int nrhs) {
+    __shared__ T sm[2 * TRI_RG * TRI_CB];
+    const int32_t a = sys ? sys[blockIdx.y] : (int32_t)blockIdx.y;
+    const int64_t ob = Optr[a];
+    const int n = (int)(Optr[a + 1] - ob);
+    const int r0 = k * cb, r1 = r0 + cb;
+    if (r1 >= n) return;
+    const int r2 = min(n, r1 + cb);
+    const T *L = Lp + Loff[a];
+    T *v = ws + ob;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T *y = sm;                       // [TRI_RG][cb]  y_k
+    T *tv = sm + TRI_RG * TRI_CB;    // [TRI_RG][cb]  block k+1 right-hand sides
+    if (blockIdx.x > 0) {
+        // rows i in [i0, i0 + TRI_ROWS) beyond block k+1: v_i -= L[i, r0:r1] y_k
+        if (k < 0) return;
+        const int64_t i0 = (int64_t)r2 + (int64_t)(blockIdx.x - 1) * TRI_ROWS;
+        if (i0 >= n) return;
+        constexpr int NQ = TRI_ROWS / 8;
+        T lv[NQ][TRI_NU];
+#pragma unroll
+        for (int q = 0; q < NQ; q++) {
+            const int64_t i = i0 + warp + 8 * q;
+#pragma unroll
+            for (int u = 0; u < TRI_NU; u++) {
+                const int j = lane + 32 * u;
+                lv[q][u] = (i < n && j < cb) ? L[i * (i + 1) / 2 + r0 + j] : (T)0;
+            }
+        }
+        for (int g0 = 0; g0 < nrhs; g0 += TRI_RG) {
+            const int nr = min(TRI_RG, nrhs - g0);
+            __syncthreads();
+            for (int q = threadIdx.x; q < nr * cb; q += blockDim.x) {
+                const int r = q / cb;
+                y[r * TRI_CB + q - r * cb] = v[(int64_t)(g0 + r) * wsn + r0 + (q - r * cb)];
+            }
+            __syncthreads();
+            for (int r = 0; r < nr; r++) {
+                T *vr = v + (int64_t)(g0 + r) * wsn;
+                T old[NQ];
+#pragma unroll
+                for (int q = 0; q < NQ; q++) {
+                    const int64_t i = i0 + warp + 8 * q;
+                    old[q] = (lane == 0 && i < n) ? vr[i] : (T)0;
+                }
+#pragma unroll
+                for (int q = 0; q < NQ; q++) {
+                    T acc = 0;
+#pragma unroll
+                    for (int u = 0; u < TRI_NU; u++) {
+                        const int j = lane + 32 * u;
+                        if (j < cb) acc += lv[q][u] * y[r * TRI_CB + j];
+                    }
+                    acc = warp_sum(acc);
+                    const int64_t i = i0 + warp + 8 * q;
+                    if (lane == 0 && i < n) vr[i] = old[q] - acc;
+                }
+            }
+        }
+        return;
+    }
+    // CTA 0: block k+1 = rows [r1, r2); t = v - L[r1:r2, r0:r1] y_k, then y_{k+1} = Dinv t
+    const int nb = r2 - r1;
+    const double *Di = Dp + Doff[a] + (int64_t)(k + 1) * tri_block_words(cb);
+    T pv[TRI_RPW][TRI_NU];
+    double dv[TRI_RPW][TRI_NU];
+#pragma unroll
+    for (int q = 0; q < TRI_RPW; q++) {
+        const int i = warp + 8 * q;
+        const int64_t gi = (int64_t)r1 + i;
+#pragma unroll
+        for (int u = 0; u < TRI_NU; u++) {
+            const int j = lane + 32 * u;
+            pv[q][u] = (k >= 0 && i < nb && j < cb) ? L[gi * (gi + 1) / 2 + r0 + j] : (T)0;
+            dv[q][u] = (i < nb && j <= i) ? Di[i * (i + 1) / 2 + j] : 0.0;
+        }
+    }
+    for (int g0 = 0; g0 < nrhs; g0 += TRI_RG) {
+        const int nr = min(TRI_RG, nrhs - g0);
+        __syncthreads();
+        for (int q = threadIdx.x; q < nr * TRI_CB; q += blockDim.x) {
+            const int r = q / TRI_CB, j = q - r * TRI_CB;
+            const T *vr = v + (int64_t)(g0 + r) * wsn;
+            y[q] = (k >= 0 && j < cb) ? vr[r0 + j] : (T)0;
+            tv[q] = (j < nb) ? vr[r1 + j] : (T)0;
+        }
+        __syncthreads();
+        if (k >= 0) {
+            for (int r = 0; r < nr; r++) {
+#pragma unroll
+                for (int q = 0; q < TRI_RPW; q++) {
+                    const int i = warp + 8 * q;
+                    T acc = 0;
+#pragma unroll
+                    for (int u = 0; u < TRI_NU; u++) acc += pv[q][u] * y[r * TRI_CB + lane + 32 * u];
+                    acc = warp_sum(acc);
+                    if (lane == 0 && i < nb) tv[r * TRI_CB + i] -= acc;
+                }
+            }
+            __syncthreads();
+        }
+        for (int r = 0; r < nr; r++) {
+            T *vr = v + (int64_t)(g0 + r) * wsn;
+#pragma unroll
+            for (int q = 0; q < TRI_RPW; q++) {
+                const int i = warp + 8 * q;
+                double acc = 0;
+#pragma unroll
+                for (int u = 0; u < TRI_NU; u++) acc += dv[q][u] * (double)tv[r * TRI_CB + lane + 32 * u];
+                acc = warp_sum(acc);
+                if (lane == 0 && i < nb) vr[r1 + i] = (T)acc;
+            }
+        }
+    }
+}
+
+// Backward substitution L^T x = y.  Block k holds x_k (k < K = ceil(n / cb)); finish block k-1.
+// k = K starts a system (solves its last block).
+template <class T>
+__global__ void __launch_bounds__(256) k_tri_bwd(const int32_t *sys, const int64_t *Optr, const T *Lp,
+                                                 const int64_t *Loff, const double *Dp, const int64_t *Doff,
+                                                 int k, int cb, T *ws, int64_t wsn, int nrhs) {
+    __shared__ T sm[2 * TRI_RG * TRI_CB + TRI_RG * TRI_COLS];
+    __shared__ double red[4 * TRI_RG * TRI_CB];   // CTA 0: partial sums of the 4 row parts
+    const int32_t a = sys ? sys[blockIdx.y] : (int32_t)blockIdx.y;
+    const int64_t ob = Optr[a];
+    const int n = (int)(Optr[a + 1] - ob);
+    const int K = (n + cb - 1) / cb;
+    if (k > K || k < 1) return;
+    const bool first = (k == K);
+    const int r0 = k * cb, r1 = min(n, r0 + cb);        // block k (unless first)
+    const int b0 = (k - 1) * cb, b1 = first ? n : r0;   // block k-1
+    const T *L = Lp + Loff[a];
+    T *v = ws + ob;
+    const int tid = threadIdx.x;
+    T *xk = sm;                                 // [TRI_RG][TRI_CB]  x_k
+    if (blockIdx.x > 0) {
+        // columns j in [c0, c0 + TRI_COLS) before block k-1: v_j -= sum_{i in block k} L[i, j] x_i
+        if (first) return;
+        const int c0 = (int)(blockIdx.x - 1) * TRI_COLS;
+        if (c0 >= b0) return;
+        const int col = tid & (TRI_COLS - 1), half = tid >> 7;
+        const int j = c0 + col;
+        T *part = sm + TRI_RG * TRI_CB;         // [TRI_RG][TRI_COLS]
+        constexpr int NL = TRI_CB / 2;
+        T lv[NL];
+#pragma unroll
+        for (int m = 0; m < NL; m++) {
+            const int i = r0 + half + 2 * m;
+            lv[m] = (j < b0 && i < r1) ? L[(int64_t)i * (i + 1) / 2 + j] : (T)0;
+        }
+        for (int g0 = 0; g0 < nrhs; g0 += TRI_RG) {
+            const int nr = min(TRI_RG, nrhs - g0);
+            __syncthreads();
+            for (int q = tid; q < nr * TRI_CB; q += blockDim.x) {
+                const int r = q / TRI_CB, i = q - r * TRI_CB;
+                xk[q] = (r0 + i < r1) ? v[(int64_t)(g0 + r) * wsn + r0 + i] : (T)0;
+            }
+            __syncthreads();
+            T acc[TRI_RG];
+#pragma unroll
+            for (int r = 0; r < TRI_RG; r++) {
+                acc[r] = 0;
+                if (r < nr) {
+#pragma unroll
+                    for (int m = 0; m < NL; m++) acc[r] += lv[m] * xk[r * TRI_CB + half + 2 * m];
+                }
+            }
+            if (half == 1)
+                for (int r = 0; r < nr; r++) part[r * TRI_COLS + col] = acc[r];
+            __syncthreads();
+            if (half == 0 && j < b0)
+                for (int r = 0; r < nr; r++) v[(int64_t)(g0 + r) * wsn + j] -= acc[r] + part[r * TRI_COLS + col];
+        }
+        return;
+    }
+    // CTA 0: block k-1 = rows [b0, b1); t = v - L[r0:r1, b0:b1]^T x_k, then x_{k-1} = Dinv^T t.
+    // Thread (col, part): column col of the block, rows part, part + 4, ...
+    const int nb = b1 - b0;
+    const int col = tid & (TRI_CB - 1), part = tid / TRI_CB;   // 4 parts
+    constexpr int NP = TRI_CB / 4;
+    const double *Di = Dp + Doff[a] + (int64_t)(k - 1) * tri_block_words(cb);
+    T pv[NP];
+    double dv[NP];
+#pragma unroll
+    for (int m = 0; m < NP; m++) {
+        const int ii = part + 4 * m;              // row within block k / within block k-1
+        const int gi = r0 + ii;
+        pv[m] = (!first && col < nb && gi < r1) ? L[(int64_t)gi * (gi + 1) / 2 + b0 + col] : (T)0;
+        dv[m] = (col < nb && ii < nb && ii >= col) ? Di[ii * (ii + 1) / 2 + col] : 0.0;
+    }
+    T *tv = sm + TRI_RG * TRI_CB;               // [TRI_RG][TRI_CB]
+    for (int g0 = 0; g0 < nrhs; g0 += TRI_RG) {
+        const int nr = min(TRI_RG, nrhs - g0);
+        __syncthreads();
+        for (int q = tid; q < nr * TRI_CB; q += blockDim.x) {
+            const int r = q / TRI_CB, i = q - r * TRI_CB;
+            const T *vr = v + (int64_t)(g0 + r) * wsn;
+            xk[q] = (!first && r0 + i < r1) ? vr[r0 + i] : (T)0;
+            tv[q] = (i < nb) ? vr[b0 + i] : (T)0;
+        }
+        __syncthreads();
+        if (!first) {
+            for (int r = 0; r < nr; r++) {
+                T acc = 0;
+#pragma unroll
+                for (int m = 0; m < NP; m++) acc += pv[m] * xk[r * TRI_CB + part + 4 * m];
+                red[(part * TRI_RG + r) * TRI_CB + col] = (double)acc;
+            }
+            __syncthreads();
+            for (int q = tid; q < nr * TRI_CB; q += blockDim.x) {
+                const int r = q / TRI_CB, c = q - r * TRI_CB;
+                tv[q] -= (T)(red[(0 * TRI_RG + r) * TRI_CB + c] + red[(1 * TRI_RG + r) * TRI_CB + c] +
+                             red[(2 * TRI_RG + r) * TRI_CB + c] + red[(3 * TRI_RG + r) * TRI_CB + c]);
+            }
+            __syncthreads();
+        }
+        for (int r = 0; r < nr; r++) {
+            double acc = 0;
+#pragma unroll
+            for (int m = 0; m < NP; m++) acc += dv[m] * (double)tv[r * TRI_CB + part + 4 * m];
+            red[(part * TRI_RG + r) * TRI_CB + col] = acc;
+        }
+        __syncthreads();
+        for (int q = tid; q < nr * TRI_CB; q += blockDim.x) {
+            const int r = q / TRI_CB, c = q - r * TRI_CB;
+            if (c < nb)
+                v[(int64_t)(g0 + r) * wsn + b0 + c] =
+                    (T)(red[(0 * TRI_RG + r) * TRI_CB + c] + red[(1 * TRI_RG + r) * TRI_CB + c] +
+                        red[(2 * TRI_RG + r) * TRI_CB + c] + red[(3 * TRI_RG + r) * TRI_CB + c]);
+        }
+    }
+}
+
+// Set-up: invert the diagonal blocks of the factors (FP64, column-parallel substitution in
+// shared memory; thread j computes column j of L_bb^{-1}).  One CTA per (block, system).
+__global__ void __launch_bounds__(TRI_CB) k_tri_inv(const int64_t *Optr, const double *Lp, const int64_t *Loff,
+                                                    const int64_t *Doff, int cb, double *Dinv, int64_t y0) {
+    __shared__ double Ls[TRI_CB * (TRI_CB + 1) / 2];   // L_bb, packed lower row-major
+    __shared__ double X[TRI_CB * (TRI_CB + 1) / 2];    // L_bb^{-1}, packed lower column-major
+    __shared__ double rd[TRI_CB];
+    const int64_t a = y0 + blockIdx.y;
+    const int n = (int)(Optr[a + 1] - Optr[a]);
+    const int b0 = (int)blockIdx.x * cb;
+    if (b0 >= n) return;
+    const int nb = min(cb, n - b0);
+    const double *L = Lp + Loff[a];
+    const int tot = nb * (nb + 1) / 2;
+    for (int q = threadIdx.x; q < tot; q += blockDim.x) {
+        int i = (int)((sqrt(8.0 * q + 1.0) - 1.0) * 0.5);
+        while ((i + 1) * (i + 2) / 2 <= q) i++;
+        while (i * (i + 1) / 2 > q) i--;
+        const int j = q - i * (i + 1) / 2;
+        const int64_t gi = (int64_t)b0 + i;
+        Ls[q] = L[gi * (gi + 1) / 2 + b0 + j];
+    }
+    __syncthreads();
+    const int j = threadIdx.x;
+    if (j < nb) rd[j] = 1.0 / Ls[j * (j + 1) / 2 + j];
+    __syncthreads();
+    if (j < nb) {
+        double *xj = X + j * nb - j * (j - 1) / 2 - j;   // xj[i] = X(i, j), i >= j
+        for (int i = j; i < nb; i++) {
+            const double *li = Ls + i * (i + 1) / 2;
+            double s = (i == j) ? 1.0 : 0.0;
+            for (int m = j; m < i; m++) s -= li[m] * xj[m];
+            xj[i] = s * rd[i];
+        }
+    }
+    __syncthreads();
+    double *D = Dinv + Doff[a] + (int64_t)blockIdx.x * tri_block_words(cb);
+    for (int q = threadIdx.x; q < tot; q += blockDim.x) {
+        int i = (int)((sqrt(8.0 * q + 1.0) - 1.0) * 0.5);
+        while ((i + 1) * (i + 2) / 2 <= q) i++;
+        while (i * (i + 1) / 2 > q) i--;
+        const int jj = q - i * (i + 1) / 2;
+        D[q] = X[jj * nb - jj * (jj - 1) / 2 + (i - jj)];
     }
 }
 
@@ -324,123 +576,6 @@ __global__ void k_sw_addx(const int32_t *aggs, const int64_t *Optr, const int32_
     for (int r = 0; r < nrhs; r++)
         for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nO; i += (int64_t)gridDim.x * blockDim.x)
             x[(int64_t)r * n + Oidx[ob + i]] += ws[(int64_t)r * wsn + ob + i];
-}
-
-template <class T>
-__global__ void __launch_bounds__(256) k_sw_fwd_diag(const int32_t *aggs, const int64_t *Optr, const T *Lp,
-                                                     const int64_t *Loff, int r0, T *ws, int64_t wsn, int nrhs) {
-    __shared__ T red[32];
-    const int32_t a = aggs[blockIdx.x];
-    const int n = (int)(Optr[a + 1] - Optr[a]);
-    if (r0 >= n) return;
-    const int r1 = min(n, r0 + CB);
-    const T *L = Lp + Loff[a];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    for (int r = 0; r < nrhs; r++) {
-        T *vr = ws + (int64_t)r * wsn + Optr[a];
-        for (int b0 = r0; b0 < r1; b0 += 32) {
-            const int rs = min(32, r1 - b0);
-            for (int i = warp; i < rs; i += nwarp) {
-                const T *row = L + (int64_t)(b0 + i) * (b0 + i + 1) / 2;
-                T sacc = 0;
-                for (int j = r0 + lane; j < b0; j += 32) sacc += row[j] * vr[j];
-                sacc = warp_sum(sacc);
-                if (lane == 0) red[i] = vr[b0 + i] - sacc;
-            }
-            __syncthreads();
-            if (warp == 0) {
-                T yl = 0;
-                for (int i = 0; i < rs; i++) {
-                    const T *row = L + (int64_t)(b0 + i) * (b0 + i + 1) / 2 + b0;
-                    T c = (lane < i) ? row[lane] * yl : (T)0;
-                    c = warp_sum(c);
-                    T yi = (red[i] - c) / row[i];
-                    if (lane == i) yl = yi;
-                }
-                if (lane < rs) vr[b0 + lane] = yl;
-            }
-            __syncthreads();
-        }
-    }
-}
-
-template <class T>
-__global__ void __launch_bounds__(256) k_sw_fwd_update(const int32_t *aggs, const int64_t *Optr, const T *Lp,
-                                                       const int64_t *Loff, int r0, T *ws, int64_t wsn, int nrhs) {
-    const int32_t a = aggs[blockIdx.y];
-    const int n = (int)(Optr[a + 1] - Optr[a]);
-    const int r1 = min(n, r0 + CB);
-    if (r1 >= n) return;
-    const T *L = Lp + Loff[a];
-    const int lane = threadIdx.x & 31;
-    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int r = 0; r < nrhs; r++) {
-        T *vr = ws + (int64_t)r * wsn + Optr[a];
-        for (int64_t i = r1 + wid; i < n; i += nw) {
-            const T *row = L + i * (i + 1) / 2;
-            T sacc = 0;
-            for (int j = r0 + lane; j < r1; j += 32) sacc += row[j] * vr[j];
-            sacc = warp_sum(sacc);
-            if (lane == 0) vr[i] -= sacc;
-        }
-    }
-}
-
-template <class T>
-__global__ void __launch_bounds__(256) k_sw_bwd_diag(const int32_t *aggs, const int64_t *Optr, const T *Lp,
-                                                     const int64_t *Loff, int r1g, T *ws, int64_t wsn, int nrhs) {
-    const int32_t a = aggs[blockIdx.x];
-    const int n = (int)(Optr[a + 1] - Optr[a]);
-    // aligned block [r1g - CB, r1g) clipped to this subdomain
-    const int r0 = max(0, r1g - CB);
-    if (r0 >= n) return;
-    const int r1 = min(r1g, n);
-    const T *L = Lp + Loff[a];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int r = 0; r < nrhs; r++) {
-        T *vr = ws + (int64_t)r * wsn + Optr[a];
-        const int nb = (r1 - r0 + 31) / 32;
-        for (int bi = nb - 1; bi >= 0; bi--) {
-            const int b0 = r0 + bi * 32, rs = min(32, r1 - b0);
-            if (warp == 0) {
-                T xl = (lane < rs) ? vr[b0 + lane] : (T)0;
-                for (int i = rs - 1; i >= 0; i--) {
-                    const T *row = L + (int64_t)(b0 + i) * (b0 + i + 1) / 2 + b0;
-                    T xi = __shfl_sync(0xffffffffu, xl, i) / row[i];
-                    if (lane == i) xl = xi;
-                    if (lane < i) xl -= row[lane] * xi;
-                }
-                if (lane < rs) vr[b0 + lane] = xl;
-            }
-            __syncthreads();
-            for (int j = r0 + threadIdx.x; j < b0; j += blockDim.x) {
-                T sacc = 0;
-                for (int i = 0; i < rs; i++) sacc += L[(int64_t)(b0 + i) * (b0 + i + 1) / 2 + j] * vr[b0 + i];
-                vr[j] -= sacc;
-            }
-            __syncthreads();
-        }
-    }
-}
-
-template <class T>
-__global__ void __launch_bounds__(256) k_sw_bwd_update(const int32_t *aggs, const int64_t *Optr, const T *Lp,
-                                                       const int64_t *Loff, int r1g, T *ws, int64_t wsn, int nrhs) {
-    const int32_t a = aggs[blockIdx.y];
-    const int n = (int)(Optr[a + 1] - Optr[a]);
-    const int r0 = max(0, r1g - CB);
-    if (r0 >= n) return;
-    const int r1 = min(r1g, n);
-    const T *L = Lp + Loff[a];
-    for (int r = 0; r < nrhs; r++) {
-        T *vr = ws + (int64_t)r * wsn + Optr[a];
-        for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < r0; j += (int64_t)gridDim.x * blockDim.x) {
-            T sacc = 0;
-            for (int i = r0; i < r1; i++) sacc += L[(int64_t)i * (i + 1) / 2 + j] * vr[i];
-            vr[j] -= sacc;
-        }
-    }
 }
 
 // residual update res -= G_T^T G_T delta_T, one CTA per (subdomain, element meeting Omega) pair
@@ -485,13 +620,6 @@ __global__ void __launch_bounds__(128) k_sw_scatter(const int32_t *pa, const int
             __syncthreads();
         }
     }
-}
-
-template <class T>
-__global__ void __launch_bounds__(1024) k_coarse_solve(const T *L, int n, T *v, int64_t stride,
-                                                       int nrhs) {
-    __shared__ T red[32];
-    for (int r = blockIdx.x; r < nrhs; r += gridDim.x) chol_solve_packed<T>(L, n, v + r * stride, red);
 }
 
 template <class T>
@@ -629,6 +757,54 @@ static T *wsvec(Level &L) {
     if constexpr (std::is_same<T, float>::value) return L.ws32.p; else return L.ws64.p;
 }
 
+// L L^T v = v for systems sys[0..nsys) (sys == nullptr: systems 0..nsys-1) whose vectors sit at
+// ws + Optr[a] (stride wsn per right-hand side), factors at Lp + Loff[a] and inverted diagonal
+// blocks at Dp + Doff[a]; maxn bounds the systems' orders, cb is the block size of Dp.
+template <class T>
+static void tri_solve(const int32_t *sys, int64_t nsys, const int64_t *Optr, const T *Lp,
+                      const int64_t *Loff, const double *Dp, const int64_t *Doff, int cb, int maxn, T *ws,
+                      int64_t wsn, int nrhs, cudaStream_t s) {
+    const int K = (maxn + cb - 1) / cb;
+    for (int64_t y0 = 0; y0 < nsys; y0 += 65535) {
+        const unsigned ny = (unsigned)std::min<int64_t>(65535, nsys - y0);
+        if (!sys && y0 > 0) fail(LSAMG_LIMIT, "more than 65535 systems without an index list");
+        const int32_t *sy = sys ? sys + y0 : nullptr;
+        for (int k = -1; k <= K - 2; k++) {
+            const int64_t rest = (int64_t)maxn - (int64_t)(k + 2) * cb;
+            const unsigned gx = 1 + (unsigned)(k >= 0 && rest > 0 ? cdiv(rest, TRI_ROWS) : 0);
+            k_tri_fwd<T><<<dim3(gx, ny), 256, 0, s>>>(sy, Optr, Lp, Loff, Dp, Doff, k, cb, ws, wsn, nrhs);
+            CK_LAUNCH();
+        }
+        for (int k = K; k >= 1; k--) {
+            const int64_t cols = (int64_t)(k - 1) * cb;
+            const unsigned gx = 1 + (unsigned)(k < K && cols > 0 ? cdiv(cols, TRI_COLS) : 0);
+            k_tri_bwd<T><<<dim3(gx, ny), 256, 0, s>>>(sy, Optr, Lp, Loff, Dp, Doff, k, cb, ws, wsn, nrhs);
+            CK_LAUNCH();
+        }
+    }
+}
+
+void tri_inverse_setup(int64_t nsys, const int64_t *Optr, const std::vector<int32_t> &h_n, const double *L64,
+                       const int64_t *Loff, int cb, DBuf<int64_t> &Doff, DBuf<double> &D64, cudaStream_t s) {
+    if (cb < 1 || cb > TRI_CB) fail(LSAMG_INVALID_ARG, "triangular block size out of range");
+    std::vector<int64_t> off(nsys + 1, 0);
+    int maxn = 0;
+    for (int64_t a = 0; a < nsys; a++) {
+        off[a + 1] = off[a] + (int64_t)((h_n[a] + cb - 1) / cb) * tri_block_words(cb);
+        maxn = std::max(maxn, h_n[a]);
+    }
+    upload(Doff, off, s);
+    D64.alloc(std::max<int64_t>(off[nsys], 1), s);
+    const int K = (maxn + cb - 1) / cb;
+    for (int64_t y0 = 0; y0 < nsys && K > 0; y0 += 65535) {
+        const unsigned ny = (unsigned)std::min<int64_t>(65535, nsys - y0);
+        k_tri_inv<<<dim3((unsigned)K, ny), TRI_CB, 0, s>>>(Optr, L64, Loff, Doff.p, cb, D64.p, y0);
+        CK_LAUNCH();
+    }
+}
+
+// one colour of the sweep with many CTAs per subdomain: gather r_Omega, blocked solves with the
+// Cholesky factor of A_Omega, x_Omega += delta, residual update through the element factors
 template <class T>
 static void sweep_split(Level &L, int c, int nrhs, cudaStream_t s) {
     const int64_t na = L.colptr[c + 1] - L.colptr[c];
@@ -647,29 +823,7 @@ static void sweep_split(Level &L, int c, int nrhs, cudaStream_t s) {
     dim3 gg((unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv(maxn, 256), 64)), (unsigned)na);
     k_sw_gather<T><<<gg, 256, 0, s>>>(aggs, L.Optr.p, L.Oidx.p, rvec<T>(L), ws, L.n, L.Omega_total, nrhs);
     CK_LAUNCH();
-    for (int r0 = 0; r0 < maxn; r0 += CB) {
-        k_sw_fwd_diag<T><<<(unsigned)na, 256, 0, s>>>(aggs, L.Optr.p, Lp, L.Loff.p, r0, ws, L.Omega_total, nrhs);
-        CK_LAUNCH();
-        if (r0 + CB < maxn) {
-            dim3 g((unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv((int64_t)(maxn - r0 - CB) * 32, 256), 256)), (unsigned)na);
-            k_sw_fwd_update<T><<<g, 256, 0, s>>>(aggs, L.Optr.p, Lp, L.Loff.p, r0, ws, L.Omega_total, nrhs);
-            CK_LAUNCH();
-        }
-    }
-    // backward: every subdomain walks its own blocks from its end; blocks are aligned to the
-    // forward partition (multiples of CB from the start), so r1 runs over CB-multiples and the
-    // subdomain's own n
-    std::vector<int> ends;
-    for (int r1 = ((maxn + CB - 1) / CB) * CB; r1 > 0; r1 -= CB) ends.push_back(r1);
-    for (int r1 : ends) {
-        // subdomains whose size is not a multiple of CB treat their last partial block when
-        // r1 is the first CB-multiple >= n: pass r1 and let each use min(r1, n)
-        k_sw_bwd_diag<T><<<(unsigned)na, 256, 0, s>>>(aggs, L.Optr.p, Lp, L.Loff.p, r1, ws, L.Omega_total, nrhs);
-        CK_LAUNCH();
-        dim3 g((unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv(std::max(r1 - CB, 1), 256), 256)), (unsigned)na);
-        k_sw_bwd_update<T><<<g, 256, 0, s>>>(aggs, L.Optr.p, Lp, L.Loff.p, r1, ws, L.Omega_total, nrhs);
-        CK_LAUNCH();
-    }
+    tri_solve<T>(aggs, na, L.Optr.p, Lp, L.Loff.p, L.Di64.p, L.Doff.p, L.tri_cb, maxn, ws, L.Omega_total, nrhs, s);
     k_sw_addx<T><<<gg, 256, 0, s>>>(aggs, L.Optr.p, L.Oidx.p, ws, xvec<T>(L), L.n, L.Omega_total, nrhs);
     CK_LAUNCH();
     const int64_t np = L.colpairs[c + 1] - L.colpairs[c];
@@ -720,33 +874,8 @@ void vcycle(Handle &H, int l, int nrhs, cudaStream_t s) {
         CK(cudaMemcpyAsync(x, b, tot * sizeof(T), cudaMemcpyDeviceToDevice, s));
         const T *Ld;
         if constexpr (std::is_same<T, float>::value) Ld = L.Ld32.p; else Ld = L.Ld64.p;
-        const int n = (int)L.n;
         KTime kt(KC_COARSE_SOLVE, s, 0.0, L.coarse_bytes[std::is_same<T, double>::value ? 1 : 0] * nrhs);
-        if (n <= 2 * CB) {
-            k_coarse_solve<T><<<(unsigned)nrhs, 1024, 0, s>>>(Ld, n, x, L.n, nrhs);
-            CK_LAUNCH();
-            return;
-        }
-        for (int r0 = 0; r0 < n; r0 += CB) {
-            const int r1 = std::min(n, r0 + CB);
-            k_cs_fwd_diag<T><<<(unsigned)nrhs, 256, 0, s>>>(Ld, r0, r1, x, L.n);
-            CK_LAUNCH();
-            if (r1 < n) {
-                dim3 g((unsigned)std::min<int64_t>(cdiv((int64_t)(n - r1) * 32, 256), 148 * 8), (unsigned)nrhs);
-                k_cs_fwd_update<T><<<g, 256, 0, s>>>(Ld, r0, r1, n, x, L.n);
-                CK_LAUNCH();
-            }
-        }
-        for (int r1 = n; r1 > 0; r1 -= CB) {
-            const int r0 = std::max(0, r1 - CB);
-            k_cs_bwd_diag<T><<<(unsigned)nrhs, 256, 0, s>>>(Ld, r0, r1, x, L.n);
-            CK_LAUNCH();
-            if (r0 > 0) {
-                dim3 g((unsigned)std::min<int64_t>(cdiv(r0, 256), 148 * 8), (unsigned)nrhs);
-                k_cs_bwd_update<T><<<g, 256, 0, s>>>(Ld, r0, r1, x, L.n);
-                CK_LAUNCH();
-            }
-        }
+        tri_solve<T>(nullptr, 1, L.cs_ptr.p, Ld, L.cs_off.p, L.Di64.p, L.Doff.p, L.tri_cb, (int)L.n, x, L.n, nrhs, s);
         return;
     }
     Level &C = H.levels[l + 1];
@@ -760,7 +889,7 @@ void vcycle(Handle &H, int l, int nrhs, cudaStream_t s) {
     if constexpr (std::is_same<T, float>::value) Z = L.Z32.p; else Z = L.Z64.p;
     {
     KTime kt(KC_TRANSFER, s);
-    k_restrict<T><<<gridv(L.nagg, 1, 148 * 16), 128, 0, s>>>(L.wptr.p, L.widx.p, L.k.p, L.off.p, Z,
+    k_restrict<T><<<gridv(L.nagg, 1, 148 * 16), 256, 0, s>>>(L.wptr.p, L.widx.p, L.k.p, L.off.p, Z,
                                                             L.zoff.p, L.nagg, r, L.n, bvec<T>(C),
                                                             C.n, nrhs);
     CK_LAUNCH();
@@ -768,7 +897,12 @@ void vcycle(Handle &H, int l, int nrhs, cudaStream_t s) {
     vcycle<T>(H, l + 1, nrhs, s);
     {
     KTime kt(KC_TRANSFER, s);
-    k_interp<T><<<gridv(L.nagg, 1, 148 * 16), 256, 0, s>>>(L.wptr.p, L.widx.p, L.k.p, L.off.p, Z,
+    const size_t ism = (size_t)std::max(1, L.max_k) * sizeof(T);
+    if (ism > 48 * 1024) {
+        if (ism > 227 * 1024) fail(LSAMG_LIMIT, "coarse block too large for the interpolation kernel");
+        CK(cudaFuncSetAttribute(k_interp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism));
+    }
+    k_interp<T><<<gridv(L.nagg, 1, 148 * 16), 256, ism, s>>>(L.wptr.p, L.widx.p, L.k.p, L.off.p, Z,
                                                           L.zoff.p, L.nagg, xvec<T>(C), C.n, x,
                                                           L.n, nrhs);
     CK_LAUNCH();

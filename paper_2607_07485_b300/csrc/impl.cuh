@@ -54,6 +54,7 @@ struct Level {
     DBuf<double> Z64;
     DBuf<float> Z32;
     std::vector<int32_t> h_k;
+    int32_t max_k = 0;                 // largest k_i (shared-memory staging of the interpolation)
     std::vector<double> h_gap;
     DBuf<int32_t> cgroup;   // [ne] coarse element of each element (-1 if none)
     // multiplicative Schwarz smoother
@@ -68,6 +69,12 @@ struct Level {
     bool coarsest = false;
     DBuf<double> Ld64;
     DBuf<float> Ld32;
+    DBuf<int64_t> cs_ptr, cs_off;   // {0, n} and {0}: the coarsest matrix as one blocked system
+    // inverted diagonal blocks of the Schwarz (or coarsest) factors for the blocked triangular
+    // solves: block b of system a at Doff[a] + b tri_cb(tri_cb+1)/2, packed lower row-major
+    int32_t tri_cb = 64;
+    DBuf<int64_t> Doff;
+    DBuf<double> Di64;
     // cycle workspaces (allocated for nrhs_ws right-hand sides)
     int32_t nrhs_ws = 0;
     int32_t max_grows_cached = 0;   // largest G_T row count (shared-memory staging size)
@@ -119,6 +126,9 @@ void local_spectral(Level &L, const lsamg_options &o, int *err, cudaStream_t s, 
 void build_coarse(Level &fine, Level &coarse, int *err, cudaStream_t s, double *flops);
 void smoother_setup(Level &L, const lsamg_options &o, int *err, cudaStream_t s, double *flops);
 void coarsest_setup(Level &L, int *err, cudaStream_t s, double *flops);
+// invert the diagonal blocks (tri_cb rows) of nsys packed factors; h_n: host orders of the systems
+void tri_inverse_setup(int64_t nsys, const int64_t *Optr, const std::vector<int32_t> &h_n, const double *L64,
+                       const int64_t *Loff, int cb, DBuf<int64_t> &Doff, DBuf<double> &D64, cudaStream_t s);
 
 // ------------------------------------------------------------------- cycle.cu
 void ensure_cycle_ws(Level &L, int nrhs, cudaStream_t s);

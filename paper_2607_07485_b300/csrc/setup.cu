@@ -748,6 +748,7 @@ void local_spectral(Level &L, const lsamg_options &o, int *err, cudaStream_t s, 
     upload(L.zoff, zoff, s);
     upload(L.off, off, s);
     upload(L.k, L.h_k, s);
+    L.max_k = L.h_k.empty() ? 0 : *std::max_element(L.h_k.begin(), L.h_k.end());
     L.Z64.alloc(std::max<int64_t>(zoff[nagg], 1), s);
     L.Z32.alloc(std::max<int64_t>(zoff[nagg], 1), s);
     for (auto &ch : chunks) {
@@ -1028,6 +1029,9 @@ void smoother_setup(Level &L, const lsamg_options &o, int *err, cudaStream_t s, 
         check_err(err, s, "Schwarz factors");
         a0 = a1;
     }
+    L.tri_cb = g_sweep_block > 0 ? std::min(g_sweep_block, 64) : 64;
+    tri_inverse_setup(nagg, L.Optr.p, L.h_nO, L.L64.p, L.Loff.p, L.tri_cb, L.Doff, L.Di64, s);
+    CK(cudaStreamSynchronize(s));
 }
 
 void coarsest_setup(Level &L, int *err, cudaStream_t s, double *flops) {
@@ -1054,6 +1058,11 @@ void coarsest_setup(Level &L, int *err, cudaStream_t s, double *flops) {
     dim3 g((unsigned)std::min<int64_t>(cdiv(tot, 256), 148 * 8), 1);
     k_pack_lower<<<g, 256, 0, s>>>(D.p, z.p, nn.p, 1, L.Ld64.p, L.Ld32.p, z.p);
     CK_LAUNCH();
+    upload(L.cs_ptr, std::vector<int64_t>{0, n}, s);
+    upload(L.cs_off, std::vector<int64_t>{0}, s);
+    L.tri_cb = g_sweep_block > 0 ? std::min(g_sweep_block, 64) : 64;
+    tri_inverse_setup(1, L.cs_ptr.p, std::vector<int32_t>{(int32_t)n}, L.Ld64.p, L.cs_off.p, L.tri_cb, L.Doff,
+                      L.Di64, s);
     CK(cudaStreamSynchronize(s));
     check_err(err, s, "coarsest factorisation");
 }
