@@ -1295,7 +1295,8 @@ void ormtr_batched(const double *base_A, const MatBatch &Ab, const double *tau, 
                    double *base_V, const MatBatch &Vb, cudaStream_t s) {
     if (Vb.count == 0 || Vb.maxm == 0) return;
     double fl = 0.0;
-    for (size_t i = 0; i < Vb.h_n.size(); i++) fl += 4.0 * Vb.h_n[i] * Vb.h_n[i] * Vb.h_m[i];
+    // n - 1 reflectors of lengths n-1 ... 1, each applied to m vectors at 4 flops per entry
+    for (size_t i = 0; i < Vb.h_n.size(); i++) fl += 2.0 * Vb.h_n[i] * Vb.h_n[i] * Vb.h_m[i];
     KTime kt(KC_ORMTR, s, fl);
     dim3 g((unsigned)cdiv(Vb.maxm, 8), (unsigned)Vb.count);
     k_ormtr<<<g, 256, 0, s>>>(base_A, Ab.off.p, Ab.ld.p, Ab.n.p, tau, toff, base_V, Vb.off.p,
