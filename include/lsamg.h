@@ -179,6 +179,25 @@ int lsamg_kernel_stats_all(double *out);
 /* Number of CUDA kernel launches the library has issued in this process. */
 int64_t lsamg_launch_count(void);
 
+/* Allocation-free Gram SpMV.  The paper has no counterpart: this is an engineering variant of
+ * the Gram SpMV of eq. 2.1 / Prop. 5.1 for callers that cannot allocate device memory.
+ *   y = sum_T R_T^T G_T^T (G_T x_T)
+ * from element factors the caller holds; no handle, no cudaMalloc, cudaFree or allocating
+ * library routine.  The intermediate G_T x_T lives in a file-scope static device array of
+ * LSAMG_STATIC_SCRATCH_WORDS doubles (8 MiB per device; the first 32 words are a header).
+ *   elem_dofs : device int32 [n_elems][n_T], 0-based DOF ids
+ *   G         : device float64 [n_elems][m][n_T] row-major, m rows per element (zero rows allowed)
+ *   x, y      : device float64 [n_dofs]; y is overwritten
+ * Returns LSAMG_LIMIT, launching nothing, if n_elems * m > LSAMG_STATIC_SCRATCH_WORDS - 32, and
+ * LSAMG_INVALID_ARG for bad sizes or a DOF id outside [0, n_dofs) (out-of-range entries are
+ * skipped, not read).  Synchronises `stream` before returning.  Every call on a device shares
+ * the one scratch array: calls that overlap on the GPU (other streams, other host threads)
+ * race and must be serialised by the caller. */
+#define LSAMG_STATIC_SCRATCH_WORDS (1 << 20)
+int lsamg_gram_spmv_static(int64_t n_dofs, int64_t n_elems, int32_t n_T, int32_t m,
+                           const int32_t *elem_dofs, const double *G, const double *x, double *y,
+                           void *stream);
+
 void lsamg_destroy(lsamg_handle *h);
 const char *lsamg_last_error(void);
 

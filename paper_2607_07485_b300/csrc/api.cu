@@ -33,6 +33,12 @@ int guarded(F &&f) {
     }
 }
 
+}  // namespace
+
+void set_last_error(const std::string &msg) { g_last_error = msg; }
+
+namespace {
+
 double now() {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }

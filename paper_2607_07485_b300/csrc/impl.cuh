@@ -126,6 +126,8 @@ void local_spectral(Level &L, const lsamg_options &o, int *err, cudaStream_t s, 
 void build_coarse(Level &fine, Level &coarse, int *err, cudaStream_t s, double *flops);
 void smoother_setup(Level &L, const lsamg_options &o, int *err, cudaStream_t s, double *flops);
 void coarsest_setup(Level &L, int *err, cudaStream_t s, double *flops);
+// thread-local message returned by lsamg_last_error
+void set_last_error(const std::string &msg);
 // invert the diagonal blocks (tri_cb rows) of nsys packed factors; h_n: host orders of the systems
 void tri_inverse_setup(int64_t nsys, const int64_t *Optr, const std::vector<int32_t> &h_n, const double *L64,
                        const int64_t *Loff, int cb, DBuf<int64_t> &Doff, DBuf<double> &D64, cudaStream_t s);

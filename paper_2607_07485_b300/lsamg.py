@@ -72,6 +72,8 @@ _lib.lsamg_stage_name.restype = C.c_char_p
 _lib.lsamg_stage_name.argtypes = [C.c_int32]
 _lib.lsamg_query.argtypes = [_H, C.c_int32, C.c_int32, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]
 _lib.lsamg_destroy.argtypes = [_H]
+_lib.lsamg_gram_spmv_static.argtypes = [C.c_int64, C.c_int64, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
+                                        C.c_void_p, C.c_void_p, C.c_void_p]
 _lib.lsamg_last_error.restype = C.c_char_p
 _lib.lsamg_kernel_classes.restype = C.c_int32
 _lib.lsamg_kernel_name.restype = C.c_char_p
@@ -82,7 +84,7 @@ _lib.lsamg_launch_count.restype = C.c_int64
 EXPORTS = ["lsamg_options_default", "lsamg_setup", "lsamg_apply", "lsamg_solve", "lsamg_solve_host",
            "lsamg_gram_spmv", "lsamg_elem_grad", "lsamg_get_stats", "lsamg_stage_name", "lsamg_query",
            "lsamg_destroy", "lsamg_last_error", "lsamg_kernel_classes", "lsamg_kernel_name",
-           "lsamg_kernel_stats_all", "lsamg_launch_count"]
+           "lsamg_kernel_stats_all", "lsamg_launch_count", "lsamg_gram_spmv_static"]
 
 
 def kernel_stats():
@@ -96,6 +98,17 @@ def kernel_stats():
         if calls:
             out[_lib.lsamg_kernel_name(c).decode()] = dict(ms=ms, calls=int(calls), flops=fl, bytes=by)
     return out
+
+
+def gram_spmv_static(elem_dofs, G, x, y, stream=None):
+    """y = sum_T R_T^T G_T^T (G_T x_T) through the allocation-free entry point (no handle).
+    elem_dofs: int32 [ne, nT], G: float64 [ne, m, nT], x, y: float64 [n] device tensors (y is
+    overwritten; nothing is allocated here or in the library)."""
+    ne, nT = elem_dofs.shape
+    m = G.shape[1] if G.dim() == 3 else 0
+    _check(_lib.lsamg_gram_spmv_static(int(x.numel()), int(ne), int(nT), int(m), _ptr(elem_dofs), _ptr(G),
+                                       _ptr(x), _ptr(y), _stream(stream)))
+    return y
 
 
 def launch_count():
