@@ -120,6 +120,13 @@ __global__ void k_elem_factor(const double *AT, const int64_t *aoff, const int32
     }
 }
 
+// CTAs per aggregate for the dense assemblies: one while the batch fills the GPU, more (each
+// taking an interleaved slice of the elements, with atomic adds) when it has few aggregates
+static int assembly_slices(int64_t na) {
+    const int64_t want = (148 * 4 + na - 1) / std::max<int64_t>(na, 1);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(want, 16));
+}
+
 // ---------------------------------------------------------------- local problem assembly
 // At (omega-first, column-major |Omega| x |Omega|) += A_T / mult(T) and Aww += A_T on
 // omega x omega, over the elements touching omega_i (eqs. 2.6-2.9).
@@ -128,7 +135,7 @@ __global__ void k_assemble_gep(const int32_t *alist, int64_t na, const int64_t *
                                const int64_t *aoff, const int32_t *mult, const int64_t *Optr,
                                const int32_t *Oidx, const int32_t *Olpos, const int64_t *wptr,
                                double *At, const int64_t *atoff, double *Aww,
-                               const int64_t *awoff) {
+                               const int64_t *awoff, int es) {
     extern __shared__ int32_t pos[];
     int64_t li = blockIdx.x;
     if (li >= na) return;
@@ -139,7 +146,8 @@ __global__ void k_assemble_gep(const int32_t *alist, int64_t na, const int64_t *
     int nw = (int)(wptr[a + 1] - wptr[a]);
     double *T1 = At + atoff[li];
     double *T2 = Aww + awoff[li];
-    for (int64_t j = aeptr[a]; j < aeptr[a + 1]; j++) {
+    // es CTAs per aggregate take interleaved element slices (atomics when es > 1)
+    for (int64_t j = aeptr[a] + blockIdx.y; j < aeptr[a + 1]; j += es) {
         int32_t e = aeidx[j];
         int64_t b = eptr[e];
         int n = (int)(eptr[e + 1] - b);
@@ -151,8 +159,13 @@ __global__ void k_assemble_gep(const int32_t *alist, int64_t na, const int64_t *
             int r = t / n, c = t % n;
             double v = Ae[t];
             int pr = pos[r], pc = pos[c];
-            T1[pr + (int64_t)pc * nO] += w * v;
-            if (pr < nw && pc < nw) T2[pr + (int64_t)pc * nw] += v;
+            if (es > 1) {
+                atomicAdd(&T1[pr + (int64_t)pc * nO], w * v);
+                if (pr < nw && pc < nw) atomicAdd(&T2[pr + (int64_t)pc * nw], v);
+            } else {
+                T1[pr + (int64_t)pc * nO] += w * v;
+                if (pr < nw && pc < nw) T2[pr + (int64_t)pc * nw] += v;
+            }
         }
         __syncthreads();
     }
@@ -162,13 +175,14 @@ __global__ void k_assemble_gep(const int32_t *alist, int64_t na, const int64_t *
 __global__ void k_assemble_smoother(int64_t a0, int64_t na, const int64_t *oeptr,
                                     const int32_t *oeidx, const int64_t *eptr, const double *AT,
                                     const int64_t *aoff, const int64_t *locoff, const int32_t *loc,
-                                    const int64_t *Optr, double *AO, const int64_t *ooff) {
+                                    const int64_t *Optr, double *AO, const int64_t *ooff, int es) {
     int64_t li = blockIdx.x;
     if (li >= na) return;
     int64_t a = a0 + li;
     int64_t nO = Optr[a + 1] - Optr[a];
     double *M = AO + ooff[li];
-    for (int64_t j = oeptr[a]; j < oeptr[a + 1]; j++) {
+    // es CTAs per subdomain take interleaved element slices (atomics when es > 1)
+    for (int64_t j = oeptr[a] + blockIdx.y; j < oeptr[a + 1]; j += es) {
         int32_t e = oeidx[j];
         int n = (int)(eptr[e + 1] - eptr[e]);
         const int32_t *p = loc + locoff[j];
@@ -176,7 +190,10 @@ __global__ void k_assemble_smoother(int64_t a0, int64_t na, const int64_t *oeptr
         for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
             int r = t / n, c = t % n;
             int pr = p[r], pc = p[c];
-            if (pr >= 0 && pc >= 0) M[pr + (int64_t)pc * nO] += Ae[t];
+            if (pr >= 0 && pc >= 0) {
+                if (es > 1) atomicAdd(&M[pr + (int64_t)pc * nO], Ae[t]);
+                else M[pr + (int64_t)pc * nO] += Ae[t];
+            }
         }
         __syncthreads();
     }
@@ -632,9 +649,10 @@ void local_spectral(Level &L, const lsamg_options &o, int *err, cudaStream_t s, 
         // 1. assemble At (omega-first) and A_ww
         { LSAMG_PROF(lvl_name(g_prof_level, "ls: assemble"), s);
         KTime kt(KC_ASSEMBLE, s);
-        k_assemble_gep<<<(unsigned)na, 256, maxE * sizeof(int32_t), s>>>(
+        const int es = assembly_slices(na);
+        k_assemble_gep<<<dim3((unsigned)na, (unsigned)es), 256, maxE * sizeof(int32_t), s>>>(
             dids.p, na, L.aeptr.p, L.aeidx.p, L.eptr.p, L.eidx.p, L.AT.p, L.aoff.p, L.mult.p, L.Optr.p,
-            L.Oidx.p, L.Olpos.p, L.wptr.p, At.p, datoff.p, Aww.p, dawoff.p);
+            L.Oidx.p, L.Olpos.p, L.wptr.p, At.p, datoff.p, Aww.p, dawoff.p, es);
         CK_LAUNCH(); }
         // 2. Schur complement S = At_ww - At_wG At_GG^+ At_Gw via a semidefinite Cholesky of At_GG
         MatBatch bGG, bGw, bww, bW, bAww, bV, bC, bY;
@@ -1013,11 +1031,14 @@ void smoother_setup(Level &L, const lsamg_options &o, int *err, cudaStream_t s, 
         upload(dmo, mo, s);
         upload(dpo, po, s);
         upload(dnn, nn, s);
-        KTime kta(KC_ASSEMBLE, s);
-        k_assemble_smoother<<<(unsigned)na, 256, 0, s>>>(a0, na, L.oeptr.p, L.oeidx.p, L.eptr.p,
-                                                          L.AT.p, L.aoff.p, L.oelocoff.p, L.oeloc.p,
-                                                          L.Optr.p, AO.p, dmo.p);
-        CK_LAUNCH();
+        {
+            KTime kta(KC_ASSEMBLE, s);
+            const int es = assembly_slices(na);
+            k_assemble_smoother<<<dim3((unsigned)na, (unsigned)es), 256, 0, s>>>(
+                a0, na, L.oeptr.p, L.oeidx.p, L.eptr.p, L.AT.p, L.aoff.p, L.oelocoff.p, L.oeloc.p, L.Optr.p,
+                AO.p, dmo.p, es);
+            CK_LAUNCH();
+        }
         MatBatch b;
         std::vector<int64_t> o1(mo.begin(), mo.end() - 1);
         b.set(o1, nn, nn, {}, s);
