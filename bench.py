@@ -39,6 +39,14 @@ WORKLOAD_N = 256
 # coarse levels and up to four levels (at 2.1M DOFs the paper's 3-level / 2-pass hierarchy
 # leaves a ~90k-DOF dense coarsest problem and ~9k-DOF local eigenproblems).
 BENCH_OPTS = dict(agg_passes=2, agg_passes_coarse=1, max_levels=4, maxit=400)
+L2_BYTES = 126e6
+
+
+def l2_note(c):
+    mb = c["elem_mats"].nbytes / 1e6
+    if mb * 1e6 > L2_BYTES:
+        return f"inputs larger than L2 (element blocks {mb:.0f} MB, read every step)"
+    return f"inputs smaller than L2 (element blocks {mb:.0f} MB), no flush: a reduced size, not the benchmark"
 FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12   # 148 SMs x 2 FP64 FMA/clk x 2 flop x 2032 MHz
 
 
@@ -118,6 +126,18 @@ def workload_name(c):
             f"{c['elem_dofs'].shape[0]:,} elements x 40 DOFs, theta_e=exp(N(0,1))")
 
 
+def max_over_ranks(value, device=None):
+    """Maximum of a per-rank number over the ranks of the default process group (the number
+    itself without one): the step time a replica run reports is its slowest rank's."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ----------------------------------------------------------------------------- CPU oracle leg
 def oracle_sample(n_full, N_sample=16):
     """The FP64 oracle on a bounded sample of the same workload (RT_[3] on an N_sample mesh):
@@ -166,7 +186,9 @@ def run_reference(args, rank):
     out = dict(metric=METRIC, value=val, unit="s", n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
                ms_per_step=1000 * val, higher_is_better=False, scaling="weak", vs_baseline=None,
                dtype="f64", data="synthetic", impl="reference",
-               config=dict(workload=workload_name(full), sample_dofs=info["n"]),
+               config=dict(workload=workload_name(full), n_dofs=n_full, solve_mode="pcg+fp64-vcycle",
+                           options=dict(BENCH_OPTS, tau_c=full["c_tau"]), l2=l2_note(full),
+                           parallelism=f"replicas x{args.gpus}", sample_dofs=info["n"]),
                cpu_baseline=dict(value=val, unit="s", cores=cpu_cores(), kind="oracle", sample=sample,
                                  raw_sample_s=statistics.mean(t[0] for t in times)),
                e2e=dict(value=val, unit="s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
@@ -253,10 +275,7 @@ def main():
     dev_ms = ev0.elapsed_time(ev1)
     ks = kernel_stats()
     per_step = dev_ms / 1000.0 / args.steps
-    if world > 1:
-        tt = torch.tensor([per_step], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        per_step = float(tt.item())
+    per_step = max_over_ranks(per_step, dev)
 
     # ---- end-to-end through the public API with host buffers (pinned), copies inside
     e2e = None
@@ -271,7 +290,7 @@ def main():
         xh, itsh, relh, rch = amg.solve_host(h_b, mode=best_mode)
         amg.close()
         torch.cuda.synchronize()
-        e2e_s = time.perf_counter() - te
+        e2e_s = max_over_ranks(time.perf_counter() - te, dev)
         e2e = dict(value=e2e_s, unit="s", h2d_bytes_per_step=int(h_dofs.nbytes + h_mats.nbytes + h_coef.nbytes + h_b.nbytes),
                    d2h_bytes_per_step=int(xh.nbytes), steps=1, iters=int(itsh[0]), converged=bool(rch == 0))
 
@@ -312,7 +331,7 @@ def main():
         ms_per_step=1000 * per_step, higher_is_better=False, scaling="weak", vs_baseline=None,
         dtype="f64 set-up / f32 V-cycle in f64 FCG" if best_mode == 1 else "f64", data="synthetic",
         config=dict(workload=workload_name(c), n_dofs=n, solve_mode="fcg+fp32-vcycle" if best_mode == 1 else "pcg+fp64-vcycle",
-                    options=opts, l2="inputs larger than L2 (element blocks 839 MB, read every step)",
+                    options=opts, l2=l2_note(c),
                     parallelism=f"replicas x{world}"),
         setup_s=statistics.mean(setups), solve_s=statistics.mean(solves), iters=its_list,
         warmup_modes={("fp32_vcycle_fcg" if m == 1 else "fp64_pcg"): v for m, v in modes.items()},
