@@ -443,13 +443,8 @@ __global__ void k_colour_unpack(const uint64_t *keys, int64_t nagg, int32_t *col
 }
 
 // ---------------------------------------------------------------- structural nnz
-// level 0: nnz = sum over DOFs of |union of N(T) for T containing the DOF|
-__global__ void k_count_i64_from_ptr(const int64_t *ptr, int64_t n, int64_t *cnt) {
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
-         r += (int64_t)gridDim.x * blockDim.x)
-        cnt[r] = ptr[r + 1] - ptr[r];
-}
-
+// (level 0: the row lengths of the DOF adjacency, computed by csr_union in
+// structural_nnz_level0)
 // coarse: nnz = sum_a k_a * sum_{b in nb(a)} k_b
 __global__ void k_block_nnz(const int64_t *nptr, const int32_t *nidx, int64_t nagg,
                             const int32_t *k, int64_t *out) {

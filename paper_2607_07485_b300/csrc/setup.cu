@@ -904,8 +904,6 @@ void build_coarse(Level &F, Level &C, int *err, cudaStream_t s, double *flops) {
                     items.push_back((int32_t)a);
                     items.push_back((int32_t)b);
                 }
-            auto ep_e = 0;
-            (void)ep_e;
             *flops += 2.0 * fr[e] * ncol * (double)(F.max_nT > 0 ? F.max_nT : 0);
         }
         DBuf<int32_t> ditems;
@@ -973,9 +971,7 @@ void build_coarse(Level &F, Level &C, int *err, cudaStream_t s, double *flops) {
         auto hr = to_host(rank.p, ng, s);
         std::vector<int64_t> ngoff(ng + 1, 0);
         std::vector<int32_t> nrows(ng);
-        for (int64_t g = 0; g < ng; g++) {
-            nrows[g] = std::min<int32_t>(hr[g], (int32_t)hrows[g]);
-            if (hr[g] > hrows[g]) nrows[g] = hr[g];  // rank cannot exceed stacked rows in exact arithmetic
+        for (int64_t g = 0; g < ng; g++) {   // G_c of group g: its rank rows x its coarse columns
             ngoff[g + 1] = ngoff[g] + (int64_t)hr[g] * hcols[g];
             nrows[g] = hr[g];
         }
