@@ -180,19 +180,28 @@ int lsamg_kernel_stats_all(double *out);
 int64_t lsamg_launch_count(void);
 
 /* Allocation-free Gram SpMV.  The paper has no counterpart: this is an engineering variant of
- * the Gram SpMV of eq. 2.1 / Prop. 5.1 for callers that cannot allocate device memory.
- *   y = sum_T R_T^T G_T^T (G_T x_T)
- * from element factors the caller holds; no handle, no cudaMalloc, cudaFree or allocating
- * library routine.  The intermediate G_T x_T lives in a file-scope static device array of
- * LSAMG_STATIC_SCRATCH_WORDS doubles (8 MiB per device; the first 32 words are a header).
+ * the Gram SpMV of eq. 2.1 / Prop. 5.1,
+ *   y = sum_T R_T^T G_T^T (G_T x_T),
+ * computed from element factors the caller holds, with no handle.  It is meant for callers that
+ * must not allocate device memory: an application whose device memory is owned by another
+ * allocator (a framework's caching pool that has reserved the GPU, so a cudaMalloc from here
+ * would fail or fragment it), and code in latency-critical loops, where cudaMalloc / cudaFree
+ * would synchronise the device.  The call makes no cudaMalloc, cudaFree or allocating library
+ * call.  The intermediate G_T x_T lives instead in a file-scope static device array of
+ * LSAMG_STATIC_SCRATCH_WORDS doubles (8 MiB, held on every GPU that loads the library until
+ * the process exits; the first 32 words are a header).
  *   elem_dofs : device int32 [n_elems][n_T], 0-based DOF ids
  *   G         : device float64 [n_elems][m][n_T] row-major, m rows per element (zero rows allowed)
  *   x, y      : device float64 [n_dofs]; y is overwritten
  * Returns LSAMG_LIMIT, launching nothing, if n_elems * m > LSAMG_STATIC_SCRATCH_WORDS - 32, and
  * LSAMG_INVALID_ARG for bad sizes or a DOF id outside [0, n_dofs) (out-of-range entries are
- * skipped, not read).  Synchronises `stream` before returning.  Every call on a device shares
- * the one scratch array: calls that overlap on the GPU (other streams, other host threads)
- * race and must be serialised by the caller. */
+ * skipped, not read).  Synchronises `stream` before returning.
+ * The first call on each device looks up the array's device address (cudaGetSymbolAddress,
+ * with that device current); make that first call before any stream capture.  The array keeps
+ * the last call's contents; each call clears the part that must start at zero (the error
+ * flag) and overwrites the rest it reads.  Every call on a device shares the one array, so
+ * calls that overlap on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller. */
 #define LSAMG_STATIC_SCRATCH_WORDS (1 << 20)
 int lsamg_gram_spmv_static(int64_t n_dofs, int64_t n_elems, int32_t n_T, int32_t m,
                            const int32_t *elem_dofs, const double *G, const double *x, double *y,

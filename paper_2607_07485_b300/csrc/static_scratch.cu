@@ -1,9 +1,16 @@
 // Allocation-free element Gram SpMV, lsamg_gram_spmv_static (include/lsamg.h).  The paper has
 // no counterpart: it is an engineering variant of the Gram SpMV y = sum_T R_T^T G_T^T (G_T R_T x)
-// (Section 2 eq. 2.1, Prop. 5.1) for callers that cannot allocate device memory.  It reads the
+// (Section 2 eq. 2.1, Prop. 5.1) for callers that must not allocate device memory: applications
+// whose GPU memory belongs to another allocator (a framework's caching pool), and latency-
+// critical loops where cudaMalloc / cudaFree would synchronise the device.  It reads the
 // element factors from caller buffers and keeps the intermediate t_T = G_T x_T in one file-scope
 // device array instead of shared memory, so the call allocates nothing: no cudaMalloc, no
 // cudaFree and no allocating library routine.
+//
+// The array's name is only a host-side stand-in in host code: the first call on each device
+// looks up its device address with cudaGetSymbolAddress (that device current) and passes that
+// address to the kernels; that first call should come before any stream capture.  The array
+// keeps the previous call's contents; only the error flag must start at zero and is cleared.
 //
 // Scratch layout (per device): words [0, 32) a header whose first int is the error flag (set by
 // the kernels for a DOF index outside [0, n_dofs); cleared at the start of every call), words

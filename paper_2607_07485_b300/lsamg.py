@@ -101,9 +101,12 @@ def kernel_stats():
 
 
 def gram_spmv_static(elem_dofs, G, x, y, stream=None):
-    """y = sum_T R_T^T G_T^T (G_T x_T) through the allocation-free entry point (no handle).
+    """y = sum_T R_T^T G_T^T (G_T x_T) through the allocation-free entry point (no handle), for
+    callers that must not allocate device memory (GPU memory owned by another allocator, or a
+    latency-critical loop where cudaMalloc would synchronise the device).
     elem_dofs: int32 [ne, nT], G: float64 [ne, m, nT], x, y: float64 [n] device tensors (y is
-    overwritten; nothing is allocated here or in the library)."""
+    overwritten; nothing is allocated here or in the library).  Make the first call on a device
+    before any stream capture: it looks up the library's static scratch array."""
     ne, nT = elem_dofs.shape
     m = G.shape[1] if G.dim() == 3 else 0
     _check(_lib.lsamg_gram_spmv_static(int(x.numel()), int(ne), int(nT), int(m), _ptr(elem_dofs), _ptr(G),

@@ -1,7 +1,11 @@
-"""Allocation-free Gram SpMV (lsamg_gram_spmv_static) against the handle's Gram SpMV
-(lsamg_gram_spmv) on the same element factors: two calls in a row through the one static
-scratch array, on two element families, plus the size limit.  Self-contained (builds its own
-handles), so it passes alone in a fresh process and after the other tests."""
+"""The allocation-free Gram SpMV (lsamg_gram_spmv_static), for callers that must not allocate
+device memory (GPU memory owned by another allocator, or latency-critical loops where
+cudaMalloc would synchronise the device), against the handle's Gram SpMV (lsamg_gram_spmv) on
+the same element factors.  It makes two calls in a row through the one static scratch array
+(which keeps the previous call's contents), on two element families, and checks the size
+limit.  Self-contained (it builds its own handles), so it passes alone in a fresh process and
+after the other tests; the file sorts last so that a stop-at-first-failure run has already
+run every other test."""
 import numpy as np
 import pytest
 
