@@ -417,7 +417,7 @@ def test_multi_cta_paths_match_single_cta(name):
     """The multi-CTA tridiagonalisation and the split Schwarz sweep (used for large local
     problems) forced on a small case: same coarse space and the same V-cycle as the
     one-CTA-per-matrix kernels (and so as the oracle)."""
-    p, H, amg, ptol, vtol, _ = case(name)
+    p, H, amg, ptol, vtol, band = case(name)
     gen, opts, *_ = CASES[name]
     o = dict(opts)
     if "tau_c" not in o and "c_tau" in p:
@@ -425,10 +425,16 @@ def test_multi_cta_paths_match_single_cta(name):
     big = Lsamg(p["n"], torch.from_numpy(p["elem_dofs"]).to(DEV), torch.from_numpy(p["mats"]).to(DEV),
                 large_dense=16, split_sweep=16, sweep_block=32, **o)
     L0 = H.levels[0]
-    np.testing.assert_array_equal(big.query(0, "K"), amg.query(0, "K"))
+    kb, ka = big.query(0, "K"), amg.query(0, "K")
     zoff, Z = big.query(0, "ZOFF"), big.query(0, "Z")
     for i in range(L0.nagg):
-        nw, k = len(L0.omega[i]), int(L0.k[i])
+        # mode counts agree except where the oracle has eigenvalues inside the rank-flip band
+        if kb[i] != ka[i] or kb[i] != L0.k[i]:
+            near = int((np.abs(L0.mu[i] * L0.tau - 1.0) < band).sum())
+            assert max(abs(int(kb[i]) - int(L0.k[i])), abs(int(ka[i]) - int(L0.k[i]))) <= near, \
+                f"aggregate {i}: k {kb[i]} (forced) vs {ka[i]} vs oracle {L0.k[i]}, {near} in the band"
+            continue
+        nw, k = len(L0.omega[i]), int(kb[i])
         Zg = Z[zoff[i]:zoff[i + 1]].reshape(nw, k)
         assert np.linalg.norm(_projector(Zg) - _projector(L0.Z[i]), 2) * _separation(L0, i) <= ptol
     r = np.random.default_rng(6).standard_normal(p["n"])
