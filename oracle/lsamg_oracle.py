@@ -18,7 +18,9 @@ finite elements"), cited by section / equation:
 * Section 2, eqs. (2.8)-(2.9)   local GEP and its Schur-complement reduction
 * Section 2, eq. (2.10)         tau_cut = c * max_j mult(j)
 * Section 2 (end)               P = [R_w^T Z_i], G_c = G P, recursion, direct coarsest solve
-* Section 6 preamble            multiplicative Schwarz pre/post smoothing, level limits
+* Section 6 preamble            multiplicative Schwarz pre/post smoothing, level limits,
+                                the standalone V-cycle iteration (random x0, 1e-10 reduction)
+* Section 2 (smoother choice)   additive (fully parallel) block Schwarz variant, damped
 * (outer solver, adjoint)       FP64 PCG / flexible CG(1) and the adjoint gradient
                                 g_e = -lambda_e^T K_e x_e  (not in the paper)
 
@@ -46,7 +48,7 @@ EPS = np.finfo(np.float64).eps
 __all__ = [
     "hash32", "assemble", "element_gram", "structural_graph", "mis2", "aggregate_mis2",
     "aggregate_two_pass", "closure", "local_problem", "local_problem_pinv", "local_gram_rows", "Level", "Hierarchy", "setup",
-    "vcycle", "pcg", "fcg", "elem_grad", "adjoint_grad", "gram_spmv", "greedy_colouring",
+    "vcycle", "stationary", "pcg", "fcg", "elem_grad", "adjoint_grad", "gram_spmv", "greedy_colouring",
     "options_default",
 ]
 
@@ -602,15 +604,25 @@ def _cast(H, dtype):
     return out
 
 
-def vcycle(H, b, dtype=np.float64, level=0):
+def vcycle(H, b, dtype=np.float64, level=0, smoother="multiplicative"):
     """One LS-AMG-DD V-cycle B^{-1} b (Section 2 error propagator E_TG, Section 6
-    preamble): forward multiplicative Schwarz over colours ascending, coarse-grid
-    correction, reverse-order post-smoothing; exact dense solve on the coarsest level."""
+    preamble): Schwarz pre-smoothing on the overlaps, coarse-grid correction, the adjoint
+    post-smoothing; exact dense solve on the coarsest level.
+
+    smoother="multiplicative": forward multiplicative Schwarz over colours ascending, the
+    exact reverse order after the correction (the paper's numerical tests).
+    smoother="additive": the fully parallel block Schwarz variant that Section 2 also allows,
+    x += theta sum_i R_Omega_i^T A_Omega_i^{-1} R_Omega_i r before and after the correction.
+    Reading (the paper gives no damping): theta = 1 / (number of colours).  Subdomains of one
+    colour do not conflict, so the A-projections of a colour sum to an A-orthogonal
+    projection and lambda_max(theta sum_i P_i) <= 1: the smoother is A-non-expansive."""
+    if smoother not in ("multiplicative", "additive"):
+        raise ValueError(f"unknown smoother {smoother!r}")
     ops = _cast(H, dtype)
-    return _vc(H, ops, np.asarray(b, dtype), level, dtype)
+    return _vc(H, ops, np.asarray(b, dtype), level, dtype, smoother)
 
 
-def _vc(H, ops, b, l, dtype):
+def _vc(H, ops, b, l, dtype, smoother="multiplicative"):
     L = H.levels[l]
     op = ops[l]
     if L.coarsest:
@@ -620,23 +632,59 @@ def _vc(H, ops, b, l, dtype):
     x = np.zeros(L.n, dtype)
     res = b.copy()
 
+    def solve_local(i, r):
+        Lc = op["chol"][i]
+        y = sla.solve_triangular(Lc, r[L.Omega[i]], lower=True)
+        return sla.solve_triangular(Lc.T, y, lower=False).astype(dtype)
+
     def local(i):
         Om = L.Omega[i]
-        Lc = op["chol"][i]
-        y = sla.solve_triangular(Lc, res[Om], lower=True)
-        d = sla.solve_triangular(Lc.T, y, lower=False).astype(dtype)
+        d = solve_local(i, res)
         x[Om] += d
         res[:] = res - (A[:, Om] @ d).astype(dtype)
 
-    for i in L.sweep:
-        local(i)
+    def additive():
+        theta = dtype(1.0 / (int(np.max(L.colour)) + 1))
+        dx = np.zeros(L.n, dtype)
+        for i in range(L.nagg):
+            dx[L.Omega[i]] += solve_local(i, res)
+        x[:] = x + theta * dx
+        res[:] = b - (A @ x).astype(dtype)
+
+    if smoother == "additive":
+        additive()
+    else:
+        for i in L.sweep:
+            local(i)
     rc = (op["P"].T @ res).astype(dtype)
-    ec = _vc(H, ops, rc, l + 1, dtype)
+    ec = _vc(H, ops, rc, l + 1, dtype, smoother)
     x += (op["P"] @ ec).astype(dtype)
     res[:] = b - (A @ x).astype(dtype)
-    for i in reversed(L.sweep):
-        local(i)
+    if smoother == "additive":
+        additive()
+    else:
+        for i in reversed(L.sweep):
+            local(i)
     return x
+
+
+def stationary(H, b, x0, rtol=1e-10, maxit=500, smoother="multiplicative"):
+    """The standalone V-cycle iteration of the paper's tests (Section 6 preamble):
+    x <- x + B^{-1}(b - A x) from the given (random) initial iterate, stopped when the l2 norm
+    of the residual has fallen by rtol relative to the initial residual.
+    Returns (x, iterations, residual history ||r_k|| / ||r_0||)."""
+    A = H.levels[0].A
+    x = np.array(x0, float)
+    r = b - A @ x
+    r0 = np.linalg.norm(r)
+    hist = [1.0]
+    for it in range(1, maxit + 1):
+        x += vcycle(H, r, smoother=smoother)
+        r = b - A @ x
+        hist.append(np.linalg.norm(r) / r0)
+        if hist[-1] <= rtol:
+            return x, it, hist
+    return x, maxit, hist
 
 
 def pcg(A, b, prec, rtol=1e-8, maxit=1000, x0=None):

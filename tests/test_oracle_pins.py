@@ -570,3 +570,74 @@ def test_local_problem_least_squares_form_vs_cholesky_route(cfg1):
         Pa = np.linalg.qr(Zc)[0]
         Pb = np.linalg.qr(L0.Z[i])[0]
         assert np.linalg.norm(Pa @ Pa.T - Pb @ Pb.T, 2) < 2e-8
+
+
+# ----------------------------------------------------------------------------- additive Schwarz, stationary cycle
+def _rt1_three_level():
+    n, d, K = fegen.rt_quad(8, 1, 1.0)
+    H = O.setup(n, d, np.broadcast_to(K, (d.shape[0],) + K.shape),
+                opts=dict(max_density=1.0, agg_passes=1, agg_passes_coarse=1))
+    assert len(H.levels) == 3
+    return H
+
+
+def _sum_of_projections(L, aggs):
+    """sum_i R_Omega_i^T A_Omega_i^{-1} R_Omega_i A over the given subdomains (dense)."""
+    A = L.A.toarray()
+    T = np.zeros_like(A)
+    for i in aggs:
+        Om = L.Omega[i]
+        T[np.ix_(Om, Om)] += np.linalg.inv(A[np.ix_(Om, Om)])
+    return T @ A
+
+
+def test_additive_schwarz_colour_bound():
+    # Section 2 (block Schwarz smoothers): subdomains of one colour share no element, so their
+    # A-projections are mutually A-orthogonal and sum to a projection; hence
+    # 0 < lambda(sum_i P_i) <= number of colours (the overlaps cover every DOF).
+    H = _rt1_three_level()
+    L = H.levels[0]
+    ncol = int(L.colour.max()) + 1
+    for c in range(ncol):
+        Tc = _sum_of_projections(L, np.flatnonzero(L.colour == c))
+        np.testing.assert_allclose(Tc @ Tc, Tc, atol=1e-10 * max(1.0, abs(Tc).max()))
+    lam = np.sort(np.real(np.linalg.eigvals(_sum_of_projections(L, range(L.nagg)))))
+    assert lam[0] > 1e-8 and lam[-1] <= ncol * (1 + 1e-10)
+
+
+def test_additive_vcycle_symmetric_positive_definite():
+    # theta = 1/#colours makes the smoother A-non-expansive, so the symmetric cycle's
+    # B^{-1} A has its spectrum in (0, 1]
+    H = _rt1_three_level()
+    n = H.levels[0].n
+    Binv = np.column_stack([O.vcycle(H, e, smoother="additive") for e in np.eye(n)])
+    np.testing.assert_allclose(Binv, Binv.T, rtol=0, atol=1e-12 * abs(Binv).max())
+    lam = np.sort(np.real(sla.eigvals(Binv @ H.levels[0].A.toarray())))
+    assert lam[0] > 0 and lam[-1] <= 1 + 1e-10
+
+
+@pytest.mark.parametrize("smoother", ["multiplicative", "additive"])
+def test_stationary_cycle_contracts_at_spectral_radius(smoother):
+    # Section 6 preamble: x <- x + B^{-1}(b - A x) from a random x0.  E = I - B^{-1}A is
+    # A-self-adjoint, so ||e_k||_A <= rho(E)^k ||e_0||_A exactly; the limit is A^{-1} b.
+    H = _rt1_three_level()
+    A = H.levels[0].A
+    n = A.shape[0]
+    Binv = np.column_stack([O.vcycle(H, e, smoother=smoother) for e in np.eye(n)])
+    rho = np.max(np.abs(np.linalg.eigvals(np.eye(n) - Binv @ A.toarray())))
+    assert rho < 1
+    rng = np.random.default_rng(11)
+    b = rng.uniform(-1, 1, n)
+    x0 = rng.standard_normal(n)
+    xs = spla.spsolve(A.tocsc(), b)
+
+    def anorm(v):
+        return float(np.sqrt(v @ (A @ v)))
+
+    e0 = anorm(x0 - xs)
+    for k in range(1, 7):
+        xk, _, _ = O.stationary(H, b, x0, rtol=0.0, maxit=k, smoother=smoother)
+        assert anorm(xk - xs) <= rho ** k * e0 * (1 + 1e-8) + 1e-13 * e0
+    x, it, hist = O.stationary(H, b, x0, rtol=1e-10, smoother=smoother)
+    assert hist[-1] <= 1e-10 and it < 200
+    np.testing.assert_allclose(x, xs, rtol=0, atol=1e-8 * abs(xs).max())
