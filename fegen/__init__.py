@@ -15,7 +15,10 @@ The discretisations are quad/hex analogues of the paper's Section 6 problems
 * ``bfs_quad``     -- bicubic Bogner-Fox-Schmit (Hermite) on N x N squares,
                       anisotropic hyperdiffusion in H^2 (cf. Section 6.2);
 * ``q2_elasticity``-- vector Q2 hexahedra on N^3 cubes, small-strain elasticity,
-                      clamp on x = 0 imposed by symmetric Nitsche (cf. Section 6.3).
+                      clamp on x = 0 imposed by symmetric Nitsche (cf. Section 6.3);
+* ``cg1_tri``      -- P1 (CG1) on N x N squares split into right triangles, scalar
+                      diffusion with kappa = 1 + x + y and u = 0 by symmetric Nitsche
+                      (the closure comparison of Section 5, Table 2).
 
 Workload configurations (``config``) use ``seed = 20260700 + cfg``.
 """
@@ -24,7 +27,7 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = [
-    "rt_quad", "bfs_quad", "q2_elasticity", "config", "CONFIGS", "gauss01", "gll01",
+    "rt_quad", "bfs_quad", "q2_elasticity", "cg1_tri", "config", "CONFIGS", "gauss01", "gll01",
 ]
 
 
@@ -337,6 +340,59 @@ CONFIGS = {
     4: dict(kind="q2", N=48, nu=0.45, E=(1.0, 1e4), block=6, nrhs=16, c_tau=0.75),
     5: dict(kind="rt", N=128, k=1, beta=1e-6, q=3, c_tau=0.75, coef="lognormal", adjoint=True),
 }
+
+
+def cg1_tri(N: int, gamma: float = 10.0):
+    """P1 elements on a uniform N x N grid of the unit square, every square split along its
+    (i, j)-(i+1, j+1) diagonal into two right triangles; -div(kappa grad u) = f with
+    kappa(x, y) = 1 + x + y and u = 0 on the boundary imposed weakly by symmetric Nitsche.
+
+    Element matrices (exact: grad phi is constant and kappa linear, so the volume term is
+    (grad phi_p . grad phi_q) |T| kappa(centroid); edge terms use 2-point Gauss, exact for the
+    cubic integrands):  K_T + sum over the element's boundary edges e of
+        -<kappa d_n phi_q, phi_p>_e - <kappa d_n phi_p, phi_q>_e + (gamma / h) <kappa phi_p, phi_q>_e.
+    gamma = 10 keeps every boundary element block positive semidefinite for this mesh.
+
+    Returns (n, elem_dofs [2N^2, 3] int32, elem_mats [2N^2, 3, 3]) with DOF = j (N + 1) + i
+    for the vertex (i h, j h).  The gradients of the two vertices on a hypotenuse are
+    orthogonal, so their assembled entry of A cancels exactly (it is 0 in both triangles)."""
+    h = 1.0 / N
+    n = (N + 1) ** 2
+
+    def vid(i, j):
+        return j * (N + 1) + i
+
+    gp = np.array([0.5 - 0.5 / np.sqrt(3.0), 0.5 + 0.5 / np.sqrt(3.0)])
+    dofs, mats = [], []
+    for j in range(N):
+        for i in range(N):
+            for tri in (((i, j), (i + 1, j), (i + 1, j + 1)), ((i, j), (i + 1, j + 1), (i, j + 1))):
+                X = np.array([[a * h, b * h] for a, b in tri])
+                M = np.array([[1.0, X[0, 0], X[0, 1]], [1.0, X[1, 0], X[1, 1]], [1.0, X[2, 0], X[2, 1]]])
+                C = np.linalg.inv(M)                 # phi_k(x, y) = C[0, k] + C[1, k] x + C[2, k] y
+                grad = C[1:, :].T                    # [3, 2]
+                area = 0.5 * abs(np.linalg.det(M))
+                cen = X.mean(axis=0)
+                K = (grad @ grad.T) * area * (1.0 + cen[0] + cen[1])
+                for a, b in ((0, 1), (1, 2), (2, 0)):
+                    P, Q = tri[a], tri[b]
+                    on = ((P[0] == Q[0] and P[0] in (0, N)) or (P[1] == Q[1] and P[1] in (0, N)))
+                    if not on:
+                        continue
+                    t = np.array([Q[0] - P[0], Q[1] - P[1]], float)
+                    nvec = np.array([t[1], -t[0]])
+                    if nvec @ (np.array([P[0] * h, P[1] * h]) - cen) < 0:
+                        nvec = -nvec                 # outward
+                    for qp in gp:
+                        xy = (1 - qp) * X[a] + qp * X[b]
+                        w = 0.5 * h                      # 2-point Gauss on an edge of length h
+                        kap = 1.0 + xy[0] + xy[1]
+                        phi = C[0, :] + C[1, :] * xy[0] + C[2, :] * xy[1]
+                        dn = grad @ nvec
+                        K += w * kap * (-np.outer(phi, dn) - np.outer(dn, phi) + (gamma / h) * np.outer(phi, phi))
+                dofs.append([vid(*v) for v in tri])
+                mats.append(0.5 * (K + K.T))
+    return n, np.array(dofs, np.int32), np.array(mats)
 
 
 def config(cfg: int, N: int | None = None, expand: bool = True):

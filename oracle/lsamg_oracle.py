@@ -58,9 +58,10 @@ __all__ = [
 # -----------------------------------------------------------------------------
 def options_default():
     """Paper defaults: c = 0.75 (Section 6.1/6.3), 2 aggregation passes, at most 3 levels,
-    stop below 10 DOFs or above 25 % density (Section 6 preamble)."""
+    stop below 10 DOFs or above 25 % density (Section 6 preamble); the G-row closure
+    (closure="A" selects the algebraic A-closure of the Section 5 comparison)."""
     return dict(tau_c=0.75, agg_passes=2, agg_passes_coarse=2, max_levels=3, min_coarse=10,
-                max_density=0.25, rtol=1e-8, maxit=1000)
+                max_density=0.25, rtol=1e-8, maxit=1000, closure="G")
 
 
 # -----------------------------------------------------------------------------
@@ -242,11 +243,16 @@ def aggregate_two_pass(S, passes=2):
 # -----------------------------------------------------------------------------
 # Closure, multiplicity, splitting (Section 2 eqs. 2.3-2.7; Section 5.4 Thm 5.6)
 # -----------------------------------------------------------------------------
-def closure(elems, agg, nagg):
+def closure(elems, agg, nagg, A=None):
     """Element-form closure.  With structural row supports, the rows touching omega_i are
     the rows of the elements T with N(T) & omega_i != {} (eq. 2.3), the G-row closure is
     Omega_i = U N(T) over those elements (eq. 2.4 = element closure, Thm 5.6), and
     mult(j) = mult(T) = #aggregates meeting N(T) (eq. 2.5).
+
+    With the assembled matrix A given, Omega_i is instead the algebraic A-closure of
+    Section 5 (Def. of Omega^A): omega_i together with every p whose row block A(p, omega_i)
+    has a nonzero entry after assembly (exact zeros from cancellation excluded).  Only the
+    closure changes; rows touching omega_i and multiplicities stay those of eqs. 2.3-2.5.
 
     Returns (eagg, mult, ael, omega, Omega)."""
     eagg = [np.unique(agg[np.asarray(d, np.int64)]) for d in elems]
@@ -261,6 +267,13 @@ def closure(elems, agg, nagg):
     starts = np.concatenate([[0], np.cumsum(counts)])
     omega = [order[starts[i]:starts[i + 1]] for i in range(nagg)]
     Omega = []
+    if A is not None:
+        An = sp.csr_matrix(A, copy=True)
+        An.eliminate_zeros()
+        for i in range(nagg):
+            nb = An[omega[i]].indices
+            Omega.append(np.union1d(np.asarray(omega[i], np.int64), nb.astype(np.int64)))
+        return eagg, mult, ael, omega, Omega
     for i in range(nagg):
         if len(ael[i]):
             Omega.append(np.unique(np.concatenate([np.asarray(elems[t], np.int64) for t in ael[i]])))
@@ -345,7 +358,9 @@ def local_gram_rows(i, elems, G, mult, ael, omega, Omega):
         if GT.size == 0:
             continue
         B = np.zeros((GT.shape[0], len(loc)))
-        B[:, [pos[int(g)] for g in elems[t]]] = GT
+        cols = np.array([pos.get(int(g), -1) for g in elems[t]])
+        inside = cols >= 0          # always all of N(T) for the G-row closure; the A-closure
+        B[:, cols[inside]] = GT[:, inside]   # may cut element DOFs (their columns are lost)
         blocks.append((B, float(mult[t])))
     Hm = np.vstack([B / np.sqrt(m) for B, m in blocks]) if blocks else np.zeros((0, len(loc)))
     F = np.vstack([B[:, :nw] for B, _ in blocks]) if blocks else np.zeros((0, nw))
@@ -489,7 +504,9 @@ def setup(n, elems, mats, opts=None, c_tau=None):
 
 def _coarsen(lev, o, passes):
     agg, nagg = aggregate_two_pass(lev.S, passes)
-    eagg, mult, ael, omega, Omega = closure(lev.elems, agg, nagg)
+    if o.get("closure", "G") not in ("G", "A"):
+        raise ValueError(f"unknown closure {o['closure']!r}")
+    eagg, mult, ael, omega, Omega = closure(lev.elems, agg, nagg, A=lev.A if o.get("closure") == "A" else None)
     tau = o["tau_c"] * float(mult.max())
     Z, gaps, mus = [], [], []
     for i in range(nagg):

@@ -42,6 +42,10 @@ def test_generator_sizes_match_mesh_counts():
     # every DOF is used, edge DOFs shared by at most two elements
     cnt = np.bincount(d.ravel(), minlength=n)
     assert cnt.min() == 1 and cnt.max() == 2
+    # CG1 triangles: the DOF counts of the closure comparison (Table 2), (N + 1)^2 vertices
+    assert [(N + 1) ** 2 for N in (32, 64, 128, 256, 512, 1024)] == [1089, 4225, 16641, 66049, 263169, 1050625]
+    n, d, K = fegen.cg1_tri(4)
+    assert n == 25 and d.shape == (32, 3) and K.shape == (32, 3, 3)
 
 
 def test_rt0_element_closed_form():
@@ -641,3 +645,46 @@ def test_stationary_cycle_contracts_at_spectral_radius(smoother):
     x, it, hist = O.stationary(H, b, x0, rtol=1e-10, smoother=smoother)
     assert hist[-1] <= 1e-10 and it < 200
     np.testing.assert_allclose(x, xs, rtol=0, atol=1e-8 * abs(xs).max())
+
+
+# ----------------------------------------------------------------------------- A- vs G-row closure
+@pytest.fixture(scope="module")
+def cg1_closures():
+    # CG1 on right triangles, kappa = 1 + x + y, Nitsche u = 0 (the Section 5 comparison, 1,089 DOFs)
+    n, d, K = fegen.cg1_tri(32)
+    assert n == 1089
+    A = O.assemble(n, d, K)
+    agg, nagg = O.aggregate_two_pass(O.structural_graph(n, d), 2)
+    eagg, mult, ael, omega, OmG = O.closure(d, agg, nagg)
+    *_, OmA = O.closure(d, agg, nagg, A=A)
+    G = [O.element_gram(k) for k in K]
+    return n, d, A, G, mult, ael, omega, OmG, OmA
+
+
+def test_a_closure_definition_and_cut_by_cancellation(cg1_closures):
+    # Section 5 (Def. of the A-closure): Omega^A = omega + {p : A(p, omega) != 0 after assembly}.
+    # The two vertices of a hypotenuse have orthogonal gradients, so their assembled entry is an
+    # exact zero: Omega^A is contained in Omega^G and strictly smaller for some aggregates.
+    n, d, A, G, mult, ael, omega, OmG, OmA = cg1_closures
+    Ad = A.toarray()
+    for i in range(0, len(omega), max(1, len(omega) // 12)):          # brute force, from the definition
+        w = np.asarray(omega[i])
+        brute = sorted(set(w.tolist()) | {p for p in range(n) if p not in set(w.tolist()) and np.any(Ad[p, w] != 0)})
+        assert list(OmA[i]) == brute
+    assert all(set(a.tolist()) <= set(g.tolist()) for a, g in zip(OmA, OmG))
+    assert sum(len(g) - len(a) for a, g in zip(OmA, OmG)) > 0
+
+
+def test_exact_splitting_needs_the_g_row_closure(cg1_closures):
+    # eq. 2.7 holds with the G-row closure; on the A-closure the local matrices lose the rows'
+    # entries on the cut DOFs, so the splitting no longer reassembles A (Section 5, before Table 2)
+    n, d, A, G, mult, ael, omega, OmG, OmA = cg1_closures
+    Ad = A.toarray()
+    errs = []
+    for Om in (OmG, OmA):
+        total = np.zeros((n, n))
+        for i in range(len(omega)):
+            Hm, F, loc = OL.local_gram_rows(i, d, G, mult, ael, omega, Om)
+            total[np.ix_(loc, loc)] += Hm.T @ Hm
+        errs.append(abs(total - Ad).max() / abs(Ad).max())
+    assert errs[0] <= 1e-12 and errs[1] >= 1e-3
