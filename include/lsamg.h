@@ -84,6 +84,9 @@ typedef struct {
                                     many-CTA sweep, smaller ones one CTA per subdomain (0 = 128) */
     int32_t sweep_block;         /* rows per diagonal block of the blocked triangular solves of the
                                     Schwarz and coarsest factors, 1..64 (0 = 64); fixed at setup */
+    int32_t smoother;            /* 0: multiplicative Schwarz, colour-ordered (the paper's tests);
+                                    1: additive Schwarz over all subdomains at once, damped by
+                                    1 / #colours (the parallel block smoother Section 2 allows) */
 } lsamg_options;
 
 lsamg_options lsamg_options_default(void);
@@ -102,8 +105,10 @@ int lsamg_apply(lsamg_handle *h, const double *r, double *z, int32_t nrhs, int32
 /* Preconditioned solve of A x = b to ||r|| <= rtol ||b||, x0 = the incoming x if
  * use_x0 != 0 else 0.  b, x: device float64 [nrhs][n_dofs].  iters, relres: host arrays
  * [nrhs] (may be NULL).  mode: 0 = FP64 PCG with the FP64 V-cycle, 1 = FP64 flexible
- * CG(1) with the FP32 V-cycle, -1 = from options.  Returns LSAMG_NO_CONVERGENCE if any
- * right-hand side missed the tolerance within maxit. */
+ * CG(1) with the FP32 V-cycle, 2 = the stationary iteration x <- x + B^{-1}(b - A x) with the
+ * FP64 V-cycle, stopped at ||r|| <= rtol ||r_0|| (Section 6 standalone cycles; relres is then
+ * ||r|| / ||r_0||), -1 = from options.  Returns LSAMG_NO_CONVERGENCE if any right-hand side
+ * missed the tolerance within maxit. */
 int lsamg_solve(lsamg_handle *h, const double *b, double *x, int32_t nrhs, int32_t mode,
                 int32_t use_x0, void *stream, int32_t *iters, double *relres);
 

@@ -161,6 +161,7 @@ void do_setup(Handle &H, const lsamg_problem *P, const lsamg_options &o) {
     if (P->n_dofs >= (1ll << 30)) fail(LSAMG_LIMIT, "more than 2^30 DOFs");
     if (o.max_levels < 1 || o.max_levels > 8) fail(LSAMG_INVALID_ARG, "max_levels must be in 1..8");
     if (o.sweep_block < 0 || o.sweep_block > 64) fail(LSAMG_INVALID_ARG, "sweep_block must be in 0..64");
+    if (o.smoother != 0 && o.smoother != 1) fail(LSAMG_INVALID_ARG, "smoother must be 0 or 1");
     H.err.alloc(2, s);
     H.err.zero(s);
     int *err = H.err.p;
@@ -345,11 +346,85 @@ void precondition(Handle &H, const double *r, double *z, int nrhs, bool fp32) {
     }
 }
 
+// Stationary V-cycle iteration x <- x + B^{-1}(b - A x) with the FP64 cycle, stopped when
+// ||r_k|| <= rtol ||r_0|| (the paper's standalone solver, Section 6 preamble).
+int do_stationary(Handle &H, const double *b, double *x, int nrhs, bool use_x0, int32_t *iters,
+                  double *relres) {
+    cudaStream_t s = H.stream;
+    const lsamg_options &o = H.opt;
+    ensure_solve_ws(H, nrhs);
+    Level &L0 = H.levels[0];
+    const int64_t n = L0.n;
+    double *r = H.kr.p, *z = H.kz.p, *d = H.dots.p;
+    if (!use_x0) CK(cudaMemsetAsync(x, 0, n * nrhs * sizeof(double), s));
+    {
+        DBuf<int> f;
+        f.alloc(1, s);
+        f.zero(s);
+        k_nan_check<<<(unsigned)std::min<int64_t>(cdiv(n * nrhs, 256), 1184), 256, 0, s>>>(b, n * nrhs, f.p);
+        CK_LAUNCH();
+        if (read1(f.p, s)) fail(LSAMG_NAN, "non-finite right-hand side");
+    }
+    gram_spmv<double>(L0, x, r, b, nrhs, s);   // r = b - A x
+    std::vector<double> r0(nrhs), rr(nrhs), hv(nrhs), step(nrhs, 1.0);
+    std::vector<int32_t> its(nrhs, 0);
+    std::vector<char> done(nrhs, 0);
+    vec_dots(r, r, n, nrhs, d, s);
+    CK(cudaMemcpyAsync(hv.data(), d, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    int active = 0;
+    for (int i = 0; i < nrhs; i++) {
+        r0[i] = std::sqrt(hv[i]);
+        rr[i] = r0[i];
+        done[i] = (r0[i] == 0.0);
+        active += !done[i];
+    }
+    int it = 0;
+    for (; active > 0 && it < o.maxit; it++) {
+        {
+            LSAMG_PROF("krylov: precondition", s);
+            precondition(H, r, z, nrhs, false);
+        }
+        for (int i = 0; i < nrhs; i++) step[i] = done[i] ? 0.0 : 1.0;
+        CK(cudaMemcpyAsync(d + 4 * nrhs, step.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, s));
+        vec_axpy(x, z, d + 4 * nrhs, n, nrhs, 1.0, s);   // x += B^{-1} r (active right-hand sides)
+        gram_spmv<double>(L0, x, r, b, nrhs, s);        // r = b - A x
+        vec_dots(r, r, n, nrhs, d, s);
+        CK(cudaMemcpyAsync(hv.data(), d, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        for (int i = 0; i < nrhs; i++) {
+            if (done[i]) continue;
+            rr[i] = std::sqrt(hv[i]);
+            if (!std::isfinite(rr[i])) fail(LSAMG_NAN, "non-finite residual");
+            its[i] = it + 1;
+            if (rr[i] <= o.rtol * r0[i]) {
+                done[i] = 1;
+                active--;
+            }
+        }
+    }
+    CK(cudaStreamSynchronize(s));
+    prof_report("solve");
+    bool ok = true;
+    for (int i = 0; i < nrhs; i++) {
+        if (iters) iters[i] = its[i];
+        if (relres) relres[i] = r0[i] > 0.0 ? rr[i] / r0[i] : 0.0;
+        ok = ok && done[i];
+    }
+    if (!ok) {
+        g_last_error = "maximum number of iterations reached";
+        return LSAMG_NO_CONVERGENCE;
+    }
+    return LSAMG_OK;
+}
+
 int do_solve(Handle &H, const double *b, double *x, int nrhs, int mode, bool use_x0, int32_t *iters,
              double *relres) {
     cudaStream_t s = H.stream;
     const lsamg_options &o = H.opt;
     if (mode < 0) mode = o.vcycle_fp32 ? 1 : 0;
+    if (mode == 2) return do_stationary(H, b, x, nrhs, use_x0, iters, relres);
+    if (mode != 0 && mode != 1) fail(LSAMG_INVALID_ARG, "solve mode must be -1, 0, 1 or 2");
     const bool fp32 = (mode == 1), flexible = (mode == 1);
     ensure_solve_ws(H, nrhs);
     Level &L0 = H.levels[0];
@@ -488,6 +563,7 @@ lsamg_options lsamg_options_default(void) {
     o.large_dense = 0;
     o.split_sweep = 0;
     o.sweep_block = 0;
+    o.smoother = 0;
     return o;
 }
 

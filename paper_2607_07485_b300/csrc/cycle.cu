@@ -578,6 +578,17 @@ __global__ void k_sw_addx(const int32_t *aggs, const int64_t *Optr, const int32_
             x[(int64_t)r * n + Oidx[ob + i]] += ws[(int64_t)r * wsn + ob + i];
 }
 
+// x[Omega_a] += theta ws[sub] for subdomains that may overlap (additive smoother): atomic adds
+template <class T>
+__global__ void k_sw_addx_scaled(const int32_t *aggs, const int64_t *Optr, const int32_t *Oidx, const T *ws, T *x,
+                                 T theta, int64_t n, int64_t wsn, int nrhs) {
+    const int32_t a = aggs[blockIdx.y];
+    const int64_t ob = Optr[a], nO = Optr[a + 1] - ob;
+    for (int r = 0; r < nrhs; r++)
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nO; i += (int64_t)gridDim.x * blockDim.x)
+            atomicAdd(&x[(int64_t)r * n + Oidx[ob + i]], theta * ws[(int64_t)r * wsn + ob + i]);
+}
+
 // residual update res -= G_T^T G_T delta_T, one CTA per (subdomain, element meeting Omega) pair
 template <class T>
 __global__ void __launch_bounds__(128) k_sw_scatter(const int32_t *pa, const int64_t *pj, int64_t npairs,
@@ -864,6 +875,46 @@ static void sweep(Level &L, int c, int nrhs, cudaStream_t s) {
     CK_LAUNCH();
 }
 
+// Additive block Schwarz on the overlaps (the parallel smoother Section 2 allows):
+// x += theta sum_i R_Omega_i^T A_Omega_i^{-1} R_Omega_i r over every subdomain at once, with
+// theta = 1 / #colours (same-colour subdomains share no element, so each colour's projections
+// sum to a projection and the damped smoother is A-non-expansive); then r = b - A x if asked.
+template <class T>
+static void additive_smooth(Level &L, int nrhs, bool update_residual, cudaStream_t s) {
+    const int64_t na = L.ncol > 0 ? L.colptr[L.ncol] : 0;   // every subdomain, in colour order
+    if (na == 0) return;
+    const T *Lp;
+    if constexpr (std::is_same<T, float>::value) Lp = L.L32.p; else Lp = L.L64.p;
+    T *ws = wsvec<T>(L);
+    int maxn = 0;
+    double bytes = 0.0;
+    for (int c = 0; c < L.ncol; c++) {
+        maxn = std::max(maxn, L.colmax[c]);
+        bytes += L.sweep_bytes[std::is_same<T, double>::value ? 1 : 0][c];
+    }
+    const T theta = (T)(1.0 / (double)L.ncol);
+    {
+        KTime kt(KC_SCHWARZ, s, 0.0, bytes);
+        for (int64_t y0 = 0; y0 < na; y0 += 65535) {
+            dim3 gg((unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv(maxn, 256), 64)),
+                    (unsigned)std::min<int64_t>(65535, na - y0));
+            k_sw_gather<T><<<gg, 256, 0, s>>>(L.colagg.p + y0, L.Optr.p, L.Oidx.p, rvec<T>(L), ws, L.n,
+                                              L.Omega_total, nrhs);
+            CK_LAUNCH();
+        }
+        tri_solve<T>(L.colagg.p, na, L.Optr.p, Lp, L.Loff.p, L.Di64.p, L.Doff.p, L.tri_cb, maxn, ws,
+                     L.Omega_total, nrhs, s);
+        for (int64_t y0 = 0; y0 < na; y0 += 65535) {
+            dim3 gg((unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv(maxn, 256), 64)),
+                    (unsigned)std::min<int64_t>(65535, na - y0));
+            k_sw_addx_scaled<T><<<gg, 256, 0, s>>>(L.colagg.p + y0, L.Optr.p, L.Oidx.p, ws, xvec<T>(L), theta,
+                                                   L.n, L.Omega_total, nrhs);
+            CK_LAUNCH();
+        }
+    }
+    if (update_residual) gram_spmv<T>(L, xvec<T>(L), rvec<T>(L), bvec<T>(L), nrhs, s);
+}
+
 template <class T>
 void vcycle(Handle &H, int l, int nrhs, cudaStream_t s) {
     Level &L = H.levels[l];
@@ -883,7 +934,10 @@ void vcycle(Handle &H, int l, int nrhs, cudaStream_t s) {
     CK(cudaMemcpyAsync(r, b, tot * sizeof(T), cudaMemcpyDeviceToDevice, s));
     {
         LSAMG_PROF(l == 0 ? "vc: L0 pre-smooth" : "vc: Lc pre-smooth", s);
-        for (int c = 0; c < L.ncol; c++) sweep<T>(L, c, nrhs, s);
+        if (H.opt.smoother == 1)
+            additive_smooth<T>(L, nrhs, true, s);
+        else
+            for (int c = 0; c < L.ncol; c++) sweep<T>(L, c, nrhs, s);
     }
     const T *Z;
     if constexpr (std::is_same<T, float>::value) Z = L.Z32.p; else Z = L.Z64.p;
@@ -921,7 +975,10 @@ void vcycle(Handle &H, int l, int nrhs, cudaStream_t s) {
     }
     {
         LSAMG_PROF(l == 0 ? "vc: L0 post-smooth" : "vc: Lc post-smooth", s);
-        for (int c = L.ncol - 1; c >= 0; c--) sweep<T>(L, c, nrhs, s);
+        if (H.opt.smoother == 1)
+            additive_smooth<T>(L, nrhs, false, s);
+        else
+            for (int c = L.ncol - 1; c >= 0; c--) sweep<T>(L, c, nrhs, s);
     }
 }
 

@@ -1,0 +1,57 @@
+"""GPU parity for the additive Schwarz smoother (option smoother=1, the parallel block smoother
+Section 2 allows) and the stationary V-cycle solve mode (mode 2, the standalone iteration of
+the Section 6 tests), against the oracle's ``vcycle(smoother="additive")`` and ``stationary``.
+
+Not yet run on a B300: the whole module is skipped until it has passed there once."""
+import numpy as np
+import pytest
+
+import oracle as O
+
+pytestmark = [pytest.mark.gpu, pytest.mark.skip(reason="not yet run on a B300; enable once it passes there")]
+
+torch = pytest.importorskip("torch")
+
+from test_gpu_parity import CASES, DEV, case  # noqa: E402
+
+
+def _handle(name, **extra):
+    from paper_2607_07485_b300 import Lsamg
+    p, H, _, ptol, vtol, band = case(name)
+    o = dict(CASES[name][1])
+    if "tau_c" not in o and "c_tau" in p:
+        o["tau_c"] = p["c_tau"]
+    o.update(extra)
+    amg = Lsamg(p["n"], torch.from_numpy(p["elem_dofs"]).to(DEV), torch.from_numpy(p["mats"]).to(DEV), **o)
+    return p, H, amg, vtol
+
+
+@pytest.mark.parametrize("name", ["rt1_beta1", "cfg1", "cfg3_16"])
+def test_additive_vcycle_matches_oracle(name):
+    p, H, amg, vtol = _handle(name, smoother=1)
+    r = np.random.default_rng(21).standard_normal(p["n"])
+    z = amg.apply(torch.from_numpy(r).to(DEV), fp32=0).cpu().numpy()
+    zo = O.vcycle(H, r, smoother="additive")
+    assert np.linalg.norm(z - zo) <= vtol * np.linalg.norm(zo)
+    amg.close()
+
+
+@pytest.mark.parametrize("name", ["rt1_beta1", "cfg1"])
+@pytest.mark.parametrize("smoother", [0, 1])
+def test_stationary_mode_matches_oracle(name, smoother):
+    import scipy.sparse.linalg as spla
+    p, H, amg, vtol = _handle(name, smoother=smoother, rtol=1e-10, maxit=300)
+    n = p["n"]
+    b = p["b"][0]
+    x0 = np.random.default_rng(22).standard_normal(n)
+    x, its, rel, rc = amg.solve(torch.from_numpy(b).to(DEV), x0=torch.from_numpy(x0).to(DEV), mode=2)
+    assert rc == 0 and rel[0] <= 1e-10
+    A = H.levels[0].A
+    xs = spla.spsolve(A.tocsc(), b)
+    xg = x.cpu().numpy()
+    # the residual reduction of 1e-10 bounds the error by kappa(A) times it; compare residuals
+    assert np.linalg.norm(b - A @ xg) <= 1e-10 * np.linalg.norm(b - A @ x0) * 1.01 + 64 * np.finfo(float).eps * \
+        np.linalg.norm(abs(A) @ abs(xs))
+    xo, ito, _ = O.stationary(H, b, x0, rtol=1e-10, smoother="additive" if smoother else "multiplicative")
+    assert abs(int(its[0]) - ito) <= 1
+    amg.close()
