@@ -55,3 +55,24 @@ def test_stationary_mode_matches_oracle(name, smoother):
     xo, ito, _ = O.stationary(H, b, x0, rtol=1e-10, smoother="additive" if smoother else "multiplicative")
     assert abs(int(its[0]) - ito) <= 1
     amg.close()
+
+
+def test_autotune_on_gpu_returns_options_with_the_same_cycle(tmp_path):
+    # tile shapes change rounding only: the tuned handle's V-cycle matches the default's
+    from paper_2607_07485_b300 import Lsamg
+    from paper_2607_07485_b300.autotune import autotune
+    p, H, amg, ptol, vtol, band = case("cfg3_16")
+    o = dict(CASES["cfg3_16"][1])
+    dofs = torch.from_numpy(p["elem_dofs"]).to(DEV)
+    mats = torch.from_numpy(p["mats"]).to(DEV)
+    cache = str(tmp_path / "tune.json")
+    best = autotune(p["n"], dofs, mats, cache_file=cache, cycles=5, base_opts=o,
+                    space={"split_sweep": (16, 128), "sweep_block": (32, 64)})
+    assert set(best) == {"large_dense", "split_sweep", "sweep_block"}
+    assert autotune(p["n"], dofs, mats, cache_file=cache, base_opts=o) == best
+    tuned = Lsamg(p["n"], dofs, mats, **dict(o, **best))
+    r = torch.from_numpy(np.random.default_rng(23).standard_normal(p["n"])).to(DEV)
+    z1 = tuned.apply(r, fp32=0).cpu().numpy()
+    z0 = amg.apply(r, fp32=0).cpu().numpy()
+    assert np.linalg.norm(z1 - z0) <= vtol * np.linalg.norm(z0)
+    tuned.close()
