@@ -2,6 +2,8 @@
 // the local reduced eigenproblems that define P (Section 2 eqs. 2.6-2.10), the coarse
 // Gram G_c = G P merged by coarse element map (Section 2 end, Remark 5.2), the Schwarz
 // factors of the overlaps and the dense coarsest factor.
+#include <algorithm>
+
 #include "impl.cuh"
 #include "dense.cuh"
 
@@ -590,11 +592,19 @@ void local_spectral(Level &L, const lsamg_options &o, int *err, cudaStream_t s, 
         for (int64_t e = 0; e < L.ne; e++) maxE = std::max<int32_t>(maxE, (int32_t)(ep[e + 1] - ep[e]));
     }
     // batches: aggregates of order <= 2048 (one CTA per matrix in the tridiagonalisation) and
-    // larger ones (many CTAs per matrix) are processed in separate chunks
+    // larger ones (many CTAs per matrix) are processed in separate chunks.  Within each class the
+    // aggregates go largest first: chunks then hold problems of similar order, and inside a launch
+    // the longest ones start first, so no launch waits on one large matrix while SMs idle (local
+    // problem orders vary several-fold and their cost as the cube).  Results are placed by
+    // aggregate id, so the order changes no value.
     std::vector<int32_t> order;
-    for (int pass = 0; pass < 2; pass++)
+    for (int pass = 0; pass < 2; pass++) {
+        const size_t first = order.size();
         for (int64_t a = 0; a < nagg; a++)
             if ((L.h_nw[a] > g_large_dense) == (pass == 1)) order.push_back((int32_t)a);
+        std::stable_sort(order.begin() + first, order.end(),
+                         [&](int32_t x, int32_t y) { return L.h_nw[x] > L.h_nw[y]; });
+    }
     size_t q0 = 0;
     while (q0 < order.size()) {
         // pick a chunk that fits the budget (at least one aggregate), same size class
