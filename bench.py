@@ -1,9 +1,11 @@
 #!/usr/bin/env python3
 """Benchmark of the B300 LS-AMG-DD library.
 
-Workload: RT_[3] grad-div (div u, div v) + 1e-6 (u, v) on a 256 x 256 quad mesh of the unit
-square (2,099,200 DOFs, 65,536 elements of 40 DOFs), per-element coefficient theta_e =
-exp(N(0,1)), right-hand side uniform[-1, 1] (seed 20260702).  Synthetic inputs from fegen.
+Workload (default, --cfg 2): RT_[3] grad-div (div u, div v) + 1e-6 (u, v) on a 256 x 256 quad
+mesh of the unit square (2,099,200 DOFs, 65,536 elements of 40 DOFs), per-element coefficient theta_e =
+exp(N(0,1)), right-hand side uniform[-1, 1] (seed 20260702).  --cfg 4: Q2 hexahedral
+elasticity on 48^3 cubes (2,738,019 DOFs, E ratio 1e4 checkerboard, nu = 0.45, Nitsche clamp)
+with 16 right-hand sides solved in one batched call.  Synthetic inputs from fegen.
 
 One step = GPU set-up of the hierarchy from the element blocks already resident in HBM
 (element factorisation, aggregation, closures, local spectral problems, coarse Gram,
@@ -11,7 +13,7 @@ Schwarz factors, coarsest factorisation) + the preconditioned solve to ||r|| <= 
 The solve mode (FP64 flexible CG around the FP32 V-cycle, or FP64 PCG around the FP64
 V-cycle) is the faster converging one measured during warm-up; both are reported.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lsamg|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lsamg|reference] [--cfg 2|4] [--N mesh]
 
 Under torchrun every rank runs an independent replica on its own GPU (no data-path
 collective); rank 0 prints one JSON line with the maximum step time over ranks.
@@ -39,6 +41,13 @@ WORKLOAD_N = 256
 # coarse levels and up to four levels (at 2.1M DOFs the paper's 3-level / 2-pass hierarchy
 # leaves a ~90k-DOF dense coarsest problem and ~9k-DOF local eigenproblems).
 BENCH_OPTS = dict(agg_passes=2, agg_passes_coarse=1, max_levels=4, maxit=400)
+# Workloads: the default (RT_[3] grad-div, one right-hand side) and the 3D elasticity batch
+# (Q2 hexahedra, 16 right-hand sides in one batched solve; one aggregation pass on every level,
+# since two passes make overlaps of ~19k DOFs whose factors would not fit in HBM).
+WORKLOADS = {
+    2: dict(N=WORKLOAD_N, opts=BENCH_OPTS, sample_N=16),
+    4: dict(N=48, opts=dict(agg_passes=1, agg_passes_coarse=1, max_levels=4, maxit=400), sample_N=4),
+}
 L2_BYTES = 126e6
 
 
@@ -56,7 +65,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lsamg", choices=["lsamg", "reference"])
-    ap.add_argument("--N", type=int, default=WORKLOAD_N, help="mesh size (default: the workload's 256)")
+    ap.add_argument("--cfg", type=int, default=WORKLOAD_CFG, choices=sorted(WORKLOADS),
+                    help="2: RT_[3] grad-div, 1 right-hand side (default); 4: Q2 elasticity, 16 right-hand sides")
+    ap.add_argument("--N", type=int, default=None, help="mesh size (default: the workload's, 256 or 48)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -115,15 +126,29 @@ class ClockSampler:
                     reasons=sorted(reasons), samples=len(sm))
 
 
-def workload(N):
+def workload(N, cfg=WORKLOAD_CFG):
     import fegen
-    c = fegen.config(WORKLOAD_CFG, N=N, expand=True)
+    c = fegen.config(cfg, N=WORKLOADS[cfg]["N"] if N is None else N, expand=True)
+    c["cfg"] = cfg
     return c
 
 
 def workload_name(c):
+    if c.get("cfg", WORKLOAD_CFG) == 4:
+        return (f"Q2 hex elasticity, nu=0.45, E ratio 1e4 checkerboard, Nitsche clamp, {c['N']}^3 cubes, "
+                f"{c['n']:,} DOFs, {c['elem_dofs'].shape[0]:,} elements x 81 DOFs, "
+                f"{c['b'].shape[0]} right-hand sides in one batched solve")
     return (f"RT_[3] grad-div (div,div)+1e-6(u,v), {c['N']}x{c['N']} quads, {c['n']:,} DOFs, "
             f"{c['elem_dofs'].shape[0]:,} elements x 40 DOFs, theta_e=exp(N(0,1))")
+
+
+def rhs(c):
+    """The workload's right-hand sides: [n] for one, [nrhs, n] for a batch."""
+    return c["b"][0].copy() if c["b"].shape[0] == 1 else np.ascontiguousarray(c["b"])
+
+
+def scaled_mats(c):
+    return c["elem_mats"] if c["coef"] is None else c["elem_mats"] * c["coef"][:, None, None]
 
 
 def max_over_ranks(value, device=None):
@@ -139,18 +164,23 @@ def max_over_ranks(value, device=None):
 
 
 # ----------------------------------------------------------------------------- CPU oracle leg
-def oracle_sample(n_full, N_sample=16):
-    """The FP64 oracle on a bounded sample of the same workload (RT_[3] on an N_sample mesh):
-    set-up + FP64 PCG to 1e-8; returns (seconds, scaled seconds for the full DOF count, info)."""
+def oracle_sample(n_full, cfg=WORKLOAD_CFG):
+    """The FP64 oracle on a bounded sample of the same workload (a small mesh of the same
+    elements, the same options and the same number of right-hand sides): set-up + FP64 PCG to
+    1e-8 per right-hand side; returns (seconds, scaled seconds for the full DOF count, info)."""
     import oracle as O
-    c = workload(N_sample)
-    mats = c["elem_mats"] * c["coef"][:, None, None]
+    c = workload(WORKLOADS[cfg]["sample_N"], cfg)
+    o = dict(WORKLOADS[cfg]["opts"])
+    o.pop("maxit", None)
     t = time.perf_counter()
-    H = O.setup(c["n"], c["elem_dofs"], mats, c_tau=c["c_tau"])
+    H = O.setup(c["n"], c["elem_dofs"], scaled_mats(c), opts=o, c_tau=c["c_tau"])
     ts = time.perf_counter() - t
     A = H.levels[0].A
     t = time.perf_counter()
-    x, it, hist = O.pcg(lambda v: A @ v, c["b"][0], lambda r: O.vcycle(H, r))
+    it = 0
+    for b in c["b"]:
+        x, its_b, hist = O.pcg(lambda v: A @ v, b, lambda r: O.vcycle(H, r))
+        it = max(it, its_b)
     tsol = time.perf_counter() - t
     total = ts + tsol
     scale = n_full / c["n"]
@@ -170,24 +200,25 @@ def cpu_cores():
 def run_reference(args, rank):
     if rank != 0:
         return
-    full = workload(args.N)
+    full = workload(args.N, args.cfg)
     n_full = full["n"]
     for _ in range(args.warmup):
-        oracle_sample(n_full)
+        oracle_sample(n_full, args.cfg)
     times = []
     for _ in range(args.steps):
-        raw, scaled, info = oracle_sample(n_full)
+        raw, scaled, info = oracle_sample(n_full, args.cfg)
         times.append((raw, scaled, info))
     val = statistics.mean(t[1] for t in times)
     info = times[-1][2]
-    sample = (f"FP64 oracle (NumPy/SciPy) set-up + PCG to 1e-8 on RT_[3] 16x16 ({info['n']:,} DOFs); "
-              f"seconds scaled by the DOF ratio {info['scale']:.1f} (set-up and solve are linear in DOFs "
-              f"at fixed aggregate size)")
+    sample = (f"FP64 oracle (NumPy/SciPy) set-up + PCG to 1e-8 per right-hand side on the same elements at "
+              f"{info['n']:,} DOFs; seconds scaled by the DOF ratio {info['scale']:.1f} (set-up and solve "
+              f"are linear in DOFs at fixed aggregate size)")
     out = dict(metric=METRIC, value=val, unit="s", n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
                ms_per_step=1000 * val, higher_is_better=False, scaling="weak", vs_baseline=None,
                dtype="f64", data="synthetic", impl="reference",
-               config=dict(workload=workload_name(full), n_dofs=n_full, solve_mode="pcg+fp64-vcycle",
-                           options=dict(BENCH_OPTS, tau_c=full["c_tau"]), l2=l2_note(full),
+               config=dict(workload=workload_name(full), n_dofs=n_full, nrhs=int(full["b"].shape[0]),
+                           solve_mode="pcg+fp64-vcycle",
+                           options=dict(WORKLOADS[args.cfg]["opts"], tau_c=full["c_tau"]), l2=l2_note(full),
                            parallelism=f"replicas x{args.gpus}", sample_dofs=info["n"]),
                cpu_baseline=dict(value=val, unit="s", cores=cpu_cores(), kind="oracle", sample=sample,
                                  raw_sample_s=statistics.mean(t[0] for t in times)),
@@ -217,13 +248,13 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    c = workload(args.N)
+    c = workload(args.N, args.cfg)
     n = c["n"]
     d_dofs = torch.from_numpy(c["elem_dofs"]).to(dev)
     d_mats = torch.from_numpy(c["elem_mats"]).to(dev)
-    d_coef = torch.from_numpy(c["coef"]).to(dev)
-    d_b = torch.from_numpy(c["b"][0].copy()).to(dev)
-    opts = dict(BENCH_OPTS, tau_c=c["c_tau"])
+    d_coef = None if c["coef"] is None else torch.from_numpy(c["coef"]).to(dev)
+    d_b = torch.from_numpy(rhs(c)).to(dev)
+    opts = dict(WORKLOADS[args.cfg]["opts"], tau_c=c["c_tau"])
 
     def step(mode, profile=0):
         amg = Lsamg(n, d_dofs, d_mats, d_coef, profile=profile, **opts)
@@ -234,7 +265,7 @@ def main():
         t2 = time.perf_counter()
         st = amg.stats()
         amg.close()
-        return st, t2 - t1, int(its[0]), float(rel[0]), rc
+        return st, t2 - t1, int(np.max(its)), float(np.max(rel)), rc
 
     # ---- warm-up: both solve modes, pick the faster converging one (without warm-up steps, the
     # FP64 PCG mode)
@@ -282,8 +313,8 @@ def main():
     if not args.no_e2e:
         h_dofs = torch.from_numpy(c["elem_dofs"]).pin_memory().numpy()
         h_mats = torch.from_numpy(c["elem_mats"]).pin_memory().numpy()
-        h_coef = torch.from_numpy(c["coef"]).pin_memory().numpy()
-        h_b = torch.from_numpy(c["b"][0].copy()).pin_memory().numpy()
+        h_coef = None if c["coef"] is None else torch.from_numpy(c["coef"]).pin_memory().numpy()
+        h_b = torch.from_numpy(rhs(c)).pin_memory().numpy()
         barrier()
         te = time.perf_counter()
         amg = Lsamg(n, h_dofs, h_mats, h_coef, **opts)
@@ -291,8 +322,9 @@ def main():
         amg.close()
         torch.cuda.synchronize()
         e2e_s = max_over_ranks(time.perf_counter() - te, dev)
-        e2e = dict(value=e2e_s, unit="s", h2d_bytes_per_step=int(h_dofs.nbytes + h_mats.nbytes + h_coef.nbytes + h_b.nbytes),
-                   d2h_bytes_per_step=int(xh.nbytes), steps=1, iters=int(itsh[0]), converged=bool(rch == 0))
+        h2d = h_dofs.nbytes + h_mats.nbytes + (0 if h_coef is None else h_coef.nbytes) + h_b.nbytes
+        e2e = dict(value=e2e_s, unit="s", h2d_bytes_per_step=int(h2d), d2h_bytes_per_step=int(xh.nbytes), steps=1,
+                   iters=int(np.max(itsh)), converged=bool(rch == 0))
 
     if rank != 0:
         if world > 1:
@@ -322,15 +354,16 @@ def main():
     roof = next((r for r in rooflines if r["kernel"] == dominant), None)
     cpu = None
     if not args.no_cpu_baseline:
-        raw, scaled, info = oracle_sample(n)
+        raw, scaled, info = oracle_sample(n, args.cfg)
         cpu = dict(value=scaled, unit="s", cores=cpu_cores(), kind="oracle",
-                   sample=(f"FP64 oracle set-up + PCG to 1e-8 on RT_[3] 16x16 ({info['n']:,} DOFs) took "
-                           f"{raw:.2f} s; scaled by the DOF ratio {info['scale']:.1f}"))
+                   sample=(f"FP64 oracle set-up + PCG to 1e-8 per right-hand side on the same elements at "
+                           f"{info['n']:,} DOFs took {raw:.2f} s; scaled by the DOF ratio {info['scale']:.1f}"))
     out = dict(
         metric=METRIC, value=per_step, unit="s", n_gpus=world, steps=args.steps, warmup=args.warmup,
         ms_per_step=1000 * per_step, higher_is_better=False, scaling="weak", vs_baseline=None,
         dtype="f64 set-up / f32 V-cycle in f64 FCG" if best_mode == 1 else "f64", data="synthetic",
-        config=dict(workload=workload_name(c), n_dofs=n, solve_mode="fcg+fp32-vcycle" if best_mode == 1 else "pcg+fp64-vcycle",
+        config=dict(workload=workload_name(c), n_dofs=n, nrhs=int(c["b"].shape[0]),
+                    solve_mode="fcg+fp32-vcycle" if best_mode == 1 else "pcg+fp64-vcycle",
                     options=opts, l2=l2_note(c),
                     parallelism=f"replicas x{world}"),
         setup_s=statistics.mean(setups), solve_s=statistics.mean(solves), iters=its_list,

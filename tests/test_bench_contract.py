@@ -1,17 +1,20 @@
 """bench.py's reference arm (the FP64 oracle on the host cores) prints one JSON line with the
 fields of the benchmark contract, on the same workload, metric and config keys as the GPU
-arm.  CPU only (a one-step, no-warm-up run on the bounded 16x16 sample)."""
+arm, for both workloads.  CPU only (one step, no warm-up, on the bounded oracle samples)."""
 import json
 import os
 import subprocess
 import sys
 
+import pytest
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def test_reference_arm_json_line():
+@pytest.mark.parametrize("cfg,n_full,nrhs,tag", [(2, 2_099_200, 1, "256x256"), (4, 2_738_019, 16, "48^3")])
+def test_reference_arm_json_line(cfg, n_full, nrhs, tag):
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                          "--warmup", "0"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+                          "--warmup", "0", "--cfg", str(cfg)], capture_output=True, text=True, timeout=900, cwd=ROOT)
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
     assert len(lines) == 1
@@ -23,10 +26,10 @@ def test_reference_arm_json_line():
     assert d["value"] > 0 and d["cpu_baseline"]["value"] == d["value"]
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"] == {"value": d["value"], "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
-    cfg = d["config"]
-    assert cfg["n_dofs"] == 2_099_200 and "256x256" in cfg["workload"]
-    assert cfg["l2"].startswith("inputs larger than L2")
-    assert {"workload", "n_dofs", "solve_mode", "options", "l2", "parallelism"} <= set(cfg)
+    c = d["config"]
+    assert c["n_dofs"] == n_full and c["nrhs"] == nrhs and tag in c["workload"]
+    assert c["l2"].startswith("inputs larger than L2")
+    assert {"workload", "n_dofs", "nrhs", "solve_mode", "options", "l2", "parallelism"} <= set(c)
 
 
 def test_l2_note_flags_reduced_sizes():
