@@ -76,7 +76,9 @@ typedef struct {
     int32_t maxit;
     double rtol;                 /* stop when ||b - A x||_2 <= rtol ||b||_2 */
     int64_t chunk_bytes;         /* device workspace budget for batched local problems (0 = auto) */
-    int32_t use_graph;           /* reserved (ignored) */
+    int32_t use_graph;           /* 1: the V-cycle inside apply / solve runs as a CUDA graph, captured
+                                    at first use (per precision and right-hand-side count) and
+                                    replayed; off while profiling */
     int32_t verbose;
     int32_t profile;             /* 1: time every kernel class with CUDA events on the stream */
     int32_t large_dense;         /* local problems above this order use multi-CTA kernels (0 = 2048) */

@@ -328,6 +328,40 @@ void ensure_solve_ws(Handle &H, int nrhs) {
     H.kx.alloc(n, s);
     H.dots.alloc(8 * nrhs, s);
     H.nrhs_ws = nrhs;
+    H.ws_gen++;   // cycle workspaces may have moved: captured V-cycles are stale
+}
+
+// One V-cycle on level 0's b -> x through a CUDA graph: captured (relaxed mode, on a private
+// stream) at first use for this precision, right-hand-side count and workspace generation,
+// then replayed on the handle's stream.
+static void vcycle_graph(Handle &H, int nrhs, bool fp32, cudaStream_t s) {
+    Handle::CycleGraph &g = H.graphs[fp32 ? 1 : 0];
+    if (!g.exec || g.nrhs != nrhs || g.gen != H.ws_gen) {
+        if (g.exec) {
+            CK(cudaGraphExecDestroy(g.exec));
+            g.exec = nullptr;
+        }
+        if (!H.cap_stream) CK(cudaStreamCreateWithFlags(&H.cap_stream, cudaStreamNonBlocking));
+        CK(cudaStreamBeginCapture(H.cap_stream, cudaStreamCaptureModeRelaxed));
+        cudaGraph_t graph = nullptr;
+        try {
+            if (fp32)
+                vcycle<float>(H, 0, nrhs, H.cap_stream);
+            else
+                vcycle<double>(H, 0, nrhs, H.cap_stream);
+        } catch (...) {
+            cudaStreamEndCapture(H.cap_stream, &graph);
+            if (graph) cudaGraphDestroy(graph);
+            throw;
+        }
+        CK(cudaStreamEndCapture(H.cap_stream, &graph));
+        const cudaError_t rc = cudaGraphInstantiate(&g.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        CK(rc);
+        g.nrhs = nrhs;
+        g.gen = H.ws_gen;
+    }
+    CK(cudaGraphLaunch(g.exec, s));
 }
 
 // z = B^{-1} r (one V-cycle) for FP64 vectors r, z of nrhs right-hand sides
@@ -335,13 +369,15 @@ void precondition(Handle &H, const double *r, double *z, int nrhs, bool fp32) {
     cudaStream_t s = H.stream;
     Level &L0 = H.levels[0];
     int64_t tot = L0.n * nrhs;
+    // graphs only without per-kernel timing or the stage profiler (their events would be captured)
+    const bool graph = H.opt.use_graph != 0 && !ktimer_enabled() && !prof_on();
     if (fp32) {
         vec_convert<double, float>(L0.b32.p, r, tot, s);
-        vcycle<float>(H, 0, nrhs, s);
+        if (graph) vcycle_graph(H, nrhs, true, s); else vcycle<float>(H, 0, nrhs, s);
         vec_convert<float, double>(z, L0.x32.p, tot, s);
     } else {
         CK(cudaMemcpyAsync(L0.b64.p, r, tot * sizeof(double), cudaMemcpyDeviceToDevice, s));
-        vcycle<double>(H, 0, nrhs, s);
+        if (graph) vcycle_graph(H, nrhs, false, s); else vcycle<double>(H, 0, nrhs, s);
         CK(cudaMemcpyAsync(z, L0.x64.p, tot * sizeof(double), cudaMemcpyDeviceToDevice, s));
     }
 }

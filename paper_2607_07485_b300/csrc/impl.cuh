@@ -108,6 +108,23 @@ struct Handle {
     // solve workspaces (FP64 outer Krylov vectors)
     int32_t nrhs_ws = 0;
     DBuf<double> kr, kz, kp, kq, kro, kx, dots;
+    // V-cycle captured as a CUDA graph (option use_graph), one per precision; re-captured when
+    // the right-hand-side count or the cycle workspaces (generation ws_gen) change
+    struct CycleGraph {
+        cudaGraphExec_t exec = nullptr;
+        int32_t nrhs = 0;
+        int64_t gen = -1;
+    } graphs[2];
+    int64_t ws_gen = 0;
+    cudaStream_t cap_stream = nullptr;
+    Handle() = default;
+    Handle(const Handle &) = delete;
+    Handle &operator=(const Handle &) = delete;
+    ~Handle() {
+        for (auto &g : graphs)
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+    }
 };
 
 // ------------------------------------------------------------------- graph.cu

@@ -76,3 +76,24 @@ def test_autotune_on_gpu_returns_options_with_the_same_cycle(tmp_path):
     z0 = amg.apply(r, fp32=0).cpu().numpy()
     assert np.linalg.norm(z1 - z0) <= vtol * np.linalg.norm(z0)
     tuned.close()
+
+
+@pytest.mark.parametrize("name", ["cfg1", "cfg3_16"])
+def test_graph_vcycle_matches_eager(name):
+    # use_graph=1: first apply captures, later ones replay; a new right-hand-side count re-captures
+    p, H, amg, vtol = _handle(name, use_graph=1)
+    eager = case(name)[2]
+    rng = np.random.default_rng(24)
+    r = torch.from_numpy(rng.standard_normal(p["n"])).to(DEV)
+    z0 = eager.apply(r, fp32=0).cpu().numpy()
+    for _ in range(2):
+        z = amg.apply(r, fp32=0).cpu().numpy()
+        assert np.linalg.norm(z - z0) <= vtol * np.linalg.norm(z0)
+    R = torch.stack([r, 2 * r])
+    Z = amg.apply(R, fp32=0).cpu().numpy()
+    assert np.linalg.norm(Z[1] - 2 * z0) <= vtol * np.linalg.norm(2 * z0)
+    b = torch.from_numpy(p["b"][0]).to(DEV)
+    _, its_e, _, rc_e = eager.solve(b, mode=0)
+    _, its_g, _, rc_g = amg.solve(b, mode=0)
+    assert rc_e == rc_g == 0 and abs(int(its_e[0]) - int(its_g[0])) <= 1
+    amg.close()
