@@ -11,7 +11,7 @@ finite elements"), cited by section / equation:
 * Section 5.1, Prop. 5.1        elementwise Gram stacking G = [G_T R_T]
 * Section 5.2                   local factors (eigen range factor used here)
 * Section 2, eq. (2.2)          disjoint aggregates (MIS(2) aggregation, two passes,
-                                Section 6 preamble: "two passes of standard aggregation")
+                                the Section 6 tests use two aggregation passes)
 * Section 2, eqs. (2.3)-(2.4)   row-touching set and G-row closure Omega_i
 * Section 5.4, Def. 5.4/Thm 5.6 element closure (= G-row closure structurally)
 * Section 2, eqs. (2.5)-(2.7)   multiplicity, weights, exact SPSD splitting
@@ -140,8 +140,8 @@ def gram_spmv(elems, G, x):
 
 
 # -----------------------------------------------------------------------------
-# Aggregation (Section 2 eq. 2.2; Section 6 preamble "two passes of standard
-# aggregation").  Reading: each pass is the distance-2 maximal-independent-set
+# Aggregation (Section 2 eq. 2.2; the Section 6 tests aggregate in two passes and name
+# no algorithm).  Reading: each pass is the distance-2 maximal-independent-set
 # aggregation of Bell, Dalton & Olson (SISC 2012) on the structural graph
 # (p ~ q iff they share an element, i.e. strength threshold 0), with priorities
 # (state, hash32(index), index); pass 2 runs on the aggregate graph.

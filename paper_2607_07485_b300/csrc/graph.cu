@@ -1,6 +1,6 @@
 // Integer set-up of one level: input validation, DOF->element maps, two-pass MIS(2)
-// aggregation (Section 2 eq. 2.2 with the Section 6 "two passes of standard
-// aggregation"), element-form closure and multiplicity (eqs. 2.3-2.5, Thm 5.6),
+// aggregation (Section 2 eq. 2.2; the Section 6 tests aggregate in two passes), element-form
+// closure and multiplicity (eqs. 2.3-2.5, Thm 5.6),
 // tau_cut (eq. 2.10), the element lists of each overlap and the smoother colouring.
 //
 // The structural graph (p ~ q iff p and q share an element) is never assembled: a
