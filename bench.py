@@ -211,8 +211,8 @@ def run_reference(args, rank):
     val = statistics.mean(t[1] for t in times)
     info = times[-1][2]
     sample = (f"FP64 oracle (NumPy/SciPy) set-up + PCG to 1e-8 per right-hand side on the same elements at "
-              f"{info['n']:,} DOFs; seconds scaled by the DOF ratio {info['scale']:.1f} (set-up and solve "
-              f"are linear in DOFs at fixed aggregate size)")
+              f"{info['n']:,} DOFs; seconds scaled by the DOF ratio {info['scale']:.1f}: a lower bound, since "
+              f"small meshes have smaller aggregates and the local work grows as their cube")
     out = dict(metric=METRIC, value=val, unit="s", n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
                ms_per_step=1000 * val, higher_is_better=False, scaling="weak", vs_baseline=None,
                dtype="f64", data="synthetic", impl="reference",
@@ -357,7 +357,8 @@ def main():
         raw, scaled, info = oracle_sample(n, args.cfg)
         cpu = dict(value=scaled, unit="s", cores=cpu_cores(), kind="oracle",
                    sample=(f"FP64 oracle set-up + PCG to 1e-8 per right-hand side on the same elements at "
-                           f"{info['n']:,} DOFs took {raw:.2f} s; scaled by the DOF ratio {info['scale']:.1f}"))
+                           f"{info['n']:,} DOFs took {raw:.2f} s; scaled by the DOF ratio {info['scale']:.1f} "
+                           f"(a lower bound: small meshes have smaller aggregates)"))
     out = dict(
         metric=METRIC, value=per_step, unit="s", n_gpus=world, steps=args.steps, warmup=args.warmup,
         ms_per_step=1000 * per_step, higher_is_better=False, scaling="weak", vs_baseline=None,
