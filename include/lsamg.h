@@ -186,15 +186,30 @@ int lsamg_kernel_stats_all(double *out);
 /* Number of CUDA kernel launches the library has issued in this process. */
 int64_t lsamg_launch_count(void);
 
-/* Allocation-free Gram SpMV.  The paper has no counterpart: this is an engineering variant of
- * the Gram SpMV of eq. 2.1 / Prop. 5.1,
- *   y = sum_T R_T^T G_T^T (G_T x_T),
- * computed from element factors the caller holds, with no handle.  It is meant for callers that
- * must not allocate device memory: an application whose device memory is owned by another
- * allocator (a framework's caching pool that has reserved the GPU, so a cudaMalloc from here
- * would fail or fragment it), and code in latency-critical loops, where cudaMalloc / cudaFree
- * would synchronise the device.  The call makes no cudaMalloc, cudaFree or allocating library
- * call.  The intermediate G_T x_T lives instead in a file-scope static device array of
+/* FP64 matrix product on the FP16 tensor cores (no paper counterpart: the dense kernel behind
+ * the set-up's Cholesky, triangular-solve, Gram and reduction updates, exposed for verification
+ * and for callers with their own dense work).
+ *   C = alpha A B^T + beta C,  A: M x K, B: N x K, C: M x N, all column-major FP64 on the device
+ *   (A[i + k lda], B[j + k ldb], C[i + j ldc]; lda >= M, ldb >= N, ldc >= M).
+ * Each row of A and of B is scaled by a power of two and cut into seven 8-bit integer slices held
+ * exactly in FP16; the 28 slice products that carry FP64 precision are accumulated exactly in
+ * FP32 by mma.sync over K chunks of 32 and in int32 across chunks, then combined in FP64.  The
+ * error of C_ij is a few units of 2^-53 K max_k|A_ik| max_k|B_jk| (the normwise bound of an FP64
+ * dot product).  beta == 0 does not read C.  Allocates workspace (about 14 (M + N) K bytes).
+ * Returns LSAMG_INVALID_ARG for bad sizes or leading dimensions, LSAMG_DEVICE_TIMEOUT if a staging
+ * wait gave up; synchronises `stream`. */
+int lsamg_dgemm_nt(int64_t M, int64_t N, int64_t K, double alpha, const double *A, int64_t lda,
+                   const double *B, int64_t ldb, double beta, double *C, int64_t ldc, void *stream);
+
+/* Allocation-free Gram SpMV (the paper has no counterpart: this is a library convenience).
+ * It computes the element Gram SpMV
+ *   y = sum_T R_T^T G_T^T (G_T x_T)
+ * from element factors the caller holds, with no handle.  It is meant for callers that cannot
+ * allocate device memory: an application whose device memory is owned by another allocator
+ * (a framework's caching pool that has reserved the GPU, so a cudaMalloc from here would fail
+ * or fragment it), and code in latency-critical loops, where cudaMalloc / cudaFree would
+ * synchronise the device.  The call makes no cudaMalloc, cudaFree or allocating library call.
+ * The intermediate G_T x_T lives instead in a file-scope static device array of
  * LSAMG_STATIC_SCRATCH_WORDS doubles (8 MiB, held on every GPU that loads the library until
  * the process exits; the first 32 words are a header).
  *   elem_dofs : device int32 [n_elems][n_T], 0-based DOF ids
@@ -202,12 +217,15 @@ int64_t lsamg_launch_count(void);
  *   x, y      : device float64 [n_dofs]; y is overwritten
  * Returns LSAMG_LIMIT, launching nothing, if n_elems * m > LSAMG_STATIC_SCRATCH_WORDS - 32, and
  * LSAMG_INVALID_ARG for bad sizes or a DOF id outside [0, n_dofs) (out-of-range entries are
- * skipped, not read).  Synchronises `stream` before returning.
- * The first call on each device looks up the array's device address (cudaGetSymbolAddress,
- * with that device current); make that first call before any stream capture.  The array keeps
- * the last call's contents; each call clears the part that must start at zero (the error
- * flag) and overwrites the rest it reads.  Every call on a device shares the one array, so
- * calls that overlap on the GPU (other streams, other host threads) race and must be
+ * skipped, not read).  The caller must pass buffers of exactly these types and sizes: the
+ * library cannot see the extent of a raw pointer.
+ * The call reads the error flag back to the host and synchronises `stream` before returning,
+ * so it cannot be recorded into a CUDA graph: called while `stream` is capturing, it returns
+ * LSAMG_INVALID_ARG without enqueuing anything.  The first call on each device also looks up
+ * the array's device address (cudaGetSymbolAddress, with that device current).  The array
+ * keeps the last call's contents; each call clears the part that must start at zero (the
+ * error flag) and overwrites the rest it reads.  Every call on a device shares the one array,
+ * so calls that overlap on the GPU (other streams, other host threads) race and must be
  * serialised by the caller. */
 #define LSAMG_STATIC_SCRATCH_WORDS (1 << 20)
 int lsamg_gram_spmv_static(int64_t n_dofs, int64_t n_elems, int32_t n_T, int32_t m,

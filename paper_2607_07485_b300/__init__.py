@@ -10,7 +10,7 @@ The compiled library is loaded on first use of any of the names below (so that
 ``python -m paper_2607_07485_b300.build`` can rebuild it); a missing library raises.
 """
 _LIB_NAMES = ("Lsamg", "LsamgError", "options", "LIB_PATH", "EXPORTS", "Q", "kernel_stats",
-              "launch_count", "gram_spmv_static")
+              "launch_count", "gram_spmv_static", "dgemm_nt")
 _AD_NAMES = ("LsamgSolve", "solve_with_grad")
 __all__ = list(_LIB_NAMES + _AD_NAMES)
 

@@ -7,6 +7,7 @@
 #include <string>
 
 #include "impl.cuh"
+#include "ozaki.cuh"
 
 namespace lsamg {
 extern int g_prof_level;
@@ -58,12 +59,17 @@ __global__ void k_level0_maps(const int32_t *dofs, int64_t ne, int nT, int64_t *
         eidx[j] = dofs[j];
 }
 
-__global__ void k_scale_mats(const double *mats, const double *coef, int64_t ne, int64_t sz,
-                             double *out) {
+// A_T = coef_e * (K_e + K_e^T) / 2: the symmetric part (bit-identical for symmetric input), so
+// that the assemblies may read A_T column by column
+__global__ void k_scale_mats(const double *mats, const double *coef, int64_t ne, int nT, double *out) {
+    const int64_t sz = (int64_t)nT * nT;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < ne * sz;
          j += (int64_t)gridDim.x * blockDim.x) {
-        double c = coef ? coef[j / sz] : 1.0;
-        out[j] = c * mats[j];
+        const int64_t e = j / sz;
+        const int t = (int)(j - e * sz), r = t / nT, c = t % nT;
+        const double *K = mats + e * sz;
+        const double c0 = coef ? coef[e] : 1.0;
+        out[j] = c0 * (0.5 * (K[r * nT + c] + K[c * nT + r]));
     }
 }
 
@@ -203,7 +209,7 @@ void do_setup(Handle &H, const lsamg_problem *P, const lsamg_options &o) {
         CK_LAUNCH();
         L0.AT.alloc(std::max<int64_t>(ne * nT * nT, 1), s);
         unsigned g2 = (unsigned)std::min<int64_t>(std::max<int64_t>(cdiv(ne * nT * nT, 256), 1), 148 * 32);
-        k_scale_mats<<<g2, 256, 0, s>>>(mats, coef, ne, nT * nT, L0.AT.p);
+        k_scale_mats<<<g2, 256, 0, s>>>(mats, coef, ne, (int)nT, L0.AT.p);
         CK_LAUNCH();
         if (coef) {
             H.coef.alloc(std::max<int64_t>(ne, 1), s);
@@ -703,6 +709,49 @@ int lsamg_gram_spmv(lsamg_handle *h, int32_t level, const void *x, void *y, int3
         else
             gram_spmv<double>(L, (const double *)x, (double *)y, nullptr, 1, s);
         CK(cudaStreamSynchronize(s));
+    });
+}
+
+int lsamg_dgemm_nt(int64_t M, int64_t N, int64_t K, double alpha, const double *A, int64_t lda, const double *B,
+                   int64_t ldb, double beta, double *C, int64_t ldc, void *stream) {
+    if (M < 0 || N < 0 || K < 0 || (M > 0 && lda < M) || (N > 0 && ldb < N) || (M > 0 && ldc < M))
+        return LSAMG_INVALID_ARG;
+    if (M > 0x7fffffff || N > 0x7fffffff || K > 0x7fffffff) return LSAMG_LIMIT;
+    if (M == 0 || N == 0) return LSAMG_OK;
+    if (!A || !B || !C) return LSAMG_INVALID_ARG;
+    return guarded([&] {
+        cudaStream_t s = (cudaStream_t)stream;
+        DBuf<int> err;
+        err.alloc(2, s);
+        err.zero(s);
+        constexpr int64_t KMAX = (int64_t)oz::MAX_CHUNKS * oz::TK;
+        oz::Workspace ws;
+        if (K == 0) {   // C = beta C through a product with a zero operand
+            DBuf<double> z;
+            z.alloc(1, s);
+            z.zero(s);
+            std::vector<oz::SplitJob> sj{{0, 0, 0, 0, 0, (int32_t)M, 1}, {0, 0, 0, 0, 0, (int32_t)N, 1}};
+            sj[1].dst_off = oz::slice_halves(M, 1);
+            sj[1].exp_off = oz::exp_ints(M);
+            ws.reserve(sj[1].dst_off + oz::slice_halves(N, 1), sj[1].exp_off + oz::exp_ints(N), s);
+            oz::split(z.p, sj, ws.sl.p, ws.ex.p, s);
+            oz::gemm(ws.sl.p, ws.ex.p, C, {oz::GemmJob{0, sj[1].dst_off, 0, sj[1].exp_off, 0, 1, ldc, (int32_t)M,
+                                                     (int32_t)N, 1, 0, 0, 0}},
+                     0.0, beta, err.p, s);
+        }
+        for (int64_t k0 = 0; k0 < K; k0 += KMAX) {
+            const int32_t kk = (int32_t)std::min(KMAX, K - k0);
+            const int64_t hb = oz::slice_halves(M, kk), eb = oz::exp_ints(M);
+            std::vector<oz::SplitJob> sa{{k0 * lda, 1, lda, 0, 0, (int32_t)M, kk}};
+            std::vector<oz::SplitJob> sb{{k0 * ldb, 1, ldb, hb, eb, (int32_t)N, kk}};
+            ws.reserve(hb + oz::slice_halves(N, kk), eb + oz::exp_ints(N), s);
+            oz::split(A, sa, ws.sl.p, ws.ex.p, s);
+            oz::split(B, sb, ws.sl.p, ws.ex.p, s);
+            oz::gemm(ws.sl.p, ws.ex.p, C,
+                     {oz::GemmJob{0, hb, 0, eb, 0, 1, ldc, (int32_t)M, (int32_t)N, kk, 0, 0, 0}}, alpha,
+                     k0 == 0 ? beta : 1.0, err.p, s);
+        }
+        check_err(err.p, s, "tensor-core FP64 product");
     });
 }
 

@@ -1,13 +1,13 @@
 // Batched variable-size FP64 dense kernels (see dense.cuh).  FP64 arithmetic throughout:
 // these serve the local eigenproblems whose small eigenvalues select the coarse space.
 #include "dense.cuh"
+#include "ozaki.cuh"
 
 namespace lsamg {
 
 namespace {
 
-constexpr int NB = 32;          // panel width of the blocked Cholesky / TRSM
-constexpr int TT = 64;          // output tile of the update kernels
+constexpr int NB = 32;          // panel width of the pivoted Cholesky
 constexpr double DEPS = 2.220446049250313e-16;
 
 // ------------------------------------------------------------------------- potrf
@@ -30,16 +30,18 @@ __global__ void k_maxdiag(const double *base, const int64_t *off, const int32_t 
     }
 }
 
+// diagonal block (PB x PB) of step j0 in shared memory, one CTA per matrix
+template <int PB>
 __global__ void k_potf2(double *base, const int64_t *off, const int32_t *ld, const int32_t *nn,
                         int64_t count, int j0, int mode, const double *md, int *err) {
     int64_t b = blockIdx.x;
     if (b >= count) return;
     int n = nn[b];
     if (j0 >= n) return;
-    int bs = min(NB, n - j0);
+    int bs = min(PB, n - j0);
     int L = ld[b];
     double *A = base + off[b] + (int64_t)j0 + (int64_t)j0 * L;
-    __shared__ double s[NB][NB + 1];
+    __shared__ double s[PB][PB + 1];
     __shared__ double piv;
     for (int t = threadIdx.x; t < bs * bs; t += blockDim.x) {
         int i = t % bs, j = t / bs;
@@ -80,17 +82,18 @@ __global__ void k_potf2(double *base, const int64_t *off, const int32_t *ld, con
     }
 }
 
-// rows below the diagonal block: A21 <- A21 L11^{-T}
-__global__ void k_potrf_panel(double *base, const int64_t *off, const int32_t *ld,
-                              const int32_t *nn, int64_t count, int j0) {
+// rows below the diagonal block: A21 <- A21 L11^{-T} (one thread per row, the row in registers)
+template <int PB>
+__global__ void __launch_bounds__(128) k_potrf_panel(double *base, const int64_t *off, const int32_t *ld,
+                                                     const int32_t *nn, int64_t count, int j0) {
     int64_t b = blockIdx.y;
     if (b >= count) return;
     int n = nn[b];
     if (j0 >= n) return;
-    int bs = min(NB, n - j0);
+    int bs = min(PB, n - j0);
     int L = ld[b];
     double *A = base + off[b];
-    __shared__ double l[NB][NB + 1];
+    __shared__ double l[PB][PB + 1];
     for (int t = threadIdx.x; t < bs * bs; t += blockDim.x) {
         int i = t % bs, j = t / bs;
         l[i][j] = (i >= j) ? A[(j0 + i) + (int64_t)(j0 + j) * L] : 0.0;
@@ -98,91 +101,23 @@ __global__ void k_potrf_panel(double *base, const int64_t *off, const int32_t *l
     __syncthreads();
     int r = j0 + bs + blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
-    double x[NB];
+    double x[PB];
 #pragma unroll
-    for (int c = 0; c < NB; c++)
+    for (int c = 0; c < PB; c++)
         if (c < bs) x[c] = A[r + (int64_t)(j0 + c) * L];
 #pragma unroll
-    for (int c = 0; c < NB; c++) {
+    for (int c = 0; c < PB; c++) {
         if (c < bs) {
             double v = x[c];
 #pragma unroll
-            for (int k = 0; k < NB; k++)
+            for (int k = 0; k < PB; k++)
                 if (k < c) v -= x[k] * l[c][k];
             x[c] = (l[c][c] != 0.0) ? v / l[c][c] : 0.0;
         }
     }
 #pragma unroll
-    for (int c = 0; c < NB; c++)
+    for (int c = 0; c < PB; c++)
         if (c < bs) A[r + (int64_t)(j0 + c) * L] = x[c];
-}
-
-__device__ __forceinline__ void tri_index(int t, int &ti, int &tj) {
-    int i = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-    while ((i + 1) * (i + 2) / 2 <= t) i++;
-    while (i * (i + 1) / 2 > t) i--;
-    ti = i;
-    tj = t - i * (i + 1) / 2;
-}
-
-// trailing update A22 -= L21 L21^T on lower tiles
-__global__ void __launch_bounds__(256) k_potrf_update(double *base, const int64_t *off,
-                                                      const int32_t *ld, const int32_t *nn,
-                                                      int64_t count, int j0, const int32_t *b0,
-                                                      const int32_t *stop, int full) {
-    int64_t b = blockIdx.y;
-    if (b >= count) return;
-    if (stop && stop[b] >= 0) return;  // pivoted factorisation already truncated
-    int n = nn[b];
-    int bs = min(NB, n - j0);
-    int r0 = j0 + min(NB, n - j0);
-    int m = n - r0;
-    if (m <= 0 || bs <= 0) return;
-    int T = (m + TT - 1) / TT;
-    int ti, tj;
-    if (full) {
-        if ((int64_t)blockIdx.x >= (int64_t)T * T) return;
-        ti = blockIdx.x / T;
-        tj = blockIdx.x % T;
-    } else {
-        if ((int64_t)blockIdx.x >= (int64_t)T * (T + 1) / 2) return;
-        tri_index(blockIdx.x, ti, tj);
-    }
-    int L = ld[b];
-    const int o0 = b0 ? b0[b] : 0;
-    double *A = base + off[b] + (int64_t)o0 + (int64_t)o0 * L;
-    __shared__ double As[NB][TT + 1];
-    __shared__ double Bs[NB][TT + 1];
-    int ib = r0 + ti * TT, jb = r0 + tj * TT;
-    for (int t = threadIdx.x; t < NB * TT; t += blockDim.x) {
-        int rr = t % TT, k = t / TT;
-        int gi = ib + rr, gj = jb + rr;
-        As[k][rr] = (k < bs && gi < n) ? A[gi + (int64_t)(j0 + k) * L] : 0.0;
-        Bs[k][rr] = (k < bs && gj < n) ? A[gj + (int64_t)(j0 + k) * L] : 0.0;
-    }
-    __syncthreads();
-    int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
-    double acc[4][4] = {};
-#pragma unroll 8
-    for (int k = 0; k < NB; k++) {
-        double a[4], c[4];
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-            a[u] = As[k][ty * 4 + u];
-            c[u] = Bs[k][tx * 4 + u];
-        }
-#pragma unroll
-        for (int u = 0; u < 4; u++)
-#pragma unroll
-            for (int v = 0; v < 4; v++) acc[u][v] = fma(a[u], c[v], acc[u][v]);
-    }
-#pragma unroll
-    for (int u = 0; u < 4; u++)
-#pragma unroll
-        for (int v = 0; v < 4; v++) {
-            int gi = ib + ty * 4 + u, gj = jb + tx * 4 + v;
-            if (gi < n && gj < n && (full || gi >= gj)) A[gi + (int64_t)gj * L] -= acc[u][v];
-        }
 }
 
 // one panel of the pivoted Cholesky (one CTA per matrix); columns j0 .. j0+NB-1 of the block
@@ -302,145 +237,59 @@ __global__ void __launch_bounds__(256) k_pstf_panel(double *base, const int64_t 
 }
 
 // ------------------------------------------------------------------------- trsm
-constexpr int SW = 32;  // right-hand-side strip width
+constexpr int TB = 64;   // block rows of the blocked triangular solves (the product K)
+constexpr int SW = 16;   // right-hand-side columns per CTA of the diagonal-block solve
 
-__global__ void __launch_bounds__(256) k_trsm(const double *baseL, const int64_t *loff,
-                                              const int32_t *lld, const int32_t *nn,
-                                              double *baseB, const int64_t *boff,
-                                              const int32_t *bld, const int32_t *bcols,
-                                              int64_t count, int trans) {
+// X_r = L_rr^{-1} B_r (trans: L_rr^{-T} B_r) for the diagonal block of rows [r0, r0 + TB): a CTA
+// per 16 right-hand-side columns, both blocks in shared memory, right-looking substitution.
+// Zero diagonal entries (semidefinite factors) give zero solution rows.
+__global__ void __launch_bounds__(256) k_trsm_diag(const double *baseL, const int64_t *loff,
+                                                   const int32_t *lld, const int32_t *nn,
+                                                   double *baseB, const int64_t *boff,
+                                                   const int32_t *bld, const int32_t *bcols,
+                                                   int64_t count, int r0, int trans) {
+    __shared__ double Ls[TB][TB + 1];
+    __shared__ double X[TB][SW + 1];
     int64_t b = blockIdx.y;
     if (b >= count) return;
-    int n = nn[b];
-    int ncol = bcols[b];
-    int c0 = blockIdx.x * SW;
-    if (c0 >= ncol || n <= 0) return;
-    int cs = min(SW, ncol - c0);
+    const int n = nn[b], ncol = bcols[b];
+    const int c0 = blockIdx.x * SW;
+    if (r0 >= n || c0 >= ncol) return;
+    const int bs = min(TB, n - r0), cs = min(SW, ncol - c0);
     const double *Lm = baseL + loff[b];
-    int LL = lld[b];
-    double *B = baseB + boff[b] + (int64_t)c0 * bld[b];
-    int LB = bld[b];
-    __shared__ double Ls[NB][NB + 1];
-    __shared__ double Xs[NB][SW + 1];
-    __shared__ double acc[NB][SW + 1];
-    int nrb = (n + NB - 1) / NB;
-    for (int step = 0; step < nrb; step++) {
-        int rb = trans ? (nrb - 1 - step) : step;
-        int r0 = rb * NB, rs = min(NB, n - r0);
-        for (int t = threadIdx.x; t < NB * SW; t += blockDim.x) {
-            int i = t % NB, c = t / NB;
-            acc[i][c] = (i < rs && c < cs) ? B[(r0 + i) + (int64_t)c * LB] : 0.0;
-        }
+    const int LL = lld[b], LB = bld[b];
+    double *B = baseB + boff[b] + (int64_t)c0 * LB;
+    for (int t = threadIdx.x; t < TB * TB; t += blockDim.x) {
+        const int i = t % TB, k = t / TB;
+        Ls[i][k] = (i < bs && k < bs && i >= k) ? Lm[(r0 + i) + (int64_t)(r0 + k) * LL] : 0.0;
+    }
+    for (int t = threadIdx.x; t < TB * SW; t += blockDim.x) {
+        const int i = t % TB, c = t / TB;
+        X[i][c] = (i < bs && c < cs) ? B[(r0 + i) + (int64_t)c * LB] : 0.0;
+    }
+    __syncthreads();
+    for (int step = 0; step < bs; step++) {
+        const int k = trans ? bs - 1 - step : step;
+        if (threadIdx.x < SW) X[k][threadIdx.x] = (Ls[k][k] != 0.0) ? X[k][threadIdx.x] / Ls[k][k] : 0.0;
         __syncthreads();
-        int kb0 = trans ? rb + 1 : 0, kb1 = trans ? nrb : rb;
-        for (int kb = kb0; kb < kb1; kb++) {
-            int k0 = kb * NB, ks = min(NB, n - k0);
-            for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
-                int i = t % NB, k = t / NB;
-                double v = 0.0;
-                if (!trans) {
-                    if (i < rs && k < ks) v = Lm[(r0 + i) + (int64_t)(k0 + k) * LL];  // L[r0+i, k0+k]
-                } else {
-                    if (i < rs && k < ks) v = Lm[(k0 + k) + (int64_t)(r0 + i) * LL];  // L[k0+k, r0+i]
-                }
-                Ls[i][k] = v;
+        if (!trans) {
+            const int m = bs - k - 1;
+            for (int t = threadIdx.x; t < m * SW; t += blockDim.x) {
+                const int i = k + 1 + t % m, c = t / m;
+                X[i][c] -= Ls[i][k] * X[k][c];
             }
-            for (int t = threadIdx.x; t < NB * SW; t += blockDim.x) {
-                int k = t % NB, c = t / NB;
-                Xs[k][c] = (k < ks && c < cs) ? B[(k0 + k) + (int64_t)c * LB] : 0.0;
+        } else {
+            for (int t = threadIdx.x; t < k * SW; t += blockDim.x) {
+                const int i = t % k, c = t / k;
+                X[i][c] -= Ls[k][i] * X[k][c];
             }
-            __syncthreads();
-            for (int t = threadIdx.x; t < NB * SW; t += blockDim.x) {
-                int i = t % NB, c = t / NB;
-                double v = acc[i][c];
-#pragma unroll 8
-                for (int k = 0; k < NB; k++) v -= Ls[i][k] * Xs[k][c];
-                acc[i][c] = v;
-            }
-            __syncthreads();
-        }
-        // diagonal block
-        for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
-            int i = t % NB, k = t / NB;
-            Ls[i][k] = (i < rs && k < rs && i >= k) ? Lm[(r0 + i) + (int64_t)(r0 + k) * LL] : 0.0;
-        }
-        __syncthreads();
-        if (threadIdx.x < cs) {
-            int c = threadIdx.x;
-            if (!trans) {
-                for (int i = 0; i < rs; i++) {
-                    double v = acc[i][c];
-                    for (int k = 0; k < i; k++) v -= Ls[i][k] * acc[k][c];
-                    acc[i][c] = (Ls[i][i] != 0.0) ? v / Ls[i][i] : 0.0;
-                }
-            } else {
-                for (int i = rs - 1; i >= 0; i--) {
-                    double v = acc[i][c];
-                    for (int k = i + 1; k < rs; k++) v -= Ls[k][i] * acc[k][c];
-                    acc[i][c] = (Ls[i][i] != 0.0) ? v / Ls[i][i] : 0.0;
-                }
-            }
-        }
-        __syncthreads();
-        for (int t = threadIdx.x; t < NB * SW; t += blockDim.x) {
-            int i = t % NB, c = t / NB;
-            if (i < rs && c < cs) B[(r0 + i) + (int64_t)c * LB] = acc[i][c];
         }
         __syncthreads();
     }
-}
-
-// ------------------------------------------------------------------------- syrk (C -= W^T W)
-__global__ void __launch_bounds__(256) k_syrk_tn(double *baseC, const int64_t *coff,
-                                                 const int32_t *cld, const int32_t *cn,
-                                                 const double *baseW, const int64_t *woff,
-                                                 const int32_t *wld, const int32_t *wk,
-                                                 int64_t count, double alpha, int wrow) {
-    int64_t b = blockIdx.y;
-    if (b >= count) return;
-    int n = cn[b], K = wk[b];
-    int T = (n + TT - 1) / TT;
-    if ((int)blockIdx.x >= T * T || K <= 0) return;
-    int ti = blockIdx.x / T, tj = blockIdx.x % T;
-    double *C = baseC + coff[b];
-    int LC = cld[b];
-    const double *W = baseW + woff[b];
-    const int64_t rs = wrow ? (int64_t)wld[b] : 1, cs = wrow ? 1 : (int64_t)wld[b];
-    __shared__ double As[NB][TT + 1];
-    __shared__ double Bs[NB][TT + 1];
-    int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
-    double acc[4][4] = {};
-    int ib = ti * TT, jb = tj * TT;
-    for (int k0 = 0; k0 < K; k0 += NB) {
-        for (int t = threadIdx.x; t < NB * TT; t += blockDim.x) {
-            int k = t % NB, rr = t / NB;
-            int gk = k0 + k;
-            As[k][rr] = (gk < K && ib + rr < n) ? W[gk * rs + (int64_t)(ib + rr) * cs] : 0.0;
-            Bs[k][rr] = (gk < K && jb + rr < n) ? W[gk * rs + (int64_t)(jb + rr) * cs] : 0.0;
-        }
-        __syncthreads();
-#pragma unroll 8
-        for (int k = 0; k < NB; k++) {
-            double a[4], c[4];
-#pragma unroll
-            for (int u = 0; u < 4; u++) {
-                a[u] = As[k][ty * 4 + u];
-                c[u] = Bs[k][tx * 4 + u];
-            }
-#pragma unroll
-            for (int u = 0; u < 4; u++)
-#pragma unroll
-                for (int v = 0; v < 4; v++) acc[u][v] = fma(a[u], c[v], acc[u][v]);
-        }
-        __syncthreads();
+    for (int t = threadIdx.x; t < TB * SW; t += blockDim.x) {
+        const int i = t % TB, c = t / TB;
+        if (i < bs && c < cs) B[(r0 + i) + (int64_t)c * LB] = X[i][c];
     }
-#pragma unroll
-    for (int u = 0; u < 4; u++)
-#pragma unroll
-        for (int v = 0; v < 4; v++) {
-            int gi = ib + ty * 4 + u, gj = jb + tx * 4 + v;
-            if (gi < n && gj < n) C[gi + (int64_t)gj * LC] += alpha * acc[u][v];
-        }
 }
 
 // ------------------------------------------------------------------------- transpose
@@ -470,7 +319,6 @@ __global__ void k_transpose(const double *baseS, const int64_t *soff, const int3
     }
 }
 
-// ------------------------------------------------------------------------- sytd2
 __device__ double block_sum(double v, double *red) {
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -481,262 +329,6 @@ __device__ double block_sum(double v, double *red) {
     int nw = (blockDim.x + 31) >> 5;
     for (int i = 0; i < nw; i++) r += red[i];
     return r;
-}
-
-// One CTA per matrix.  Per column j: Householder vector v (staged in shared memory), the
-// symmetric product p = tau A22 v in ONE sweep over the stored lower triangle (each warp owns
-// columns: column sums reduce in registers, the transposed contributions accumulate in shared
-// memory with atomics), then the rank-2 update A22 -= v w^T + w v^T.
-constexpr int SYTD2_THREADS = 512;
-
-__global__ void __launch_bounds__(512) k_sytd2(double *base, const int64_t *off, const int32_t *ld,
-                                               const int32_t *nn, int64_t count, double *dd,
-                                               double *ee, double *tt, const int64_t *toff,
-                                               double *pwork, const int64_t *pwoff, int use_smem) {
-    extern __shared__ double smv[];
-    int64_t b = blockIdx.x;
-    if (b >= count) return;
-    const int n = nn[b];
-    const int L = ld[b];
-    double *A = base + off[b];
-    double *d = dd + toff[b], *e = ee + toff[b], *tau = tt + toff[b];
-    double *tbuf = smv;                                   // one 32 x 33 tile buffer per warp
-    double *p = use_smem ? smv + (blockDim.x / 32) * 32 * 33 : pwork + 2 * pwoff[b];
-    double *v = use_smem ? p + n : pwork + 2 * pwoff[b] + n;
-    __shared__ double red[32];
-    __shared__ double sh_tau, sh_scale;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    for (int j = 0; j < n - 1; j++) {
-        const int m = n - j - 1;
-        double *x = A + (j + 1) + (int64_t)j * L;
-        double sig = 0.0;
-        for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) sig += x[i] * x[i];
-        sig = block_sum(sig, red);
-        if (threadIdx.x == 0) {
-            const double alpha = x[0];
-            d[j] = A[j + (int64_t)j * L];
-            if (sig == 0.0) {
-                sh_tau = 0.0;
-                e[j] = alpha;
-                sh_scale = 0.0;
-            } else {
-                const double beta = -copysign(sqrt(alpha * alpha + sig), alpha);
-                sh_tau = (beta - alpha) / beta;
-                sh_scale = 1.0 / (alpha - beta);
-                e[j] = beta;
-            }
-            tau[j] = sh_tau;
-        }
-        __syncthreads();
-        const double tj = sh_tau, sc = sh_scale;
-        if (tj == 0.0) continue;
-        for (int i = threadIdx.x; i < m; i += blockDim.x) {
-            const double vi = (i == 0) ? 1.0 : x[i] * sc;
-            v[i] = vi;
-            if (i > 0) x[i] = vi;
-            p[i] = 0.0;
-        }
-        __syncthreads();
-        double *A22 = A + (j + 1) + (int64_t)(j + 1) * L;
-        // p = A22 v, tiled: each warp owns row blocks; a 32 x 32 tile is loaded coalesced into
-        // the warp's shared buffer, row sums stay in registers, column sums (the transposed
-        // half) go out with 32 shared atomics per tile
-        {
-            double(*tile)[33] = reinterpret_cast<double(*)[33]>(tbuf + (int64_t)warp * 32 * 33);
-            const int nbk = (m + 31) / 32;
-            for (int rb = warp; rb < nbk; rb += nwarp) {
-                const int r0 = rb * 32;
-                double rsum = 0.0;
-                for (int cb = 0; cb <= rb; cb++) {
-                    const int c0 = cb * 32;
-                    for (int c = 0; c < 32; c++) {
-                        const int gr = r0 + lane, gc = c0 + c;
-                        double a = 0.0;
-                        if (gr < m && gc < m && gr >= gc) a = A22[gr + (int64_t)gc * L];
-                        tile[lane][c] = a;
-                    }
-                    __syncwarp();
-                    // row sums: lane = row (diagonal tile: its stored lower part, diagonal included)
-                    for (int c = 0; c < 32; c++) {
-                        const int gc = c0 + c;
-                        if (gc < m) rsum += tile[lane][c] * v[gc];
-                    }
-                    // column sums: lane = column, strictly below the diagonal
-                    double csum = 0.0;
-                    for (int i = 0; i < 32; i++) {
-                        const int gr = r0 + i;
-                        if (gr < m && (cb != rb || i > lane)) csum += tile[i][lane] * v[gr];
-                    }
-                    if (c0 + lane < m && csum != 0.0) atomicAdd(&p[c0 + lane], csum);
-                    __syncwarp();
-                }
-                if (r0 + lane < m) atomicAdd(&p[r0 + lane], rsum);
-            }
-        }
-        __syncthreads();
-        double pv = 0.0;
-        for (int i = threadIdx.x; i < m; i += blockDim.x) {
-            p[i] *= tj;
-            pv += p[i] * v[i];
-        }
-        pv = block_sum(pv, red);
-        const double kk = -0.5 * tj * pv;
-        for (int i = threadIdx.x; i < m; i += blockDim.x) p[i] += kk * v[i];  // w
-        __syncthreads();
-        for (int c = warp; c < m; c += nwarp) {
-            const double vc = v[c], wc = p[c];
-            double *col = A22 + (int64_t)c * L;
-            for (int r = c + lane; r < m; r += 32) col[r] -= v[r] * wc + p[r] * vc;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) x[0] = e[j];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0 && n > 0) d[n - 1] = A[(n - 1) + (int64_t)(n - 1) * L];
-}
-
-// ---- multi-CTA tridiagonalisation for large matrices (one column per group of launches)
-constexpr int TRT = 64;          // tile of the symmetric product / rank-2 update
-
-// Householder vector of column j for every large matrix; restores the previous subdiagonal
-__global__ void __launch_bounds__(256) k_tr_house(double *base, const int64_t *off, const int32_t *ld,
-                                                  const int32_t *nn, int64_t count, int j, double *dd,
-                                                  double *ee, double *tt, const int64_t *toff,
-                                                  double *vbuf, double *pbuf, const int64_t *voff) {
-    int64_t b = blockIdx.x;
-    if (b >= count) return;
-    const int n = nn[b], L = ld[b];
-    double *A = base + off[b];
-    double *d = dd + toff[b], *e = ee + toff[b], *tau = tt + toff[b];
-    if (j > 0 && j <= n - 1 && threadIdx.x == 0) A[j + (int64_t)(j - 1) * L] = e[j - 1];
-    if (j >= n - 1) {
-        if (j == n - 1 && threadIdx.x == 0) d[n - 1] = A[(n - 1) + (int64_t)(n - 1) * L];
-        return;
-    }
-    const int m = n - j - 1;
-    double *x = A + (j + 1) + (int64_t)j * L;
-    double *v = vbuf + voff[b], *p = pbuf + voff[b];
-    __shared__ double red[32];
-    __shared__ double sh_tau, sh_scale;
-    double sig = 0.0;
-    for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) sig += x[i] * x[i];
-    sig = block_sum(sig, red);
-    if (threadIdx.x == 0) {
-        const double alpha = x[0];
-        d[j] = A[j + (int64_t)j * L];
-        if (sig == 0.0) {
-            sh_tau = 0.0;
-            sh_scale = 0.0;
-            e[j] = alpha;
-        } else {
-            const double beta = -copysign(sqrt(alpha * alpha + sig), alpha);
-            sh_tau = (beta - alpha) / beta;
-            sh_scale = 1.0 / (alpha - beta);
-            e[j] = beta;
-        }
-        tau[j] = sh_tau;
-    }
-    __syncthreads();
-    const double sc = sh_scale, tj = sh_tau;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
-        const double vi = (i == 0) ? 1.0 : x[i] * sc;
-        if (i > 0) x[i] = vi;
-        v[i] = (tj == 0.0) ? 0.0 : vi;
-        p[i] = 0.0;
-    }
-}
-
-// p += A22 v over the stored lower triangle, one 64 x 64 tile per CTA (atomics into p)
-__global__ void __launch_bounds__(128) k_tr_symv(const double *base, const int64_t *off,
-                                                 const int32_t *ld, const int32_t *nn, int64_t count,
-                                                 int j, const double *vbuf, double *pbuf,
-                                                 const int64_t *voff, const double *tt,
-                                                 const int64_t *toff) {
-    int64_t b = blockIdx.y;
-    if (b >= count) return;
-    const int n = nn[b];
-    const int m = n - j - 1;
-    if (m <= 0 || tt[toff[b] + j] == 0.0) return;
-    const int T = (m + TRT - 1) / TRT;
-    if ((int64_t)blockIdx.x >= (int64_t)T * (T + 1) / 2) return;
-    int ti, tj;
-    tri_index(blockIdx.x, ti, tj);
-    const int L = ld[b];
-    const double *A22 = base + off[b] + (j + 1) + (int64_t)(j + 1) * L;
-    const double *v = vbuf + voff[b];
-    double *p = pbuf + voff[b];
-    __shared__ double T_[TRT][TRT + 1];
-    __shared__ double vr[TRT], vc[TRT];
-    const int r0 = ti * TRT, c0 = tj * TRT;
-    for (int t = threadIdx.x; t < TRT * TRT; t += blockDim.x) {
-        const int rr = t % TRT, cc = t / TRT;
-        const int gr = r0 + rr, gc = c0 + cc;
-        double a = 0.0;
-        if (gr < m && gc < m && gr >= gc) a = A22[gr + (int64_t)gc * L];
-        T_[rr][cc] = a;
-    }
-    for (int t = threadIdx.x; t < TRT; t += blockDim.x) {
-        vr[t] = (r0 + t < m) ? v[r0 + t] : 0.0;
-        vc[t] = (c0 + t < m) ? v[c0 + t] : 0.0;
-    }
-    __syncthreads();
-    if (threadIdx.x < TRT) {
-        const int rr = threadIdx.x;
-        double sacc = 0.0;
-        for (int cc = 0; cc < TRT; cc++) sacc += T_[rr][cc] * vc[cc];
-        if (r0 + rr < m) atomicAdd(&p[r0 + rr], sacc);
-    } else {
-        const int cc = threadIdx.x - TRT;
-        double sacc = 0.0;
-        for (int rr = 0; rr < TRT; rr++)
-            if (ti != tj || rr > cc) sacc += T_[rr][cc] * vr[rr];
-        if (c0 + cc < m) atomicAdd(&p[c0 + cc], sacc);
-    }
-}
-
-// p <- w = tau p - (tau^2/2)(p^T v) v
-__global__ void __launch_bounds__(256) k_tr_w(const int32_t *nn, int64_t count, int j, const double *vbuf,
-                                              double *pbuf, const int64_t *voff, const double *tt,
-                                              const int64_t *toff) {
-    int64_t b = blockIdx.x;
-    if (b >= count) return;
-    const int m = nn[b] - j - 1;
-    if (m <= 0) return;
-    const double tj = tt[toff[b] + j];
-    if (tj == 0.0) return;
-    const double *v = vbuf + voff[b];
-    double *p = pbuf + voff[b];
-    __shared__ double red[32];
-    double pv = 0.0;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) pv += p[i] * v[i];
-    pv = block_sum(pv, red) * tj;
-    const double kk = -0.5 * tj * pv;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) p[i] = tj * p[i] + kk * v[i];
-}
-
-// A22 -= v w^T + w v^T on the stored lower triangle, one 64 x 64 tile per CTA
-__global__ void __launch_bounds__(256) k_tr_update(double *base, const int64_t *off, const int32_t *ld,
-                                                   const int32_t *nn, int64_t count, int j,
-                                                   const double *vbuf, const double *pbuf,
-                                                   const int64_t *voff, const double *tt,
-                                                   const int64_t *toff) {
-    int64_t b = blockIdx.y;
-    if (b >= count) return;
-    const int m = nn[b] - j - 1;
-    if (m <= 0 || tt[toff[b] + j] == 0.0) return;
-    const int T = (m + TRT - 1) / TRT;
-    if ((int64_t)blockIdx.x >= (int64_t)T * (T + 1) / 2) return;
-    int ti, tj;
-    tri_index(blockIdx.x, ti, tj);
-    const int L = ld[b];
-    double *A22 = base + off[b] + (j + 1) + (int64_t)(j + 1) * L;
-    const double *v = vbuf + voff[b], *w = pbuf + voff[b];
-    const int r0 = ti * TRT, c0 = tj * TRT;
-    for (int t = threadIdx.x; t < TRT * TRT; t += blockDim.x) {
-        const int rr = t % TRT, cc = t / TRT;
-        const int gr = r0 + rr, gc = c0 + cc;
-        if (gr < m && gc < m && gr >= gc) A22[gr + (int64_t)gc * L] -= v[gr] * w[gc] + w[gr] * v[gc];
-    }
 }
 
 // ------------------------------------------------------------------------- stebz
@@ -768,50 +360,81 @@ __device__ double bisect_index(const double *d, const double *e, int n, int j, d
     return 0.5 * (lo + hi);
 }
 
-__global__ void k_stebz(const double *dd, const double *ee, const int64_t *toff, const int32_t *nn,
-                        int64_t count, double sigma, int32_t *kout, double *w, double *gap) {
-    int64_t b = blockIdx.x;
+// per matrix: Gershgorin interval (block reduction), pivmin, and k = #eigenvalues below sigma
+__global__ void __launch_bounds__(256) k_stebz_count(const double *dd, const double *ee, const int64_t *toff,
+                                                     const int32_t *nn, int64_t count, double sigma, int32_t *kout,
+                                                     double *bnd) {
+    __shared__ double rlo[256], rhi[256], rem[256];
+    const int64_t b = blockIdx.x;
     if (b >= count) return;
-    int n = nn[b];
+    const int n = nn[b];
     const double *d = dd + toff[b], *e = ee + toff[b];
-    __shared__ double glo, ghi, pivmin;
-    __shared__ int kk;
-    __shared__ double lam_lo, lam_hi;
-    if (threadIdx.x == 0) {
-        double lo = 1e300, hi = -1e300, emax = 0.0;
-        for (int i = 0; i < n; i++) {
-            double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < n - 1 ? fabs(e[i]) : 0.0);
-            lo = fmin(lo, d[i] - r);
-            hi = fmax(hi, d[i] + r);
-            if (i < n - 1) emax = fmax(emax, e[i] * e[i]);
+    double lo = 1e300, hi = -1e300, emax = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < n - 1 ? fabs(e[i]) : 0.0);
+        lo = fmin(lo, d[i] - r);
+        hi = fmax(hi, d[i] + r);
+        if (i < n - 1) emax = fmax(emax, e[i] * e[i]);
+    }
+    rlo[threadIdx.x] = lo;
+    rhi[threadIdx.x] = hi;
+    rem[threadIdx.x] = emax;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            rlo[threadIdx.x] = fmin(rlo[threadIdx.x], rlo[threadIdx.x + o]);
+            rhi[threadIdx.x] = fmax(rhi[threadIdx.x], rhi[threadIdx.x + o]);
+            rem[threadIdx.x] = fmax(rem[threadIdx.x], rem[threadIdx.x + o]);
         }
-        double tn = fmax(fabs(lo), fabs(hi));
-        pivmin = 2.2250738585072014e-308 * fmax(1.0, emax);
-        glo = lo - 2.0 * DEPS * tn * n - pivmin;
-        ghi = hi + 2.0 * DEPS * tn * n + pivmin;
-        kk = (n > 0) ? sturm_count(d, e, n, sigma, pivmin) : 0;
-        kout[b] = kk;
-        lam_lo = -1.0;
-        lam_hi = -1.0;
+        __syncthreads();
     }
-    __syncthreads();
-    int k = kk;
-    // eigenvalues 0..k-1 (kept) and k (first discarded) for the gap
-    for (int j = threadIdx.x; j <= k && j < n; j += blockDim.x) {
-        // shifts to 1e-12 ||T||: the retained vectors are orthonormalised together afterwards, so
-        // eigenvalues closer than that only need to land in their cluster's subspace
-        double lam = bisect_index(d, e, n, j, glo, ghi, pivmin, 1e-12 * fmax(fabs(glo), fabs(ghi)));
-        if (j < k) w[toff[b] + j] = lam;
-        if (j == k - 1) lam_lo = lam;
-        if (j == k) lam_hi = lam;
-    }
-    __syncthreads();
     if (threadIdx.x == 0) {
-        double g = 1e300;
-        if (k > 0) g = fmin(g, fabs(lam_lo / sigma - 1.0));
-        if (k < n) g = fmin(g, fabs(lam_hi / sigma - 1.0));
-        gap[b] = g;
+        const double l = rlo[0], h = rhi[0];
+        const double tn = fmax(fabs(l), fabs(h));
+        const double pivmin = 2.2250738585072014e-308 * fmax(1.0, rem[0]);
+        bnd[3 * b + 0] = l - 2.0 * DEPS * tn * n - pivmin;
+        bnd[3 * b + 1] = h + 2.0 * DEPS * tn * n + pivmin;
+        bnd[3 * b + 2] = pivmin;
+        kout[b] = (n > 0) ? sturm_count(d, e, n, sigma, pivmin) : 0;
     }
+}
+
+// one thread per wanted eigenvalue: indices 0 .. k-1 (kept) and k (the first discarded, for the
+// gap) of every matrix, spread over the whole GPU
+__global__ void __launch_bounds__(128) k_stebz_bisect(const double *dd, const double *ee, const int64_t *toff,
+                                                      const int32_t *nn, int64_t count, const int32_t *kk,
+                                                      const double *bnd, const int64_t *pre, double *w,
+                                                      double *edge) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= pre[count]) return;
+    int64_t lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (pre[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    const int64_t b = lo;
+    const int j = (int)(t - pre[b]);
+    const int n = nn[b], k = kk[b];
+    const double glo = bnd[3 * b], ghi = bnd[3 * b + 1], pivmin = bnd[3 * b + 2];
+    // shifts to 1e-12 ||T||: the retained vectors are orthonormalised together afterwards, so
+    // eigenvalues closer than that only need to land in their cluster's subspace
+    const double lam = bisect_index(dd + toff[b], ee + toff[b], n, j, glo, ghi, pivmin,
+                                    1e-12 * fmax(fabs(glo), fabs(ghi)));
+    if (j < k) w[toff[b] + j] = lam;
+    if (j == k - 1) edge[2 * b] = lam;
+    if (j == k) edge[2 * b + 1] = lam;
+}
+
+// gap = min |lambda / sigma - 1| over the last kept and the first discarded eigenvalue
+__global__ void k_stebz_gap(const int32_t *nn, int64_t count, const int32_t *kk, const double *edge, double sigma,
+                            double *gap) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= count) return;
+    const int n = nn[b], k = kk[b];
+    double g = 1e300;
+    if (k > 0) g = fmin(g, fabs(edge[2 * b] / sigma - 1.0));
+    if (k < n) g = fmin(g, fabs(edge[2 * b + 1] / sigma - 1.0));
+    gap[b] = g;
 }
 
 // ------------------------------------------------------------------------- stein
@@ -962,42 +585,131 @@ __global__ void __launch_bounds__(256) k_stein(const double *dd, const double *e
     }
 }
 
-// ------------------------------------------------------------------------- ormtr
-__global__ void __launch_bounds__(256) k_ormtr(const double *baseA, const int64_t *aoff,
-                                               const int32_t *ald, const int32_t *nn,
-                                               const double *tt, const int64_t *toff,
-                                               double *baseV, const int64_t *voff,
-                                               const int32_t *vld, const int32_t *vcols,
-                                               int64_t count) {
-    int64_t b = blockIdx.y;
+// ------------------------------------------------------------------------- ormtr (blocked)
+constexpr int QB = 64;   // reflectors per block of the back-transformation
+
+// explicit Y of reflector block [j0, j0 + QB): column i = reflector j0 + i (unit at row j0+i+1,
+// A's entries below it, zeros above; a zero column past the last reflector), rows j0+1 .. n-1,
+// stored at Y[yoff + r + i n] with r the absolute row
+__global__ void __launch_bounds__(256) k_ormtr_y(const double *baseA, const int64_t *aoff, const int32_t *ald,
+                                                 const int32_t *nn, int64_t count, int j0, double *Y,
+                                                 const int64_t *yoff) {
+    const int64_t b = blockIdx.y;
     if (b >= count) return;
-    int n = nn[b], k = vcols[b];
-    const int lane = threadIdx.x & 31;
-    int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (c >= k) return;
+    const int n = nn[b];
+    if (j0 > n - 2) return;
     const double *A = baseA + aoff[b];
-    int LA = ald[b];
-    const double *tau = tt + toff[b];
-    double *v = baseV + voff[b] + (int64_t)c * vld[b];
-    for (int j = n - 2; j >= 0; j--) {
-        double t = tau[j];
-        if (t == 0.0) continue;
-        int m = n - j - 1;
-        const double *h = A + (j + 1) + (int64_t)j * LA;  // h[0] implicit 1
-        double s = 0.0;
-        for (int r = lane; r < m; r += 32) s += (r == 0 ? 1.0 : h[r]) * v[j + 1 + r];
-        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        s *= t;
-        for (int r = lane; r < m; r += 32) v[j + 1 + r] -= s * (r == 0 ? 1.0 : h[r]);
-        __syncwarp();
+    const int LA = ald[b];
+    double *Yb = Y + yoff[b];
+    const int R = n - j0 - 1;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)R * QB;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(t / R), r = j0 + 1 + (int)(t % R);
+        const int j = j0 + i;
+        double y = 0.0;
+        if (j <= n - 2) {
+            if (r == j + 1) y = 1.0;
+            else if (r > j + 1) y = A[r + (int64_t)j * LA];
+        }
+        Yb[r + (int64_t)i * n] = y;
+    }
+}
+
+// T of the block (forward, columnwise): T(i,i) = tau_i, T(0:i, i) = -tau_i T(0:i, 0:i) G(0:i, i)
+// with G = Y^T Y; one CTA per matrix, T upper triangular at Tb[b QB^2] column-major
+__global__ void __launch_bounds__(64) k_ormtr_t(const int32_t *nn, int64_t count, int j0, const double *tt,
+                                                const int64_t *toff, const double *G, double *Tb) {
+    __shared__ double T[QB][QB + 1];
+    __shared__ double g[QB];
+    const int64_t b = blockIdx.x;
+    if (b >= count) return;
+    const int n = nn[b];
+    if (j0 > n - 2) return;
+    const double *Gb = G + b * QB * QB;
+    const int c = threadIdx.x;
+    for (int i = 0; i < QB; i++) {
+        const int j = j0 + i;
+        const double ti = (j <= n - 2) ? tt[toff[b] + j] : 0.0;
+        if (c < i) g[c] = Gb[c + i * QB];
+        __syncthreads();
+        // row c of column i: -tau_i sum_{p=c..i-1} T(c, p) g(p)
+        if (c < i) {
+            double acc = 0.0;
+            for (int p2 = c; p2 < i; p2++) acc += T[c][p2] * g[p2];
+            T[c][i] = -ti * acc;
+        }
+        if (c == i) T[i][i] = ti;
+        if (c > i) T[c][i] = 0.0;
+        __syncthreads();
+    }
+    double *out = Tb + b * QB * QB;
+    for (int i = 0; i < QB; i++) out[c + i * QB] = T[c][i];
+}
+
+// Z = T Z for the block (Z: QB x k column-major at Z[zoff])
+__global__ void __launch_bounds__(256) k_ormtr_tz(const int32_t *nn, const int32_t *kk, int64_t count, int j0,
+                                                  const double *Tb, double *Z, const int64_t *zoff) {
+    __shared__ double T[QB][QB + 1];
+    __shared__ double zc[4][QB];
+    const int64_t b = blockIdx.y;
+    if (b >= count) return;
+    const int n = nn[b], k = kk[b];
+    if (j0 > n - 2) return;
+    const double *Tm = Tb + b * QB * QB;
+    for (int t = threadIdx.x; t < QB * QB; t += blockDim.x) T[t % QB][t / QB] = Tm[t];
+    __syncthreads();
+    const int sub = threadIdx.x >> 6, r = threadIdx.x & 63;
+    for (int c0 = blockIdx.x * 4; c0 < k; c0 += gridDim.x * 4) {
+        const int c = c0 + sub;
+        double *z = Z + zoff[b] + (int64_t)c * QB;
+        if (c < k) zc[sub][r] = z[r];
+        __syncthreads();
+        if (c < k) {
+            double acc = 0.0;
+            for (int p2 = r; p2 < QB; p2++) acc += T[r][p2] * zc[sub][p2];
+            z[r] = acc;
+        }
+        __syncthreads();
     }
 }
 
 }  // namespace
 
 // ============================================================================= host wrappers
+namespace {
+// A22 -= L21 L21^T (lower triangle) after panel [j0, j0 + w) of every view: L21 = rows
+// [j0 + w, n_b) of those columns, all on the tensor cores.  g0[b] offsets the factored block
+// inside view b (pivoted Cholesky); skip[b] >= 0 skips a view (factorisation already stopped).
+void lower_update(double *base, const MatBatch &A, const std::vector<int32_t> &nb_of,
+                  const std::vector<int32_t> *g0, int j0, int w, oz::Workspace &ws, const int32_t *skip,
+                  int *err, cudaStream_t s) {
+    std::vector<oz::SplitJob> sj;
+    std::vector<oz::GemmJob> gj;
+    int64_t h = 0, e = 0;
+    for (int64_t b = 0; b < A.count; b++) {
+        const int n = nb_of[b];
+        const int r0 = j0 + w;
+        const int m = n - r0;
+        if (m <= 0 || j0 >= n) continue;
+        const int64_t L = A.h_ld[b], g = g0 ? (*g0)[b] : 0;
+        const int64_t base_off = A.h_off[b] + g + g * L;
+        oz::SplitJob J{base_off + r0 + (int64_t)j0 * L, 1, L, h, e, m, w};
+        sj.push_back(J);
+        oz::GemmJob G{h, h, e, e, base_off + r0 + (int64_t)r0 * L, 1, L, m, m, w, 1, (int32_t)b, 0};
+        gj.push_back(G);
+        h += oz::slice_halves(m, w);
+        e += oz::exp_ints(m);
+    }
+    if (gj.empty()) return;
+    ws.reserve(h, e, s);
+    oz::split(base, sj, ws.sl.p, ws.ex.p, s);
+    oz::gemm(ws.sl.p, ws.ex.p, base, gj, -1.0, 1.0, err, s, skip);
+}
+}  // namespace
+
 void potrf_batched(double *base, const MatBatch &A, PotrfMode mode, int *err, cudaStream_t s) {
     if (A.count == 0 || A.maxn == 0) return;
+    constexpr int PB = 64;
     double fl = 0.0;
     for (auto v : A.h_n) fl += (double)v * v * v / 3.0;
     KTime kt(KC_POTRF, s, fl);
@@ -1005,20 +717,16 @@ void potrf_batched(double *base, const MatBatch &A, PotrfMode mode, int *err, cu
     md.alloc(A.count, s);
     k_maxdiag<<<(unsigned)A.count, 256, 0, s>>>(base, A.off.p, A.ld.p, A.n.p, A.count, md.p);
     CK_LAUNCH();
-    for (int j0 = 0; j0 < A.maxn; j0 += NB) {
-        k_potf2<<<(unsigned)A.count, 256, 0, s>>>(base, A.off.p, A.ld.p, A.n.p, A.count, j0, mode,
-                                                 md.p, err);
+    oz::Workspace ws;
+    for (int j0 = 0; j0 < A.maxn; j0 += PB) {
+        k_potf2<PB><<<(unsigned)A.count, 256, 0, s>>>(base, A.off.p, A.ld.p, A.n.p, A.count, j0, mode, md.p, err);
         CK_LAUNCH();
-        int rem = A.maxn - j0 - NB;
+        int rem = A.maxn - j0 - PB;
         if (rem <= 0) break;
         dim3 gp((unsigned)cdiv(rem, 128), (unsigned)A.count);
-        k_potrf_panel<<<gp, 128, 0, s>>>(base, A.off.p, A.ld.p, A.n.p, A.count, j0);
+        k_potrf_panel<PB><<<gp, 128, 0, s>>>(base, A.off.p, A.ld.p, A.n.p, A.count, j0);
         CK_LAUNCH();
-        int64_t T = cdiv(rem, TT);
-        dim3 gu((unsigned)(T * (T + 1) / 2), (unsigned)A.count);
-        k_potrf_update<<<gu, 256, 0, s>>>(base, A.off.p, A.ld.p, A.n.p, A.count, j0, nullptr,
-                                          nullptr, 0);
-        CK_LAUNCH();
+        lower_update(base, A, A.h_n, nullptr, j0, PB, ws, nullptr, err, s);
     }
 }
 
@@ -1056,8 +764,9 @@ __global__ void k_rank_finish(int32_t *rank, const int32_t *bn, int64_t count) {
 }  // namespace
 
 void pstrf_batched(double *base, const MatBatch &A, const int32_t *b0, const int32_t *bn,
+                   const std::vector<int32_t> &h_b0, const std::vector<int32_t> &h_bn,
                    int32_t max_bn, int32_t *perm, const int64_t *permoff, int32_t *rank,
-                   cudaStream_t s) {
+                   int *err, cudaStream_t s) {
     if (A.count == 0 || max_bn == 0) return;
     KTime kt(KC_PSTRF, s);
     DBuf<double> md, work;
@@ -1069,45 +778,104 @@ void pstrf_batched(double *base, const MatBatch &A, const int32_t *b0, const int
     k_maxdiag_block<<<(unsigned)A.count, 256, 0, s>>>(base, A.off.p, A.ld.p, b0, bn, A.count, md.p,
                                                        perm, permoff, rank);
     CK_LAUNCH();
+    oz::Workspace ws;
     for (int j0 = 0; j0 < max_bn; j0 += NB) {
         k_pstf_panel<<<(unsigned)A.count, 256, 0, s>>>(base, A.off.p, A.ld.p, A.n.p, b0, bn,
                                                       A.count, j0, perm, permoff, rank, work.p,
                                                       permoff, md.p);
         CK_LAUNCH();
-        int rem = max_bn - j0 - NB;
-        if (rem <= 0) break;
-        int64_t T = cdiv(rem, TT);
-        dim3 gu((unsigned)(T * (T + 1) / 2), (unsigned)A.count);
-        k_potrf_update<<<gu, 256, 0, s>>>(base, A.off.p, A.ld.p, bn, A.count, j0, b0, rank, 0);
-        CK_LAUNCH();
+        if (max_bn - j0 - NB <= 0) break;
+        lower_update(base, A, h_bn, &h_b0, j0, NB, ws, rank, err, s);
     }
     k_rank_finish<<<(unsigned)cdiv(A.count, 256), 256, 0, s>>>(rank, bn, A.count);
     CK_LAUNCH();
 }
 
 void trsm_batched(const double *base_L, const MatBatch &Lb, double *base_B, const MatBatch &Bb,
-                  bool trans, cudaStream_t s) {
+                  bool trans, cudaStream_t s, int *err) {
     if (Bb.count == 0 || Bb.maxm == 0 || Lb.maxn == 0) return;
     double fl = 0.0;
     for (size_t i = 0; i < Bb.h_n.size(); i++) fl += (double)Bb.h_n[i] * Bb.h_n[i] * Bb.h_m[i];
     KTime kt(KC_TRSM, s, fl);
+    const int nblk = (int)cdiv(Bb.maxn, TB);
     dim3 g((unsigned)cdiv(Bb.maxm, SW), (unsigned)Bb.count);
-    k_trsm<<<g, 256, 0, s>>>(base_L, Lb.off.p, Lb.ld.p, Lb.n.p, base_B, Bb.off.p, Bb.ld.p, Bb.m.p,
-                             Bb.count, trans ? 1 : 0);
-    CK_LAUNCH();
+    oz::Workspace ws;
+    for (int step = 0; step < nblk; step++) {
+        const int kb = trans ? nblk - 1 - step : step;
+        const int r0 = kb * TB;
+        k_trsm_diag<<<g, 256, 0, s>>>(base_L, Lb.off.p, Lb.ld.p, Lb.n.p, base_B, Bb.off.p, Bb.ld.p, Bb.m.p,
+                                      Bb.count, r0, trans ? 1 : 0);
+        CK_LAUNCH();
+        // the rest of B: below the block (L21 X_r) or above it (L_r,0:r0^T X_r)
+        std::vector<oz::SplitJob> sj;
+        std::vector<oz::GemmJob> gj;
+        int64_t h = 0, e = 0;
+        for (int64_t b = 0; b < Bb.count; b++) {
+            const int n = Bb.h_n[b], m = Bb.h_m[b];
+            if (r0 >= n || m <= 0) continue;
+            const int bs = std::min(TB, n - r0);
+            const int M = trans ? r0 : n - r0 - bs;
+            if (M <= 0) continue;
+            const int64_t LL = Lb.h_ld[b], LB = Bb.h_ld[b];
+            oz::SplitJob JA = trans ? oz::SplitJob{Lb.h_off[b] + r0, LL, 1, h, e, M, bs}
+                                    : oz::SplitJob{Lb.h_off[b] + (r0 + bs) + (int64_t)r0 * LL, 1, LL, h, e, M, bs};
+            const int64_t ha = h, ea = e;
+            h += oz::slice_halves(M, bs);
+            e += oz::exp_ints(M);
+            oz::SplitJob JB{Bb.h_off[b] + r0, LB, 1, h, e, m, bs};
+            const int64_t hb = h, eb = e;
+            h += oz::slice_halves(m, bs);
+            e += oz::exp_ints(m);
+            sj.push_back(JA);
+            sj.push_back(JB);
+            const int64_t c_off = Bb.h_off[b] + (trans ? 0 : r0 + bs);
+            gj.push_back(oz::GemmJob{ha, hb, ea, eb, c_off, 1, LB, M, m, bs, 0, 0, 0});
+        }
+        if (gj.empty()) continue;
+        ws.reserve(h, e, s);
+        // A and B operands come from different arrays: split them in two calls
+        std::vector<oz::SplitJob> sa, sb;
+        for (size_t q = 0; q < sj.size(); q += 2) {
+            sa.push_back(sj[q]);
+            sb.push_back(sj[q + 1]);
+        }
+        oz::split(base_L, sa, ws.sl.p, ws.ex.p, s);
+        oz::split(base_B, sb, ws.sl.p, ws.ex.p, s);
+        oz::gemm(ws.sl.p, ws.ex.p, base_B, gj, -1.0, 1.0, err, s);
+    }
 }
 
 void syrk_tn_batched(double *base_C, const MatBatch &Cb, const double *base_W, const MatBatch &Wb,
-                     double alpha, bool w_rowmajor, cudaStream_t s) {
+                     double alpha, bool w_rowmajor, cudaStream_t s, int *err) {
     if (Cb.count == 0 || Cb.maxn == 0) return;
     double fl = 0.0;
     for (size_t i = 0; i < Cb.h_n.size(); i++) fl += 2.0 * Cb.h_n[i] * Cb.h_n[i] * Wb.h_n[i];
     KTime kt(KC_SYRK, s, fl);
-    int64_t T = cdiv(Cb.maxn, TT);
-    dim3 g((unsigned)(T * T), (unsigned)Cb.count);
-    k_syrk_tn<<<g, 256, 0, s>>>(base_C, Cb.off.p, Cb.ld.p, Cb.n.p, base_W, Wb.off.p, Wb.ld.p, Wb.n.p,
-                                Cb.count, alpha, w_rowmajor ? 1 : 0);
-    CK_LAUNCH();
+    // C (n x n, full) += alpha W^T W, W: K x n; the split operand is W^T (n rows of length K),
+    // in pieces of at most 16,352 along K
+    constexpr int KMAX = oz::MAX_CHUNKS * oz::TK;
+    int kmax = 0;
+    for (auto v : Wb.h_n) kmax = std::max(kmax, v);
+    oz::Workspace ws;
+    for (int k0 = 0; k0 < kmax; k0 += KMAX) {
+        std::vector<oz::SplitJob> sj;
+        std::vector<oz::GemmJob> gj;
+        int64_t h = 0, e = 0;
+        for (int64_t b = 0; b < Cb.count; b++) {
+            const int n = Cb.h_n[b], K = std::min(Wb.h_n[b] - k0, KMAX);
+            if (n <= 0 || K <= 0) continue;
+            const int64_t ld = Wb.h_ld[b];
+            const int64_t rs = w_rowmajor ? 1 : ld, ks = w_rowmajor ? ld : 1;   // W(k, i) at k*ks + i*rs
+            sj.push_back(oz::SplitJob{Wb.h_off[b] + (int64_t)k0 * ks, rs, ks, h, e, n, K});
+            gj.push_back(oz::GemmJob{h, h, e, e, Cb.h_off[b], 1, Cb.h_ld[b], n, n, K, 0, 0, 0});
+            h += oz::slice_halves(n, K);
+            e += oz::exp_ints(n);
+        }
+        if (gj.empty()) continue;
+        ws.reserve(h, e, s);
+        oz::split(base_W, sj, ws.sl.p, ws.ex.p, s);
+        oz::gemm(ws.sl.p, ws.ex.p, base_C, gj, alpha, 1.0, err, s);
+    }
 }
 
 void transpose_batched(const double *base_S, const MatBatch &Sb, double *base_D, const MatBatch &Db,
@@ -1120,64 +888,28 @@ void transpose_batched(const double *base_S, const MatBatch &Sb, double *base_D,
     CK_LAUNCH();
 }
 
-namespace {
-void sytd2_large(double *base, const MatBatch &Ab, double *d, double *e, double *tau,
-                 const int64_t *toff, cudaStream_t s) {
-    // v / p workspaces: reuse the toff layout (n entries per matrix)
-    int64_t tot = read1(toff + Ab.count, s);
-    DBuf<double> vb, pb;
-    vb.alloc(std::max<int64_t>(tot, 1), s);
-    pb.alloc(std::max<int64_t>(tot, 1), s);
-    for (int j = 0; j < Ab.maxn; j++) {
-        k_tr_house<<<(unsigned)Ab.count, 256, 0, s>>>(base, Ab.off.p, Ab.ld.p, Ab.n.p, Ab.count, j, d, e,
-                                                      tau, toff, vb.p, pb.p, toff);
-        CK_LAUNCH();
-        const int m = Ab.maxn - j - 1;
-        if (m <= 0) break;
-        const int64_t T = cdiv(m, TRT);
-        dim3 g((unsigned)(T * (T + 1) / 2), (unsigned)Ab.count);
-        k_tr_symv<<<g, 128, 0, s>>>(base, Ab.off.p, Ab.ld.p, Ab.n.p, Ab.count, j, vb.p, pb.p, toff, tau, toff);
-        CK_LAUNCH();
-        k_tr_w<<<(unsigned)Ab.count, 256, 0, s>>>(Ab.n.p, Ab.count, j, vb.p, pb.p, toff, tau, toff);
-        CK_LAUNCH();
-        k_tr_update<<<g, 256, 0, s>>>(base, Ab.off.p, Ab.ld.p, Ab.n.p, Ab.count, j, vb.p, pb.p, toff, tau, toff);
-        CK_LAUNCH();
-    }
-}
-}  // namespace
-
-void sytd2_batched(double *base, const MatBatch &Ab, double *d, double *e, double *tau,
-                   const int64_t *toff, cudaStream_t s) {
-    if (Ab.count == 0) return;
-    double fl = 0.0;
-    for (auto v : Ab.h_n) fl += 4.0 / 3.0 * v * v * v;
-    KTime kt(KC_SYTD2, s, fl);
-    if (Ab.maxn > g_large_dense) {
-        // large matrices get many CTAs per column; all matrices of this batch go this way
-        sytd2_large(base, Ab, d, e, tau, toff, s);
-        return;
-    }
-    const size_t tiles = (SYTD2_THREADS / 32) * 32 * 33 * sizeof(double);
-    const size_t need = tiles + 2 * (size_t)std::max(Ab.maxn, 1) * sizeof(double);
-    const bool smem = need <= 220 * 1024;
-    DBuf<double> pw;
-    if (!smem) {
-        int64_t tot = read1(toff + Ab.count, s);
-        pw.alloc(std::max<int64_t>(2 * tot, 1), s);
-    }
-    const size_t dyn = smem ? need : tiles;
-    CK(cudaFuncSetAttribute(k_sytd2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
-    k_sytd2<<<(unsigned)Ab.count, SYTD2_THREADS, dyn, s>>>(base, Ab.off.p, Ab.ld.p, Ab.n.p, Ab.count,
-                                                 d, e, tau, toff, pw.p, toff, smem ? 1 : 0);
-    CK_LAUNCH();
-}
-
 void stebz_batched(const double *d, const double *e, const int64_t *toff, const int32_t *n,
                    int64_t count, double sigma, int32_t *k, double *w, double *gap,
                    cudaStream_t s) {
     if (count == 0) return;
     KTime kt(KC_STEBZ, s);
-    k_stebz<<<(unsigned)count, 128, 0, s>>>(d, e, toff, n, count, sigma, k, w, gap);
+    DBuf<double> bnd, edge;
+    bnd.alloc(3 * count, s);
+    edge.alloc(2 * count, s);
+    k_stebz_count<<<(unsigned)count, 256, 0, s>>>(d, e, toff, n, count, sigma, k, bnd.p);
+    CK_LAUNCH();
+    auto hk = to_host(k, count, s);
+    auto hn = to_host(n, count, s);
+    std::vector<int64_t> pre(count + 1, 0);
+    for (int64_t b = 0; b < count; b++) pre[b + 1] = pre[b] + std::min(hk[b] + 1, hn[b]);
+    DBuf<int64_t> dpre;
+    upload(dpre, pre, s);
+    if (pre[count] > 0) {
+        k_stebz_bisect<<<(unsigned)cdiv(pre[count], 128), 128, 0, s>>>(d, e, toff, n, count, k, bnd.p, dpre.p, w,
+                                                                      edge.p);
+        CK_LAUNCH();
+    }
+    k_stebz_gap<<<(unsigned)cdiv(count, 256), 256, 0, s>>>(n, count, k, edge.p, sigma, gap);
     CK_LAUNCH();
 }
 
@@ -1292,16 +1024,89 @@ void stein_batched(const double *d, const double *e, const int64_t *toff, const 
 }
 
 void ormtr_batched(const double *base_A, const MatBatch &Ab, const double *tau, const int64_t *toff,
-                   double *base_V, const MatBatch &Vb, cudaStream_t s) {
+                   double *base_V, const MatBatch &Vb, cudaStream_t s, int *err) {
     if (Vb.count == 0 || Vb.maxm == 0) return;
     double fl = 0.0;
-    // n - 1 reflectors of lengths n-1 ... 1, each applied to m vectors at 4 flops per entry
     for (size_t i = 0; i < Vb.h_n.size(); i++) fl += 2.0 * Vb.h_n[i] * Vb.h_n[i] * Vb.h_m[i];
     KTime kt(KC_ORMTR, s, fl);
-    dim3 g((unsigned)cdiv(Vb.maxm, 8), (unsigned)Vb.count);
-    k_ormtr<<<g, 256, 0, s>>>(base_A, Ab.off.p, Ab.ld.p, Ab.n.p, tau, toff, base_V, Vb.off.p,
-                              Vb.ld.p, Vb.m.p, Vb.count);
-    CK_LAUNCH();
+    // V = Q V, Q = H_0 ... H_{n-2} in blocks of QB reflectors, last block first; each block is
+    // I - Y T Y^T (compact WY), applied as V -= Y (T (Y^T V)) with the two large products on the
+    // tensor cores
+    const int64_t cnt = Vb.count;
+    std::vector<int64_t> yoff(cnt + 1, 0), zoff(cnt + 1, 0);
+    for (int64_t b = 0; b < cnt; b++) {
+        yoff[b + 1] = yoff[b] + (int64_t)Vb.h_n[b] * QB;
+        zoff[b + 1] = zoff[b] + (int64_t)QB * std::max(Vb.h_m[b], 1);
+    }
+    DBuf<double> Y, Z, G, T;
+    DBuf<int64_t> dyo, dzo;
+    Y.alloc(std::max<int64_t>(yoff[cnt], 1), s);
+    Z.alloc(std::max<int64_t>(zoff[cnt], 1), s);
+    G.alloc(cnt * QB * QB, s);
+    T.alloc(cnt * QB * QB, s);
+    upload(dyo, std::vector<int64_t>(yoff.begin(), yoff.end() - 1), s);
+    upload(dzo, std::vector<int64_t>(zoff.begin(), zoff.end() - 1), s);
+    oz::Workspace ws;
+    const int nblk = (int)cdiv(std::max(Vb.maxn - 1, 1), QB);
+    for (int p = nblk - 1; p >= 0; p--) {
+        const int j0 = p * QB;
+        dim3 gy((unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv((int64_t)Vb.maxn * QB, 256), 64)),
+                (unsigned)cnt);
+        k_ormtr_y<<<gy, 256, 0, s>>>(base_A, Ab.off.p, Ab.ld.p, Ab.n.p, cnt, j0, Y.p, dyo.p);
+        CK_LAUNCH();
+        // operands: Y^T (QB rows of length R), V^T (k rows of length R), Y (R rows of length QB)
+        std::vector<oz::SplitJob> sy, sv;
+        std::vector<oz::GemmJob> gg, gz, gv;
+        int64_t h = 0, e = 0;
+        for (int64_t b = 0; b < cnt; b++) {
+            const int n = Vb.h_n[b], k = Vb.h_m[b];
+            if (j0 > n - 2 || k <= 0) continue;
+            const int R = n - j0 - 1;
+            sy.push_back(oz::SplitJob{yoff[b] + j0 + 1, n, 1, h, e, QB, R});
+            const int64_t hy = h, ey = e;
+            h += oz::slice_halves(QB, R);
+            e += oz::exp_ints(QB);
+            sv.push_back(oz::SplitJob{Vb.h_off[b] + j0 + 1, Vb.h_ld[b], 1, h, e, k, R});
+            const int64_t hv = h, ev = e;
+            h += oz::slice_halves(k, R);
+            e += oz::exp_ints(k);
+            gg.push_back(oz::GemmJob{hy, hy, ey, ey, b * QB * QB, 1, QB, QB, QB, R, 0, 0, 0});
+            gz.push_back(oz::GemmJob{hy, hv, ey, ev, zoff[b], 1, QB, QB, k, R, 0, 0, 0});
+        }
+        if (gg.empty()) continue;
+        ws.reserve(h, e, s);
+        oz::split(Y.p, sy, ws.sl.p, ws.ex.p, s);
+        oz::split(base_V, sv, ws.sl.p, ws.ex.p, s);
+        oz::gemm(ws.sl.p, ws.ex.p, G.p, gg, 1.0, 0.0, err, s);
+        oz::gemm(ws.sl.p, ws.ex.p, Z.p, gz, 1.0, 0.0, err, s);
+        k_ormtr_t<<<(unsigned)cnt, QB, 0, s>>>(Vb.n.p, cnt, j0, tau, toff, G.p, T.p);
+        CK_LAUNCH();
+        dim3 gt((unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv(Vb.maxm, 4), 32)), (unsigned)cnt);
+        k_ormtr_tz<<<gt, 256, 0, s>>>(Vb.n.p, Vb.m.p, cnt, j0, T.p, Z.p, dzo.p);
+        CK_LAUNCH();
+        // V(j0+1:, :) -= Y Z
+        std::vector<oz::SplitJob> s1, s2;
+        h = 0;
+        e = 0;
+        for (int64_t b = 0; b < cnt; b++) {
+            const int n = Vb.h_n[b], k = Vb.h_m[b];
+            if (j0 > n - 2 || k <= 0) continue;
+            const int R = n - j0 - 1;
+            s1.push_back(oz::SplitJob{yoff[b] + j0 + 1, 1, n, h, e, R, QB});
+            const int64_t ha = h, ea = e;
+            h += oz::slice_halves(R, QB);
+            e += oz::exp_ints(R);
+            s2.push_back(oz::SplitJob{zoff[b], QB, 1, h, e, k, QB});
+            const int64_t hb = h, eb = e;
+            h += oz::slice_halves(k, QB);
+            e += oz::exp_ints(k);
+            gv.push_back(oz::GemmJob{ha, hb, ea, eb, Vb.h_off[b] + j0 + 1, 1, Vb.h_ld[b], R, k, QB, 0, 0, 0});
+        }
+        ws.reserve(h, e, s);
+        oz::split(Y.p, s1, ws.sl.p, ws.ex.p, s);
+        oz::split(Z.p, s2, ws.sl.p, ws.ex.p, s);
+        oz::gemm(ws.sl.p, ws.ex.p, base_V, gv, -1.0, 1.0, err, s);
+    }
 }
 
 }  // namespace lsamg

@@ -13,7 +13,9 @@ struct MatBatch {
     DBuf<int32_t> m;    // extra dimension (columns of a right-hand side, K of an update)
     int64_t count = 0;
     int32_t maxn = 0, maxm = 0;
-    std::vector<int32_t> h_n, h_m;  // host copies of the sizes (FLOP accounting)
+    std::vector<int32_t> h_n, h_m;  // host copies of the sizes (FLOP accounting, product jobs)
+    std::vector<int64_t> h_off;     // host copies of the offsets and leading dimensions
+    std::vector<int32_t> h_ld;
     void set(const std::vector<int64_t> &o, const std::vector<int32_t> &l,
              const std::vector<int32_t> &nn, const std::vector<int32_t> &mm, cudaStream_t s) {
         count = (int64_t)o.size();
@@ -24,6 +26,8 @@ struct MatBatch {
         upload(m, m2, s);
         h_n = nn;
         h_m = m2;
+        h_off = o;
+        h_ld = l;
         maxn = 0;
         maxm = 0;
         for (auto v : nn) maxn = std::max(maxn, v);
@@ -47,20 +51,21 @@ void potrf_batched(double *base, const MatBatch &A, PotrfMode mode, int *err, cu
 // blocks are permuted consistently.  perm receives the pivot order (block-local), rank the
 // numerical rank.
 void pstrf_batched(double *base, const MatBatch &A, const int32_t *b0, const int32_t *bn,
+                   const std::vector<int32_t> &h_b0, const std::vector<int32_t> &h_bn,
                    int32_t max_bn, int32_t *perm, const int64_t *permoff, int32_t *rank,
-                   cudaStream_t s);
+                   int *err, cudaStream_t s);
 
 // X = L^{-1} B (trans = false) or X = L^{-T} B (trans = true), in place on B.
 // L views in Lb (n = order), B views in Bb (n = rows = order, m = columns).
 // Zero diagonal entries of L (PSD mode) give zero solution rows.
 void trsm_batched(const double *base_L, const MatBatch &Lb, double *base_B, const MatBatch &Bb,
-                  bool trans, cudaStream_t s);
+                  bool trans, cudaStream_t s, int *err = nullptr);
 
 // C += alpha W^T W over the full square C (n x n, column-major, ld); W views (n = K rows,
 // m = columns = C order).  W(k, i) is base_W[off + k + i*ld] (column-major) or, with
 // w_rowmajor, base_W[off + k*ld + i].
 void syrk_tn_batched(double *base_C, const MatBatch &Cb, const double *base_W, const MatBatch &Wb,
-                     double alpha, bool w_rowmajor, cudaStream_t s);
+                     double alpha, bool w_rowmajor, cudaStream_t s, int *err = nullptr);
 
 // dst = src^T for square views (src n x n -> dst n x n).
 void transpose_batched(const double *base_S, const MatBatch &Sb, double *base_D, const MatBatch &Db,
@@ -95,6 +100,6 @@ void cholqr2_batched(double *base_V, const MatBatch &Vb, int *err, cudaStream_t 
 
 // V = Q V with Q the product of the sytd2 reflectors stored in A.
 void ormtr_batched(const double *base_A, const MatBatch &Ab, const double *tau, const int64_t *toff,
-                   double *base_V, const MatBatch &Vb, cudaStream_t s);
+                   double *base_V, const MatBatch &Vb, cudaStream_t s, int *err = nullptr);
 
 }  // namespace lsamg

@@ -1,0 +1,395 @@
+// FP64 products on FP16 tensor cores by exact splitting (see ozaki.cuh for the scheme).
+#include <cstring>
+
+#include "ozaki.cuh"
+
+namespace lsamg {
+namespace oz {
+namespace {
+
+constexpr int NST = 3;                         // staging ring depth
+constexpr int STAGE_BYTES = 2 * NS * BLK * 2;  // A and B slices of one K chunk
+constexpr int GEMM_SMEM = NST * STAGE_BYTES + 64;
+
+__device__ __forceinline__ int dcdiv(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+__device__ __forceinline__ int swz(int r, int k) {  // halves offset inside a 64 x 32 block
+    return r * TK + ((((k >> 3) ^ (r >> 1)) & 3) << 3) + (k & 7);
+}
+
+// job index of CTA `blk` from an exclusive prefix of per-job CTA counts
+__device__ __forceinline__ int find_job(const int64_t *pre, int njobs, int64_t blk) {
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pre[mid] <= blk) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ------------------------------------------------------------------------------- split
+__global__ void __launch_bounds__(256) k_split(const double *src, const SplitJob *jobs, const int64_t *pre,
+                                               int njobs, __half *dst, int32_t *exps) {
+    __shared__ double rmax[TM][5];
+    __shared__ int rexp[TM];
+    const int j = find_job(pre, njobs, blockIdx.x);
+    const SplitJob J = jobs[j];
+    const int t = (int)(blockIdx.x - pre[j]);
+    const int tiles = dcdiv(J.rows, TM), nch = dcdiv(max(J.K, 1), TK);
+    const int i0 = t * TM;
+    const bool kfast = (J.ks == 1);
+    const double *S = src + J.src_off;
+    // row maxima over the whole K
+    {
+        double m = 0.0;
+        int r, g, gs;
+        if (kfast) { r = threadIdx.x >> 2; g = threadIdx.x & 3; gs = 4; }   // 4 threads per row
+        else       { r = threadIdx.x & 63; g = threadIdx.x >> 6; gs = 4; }
+        const int i = i0 + r;
+        if (i < J.rows)
+            for (int k = g; k < J.K; k += gs) m = fmax(m, fabs(S[(int64_t)i * J.rs + (int64_t)k * J.ks]));
+        rmax[r][g] = m;
+        __syncthreads();
+        if (threadIdx.x < TM) {
+            const double v = fmax(fmax(rmax[threadIdx.x][0], rmax[threadIdx.x][1]),
+                                  fmax(rmax[threadIdx.x][2], rmax[threadIdx.x][3]));
+            int e = 0;
+            if (v > 0.0) frexp(v, &e);     // v < 2^e
+            rexp[threadIdx.x] = e;
+            exps[J.exp_off + i0 + threadIdx.x] = e;
+        }
+        __syncthreads();
+    }
+    for (int c = 0; c < nch; c++) {
+        for (int idx = threadIdx.x; idx < BLK; idx += blockDim.x) {
+            int r, kk;
+            if (kfast) { r = idx >> 5; kk = idx & 31; } else { r = idx & 63; kk = idx >> 6; }
+            const int i = i0 + r, k = c * TK + kk;
+            double v = 0.0;
+            if (i < J.rows && k < J.K) v = S[(int64_t)i * J.rs + (int64_t)k * J.ks];
+            double x = ldexp(v, 7 - rexp[r]);            // |x| < 128
+            const int o = swz(r, kk);
+            __half *d = dst + J.dst_off + ((int64_t)t * nch + c) * BLK + o;
+            const int64_t pstride = (int64_t)tiles * nch * BLK;
+#pragma unroll
+            for (int p = 0; p < NS; p++) {
+                const double a = rint(x);                // |a| <= 128, exact in FP16
+                d[p * pstride] = __double2half(a);
+                x = (x - a) * 256.0;                     // exact
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------- gemm
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// wait for phase `parity` of `bar`, giving up after `ns` nanoseconds
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint64_t ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = gtimer();
+    while (!mbar_try_wait(bar, parity))
+        if (gtimer() - t0 > ns) return false;
+    return true;
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], uint32_t addr) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr));
+}
+__device__ __forceinline__ void mma16816(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ void tri_index(int64_t t, int &ti, int &tj) {
+    int i = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while ((int64_t)(i + 1) * (i + 2) / 2 <= t) i++;
+    while ((int64_t)i * (i + 1) / 2 > t) i--;
+    ti = i;
+    tj = (int)(t - (int64_t)i * (i + 1) / 2);
+}
+
+// v 2^e rounded to nearest (ties to even), negated if neg: integer instructions only while the
+// result is a normal FP64 number (the FP64 pipe of this GPU is 1/64 of its FP32 rate)
+__device__ __forceinline__ double i128_to_double(__int128 v, int e, bool neg) {
+    if (v == 0) return 0.0;
+    if (v < 0) { v = -v; neg = !neg; }
+    const unsigned __int128 m = (unsigned __int128)v;
+    const uint64_t h = (uint64_t)(m >> 64), l = (uint64_t)m;
+    int p = h ? 127 - __clzll((long long)h) : 63 - __clzll((long long)l);   // top bit
+    uint64_t mant;
+    if (p <= 52) {
+        mant = l << (52 - p);
+    } else {
+        const int sh = p - 52;
+        const unsigned __int128 qq = m >> sh;
+        const unsigned __int128 rem = m - (qq << sh);
+        const unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
+        mant = (uint64_t)qq;
+        if (rem > half || (rem == half && (mant & 1ull))) {
+            mant++;
+            if (mant == (1ull << 53)) { mant >>= 1; p++; }
+        }
+    }
+    const int E = p + e;
+    if (E > 1023 || E < -1022) {
+        const double r = ldexp((double)mant, p - 52 + e);
+        return neg ? -r : r;
+    }
+    const uint64_t bits = ((uint64_t)(E + 1023) << 52) | (mant & ((1ull << 52) - 1)) | (neg ? (1ull << 63) : 0ull);
+    return __longlong_as_double((long long)bits);
+}
+
+__global__ void __launch_bounds__(256, 1) k_gemm(const __half *sl, const int32_t *ex, double *C,
+                                                 const GemmJob *jobs, const int64_t *pre, int njobs, double alpha,
+                                                 double beta, int *err, const int32_t *skip) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + NST * STAGE_BYTES);
+    __shared__ int s_bad;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int j = find_job(pre, njobs, blockIdx.x);
+    const GemmJob J = jobs[j];
+    if (skip && skip[J.skip_idx] >= 0) return;
+    const int64_t local = blockIdx.x - pre[j];
+    const int tilesM = dcdiv(J.M, TM), tilesN = dcdiv(J.N, TM);
+    int tm, tn;
+    if (J.lower) tri_index(local, tm, tn);
+    else { tm = (int)(local / tilesN); tn = (int)(local % tilesN); }
+    const int nch = dcdiv(max(J.K, 1), TK);
+    const __half *gA = sl + J.a_off + (int64_t)tm * nch * BLK;
+    const __half *gB = sl + J.b_off + (int64_t)tn * nch * BLK;
+    const int64_t pA = (int64_t)tilesM * nch * BLK, pB = (int64_t)tilesN * nch * BLK;
+    if (tid == 0) {
+        for (int st = 0; st < NST; st++) mbar_init(&full[st], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_bad = 0;
+    }
+    __syncthreads();
+    auto issue = [&](int c) {
+        const int st = c % NST;
+        unsigned char *sb = smem + st * STAGE_BYTES;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(&full[st], STAGE_BYTES);
+        for (int p = 0; p < NS; p++) {
+            bulk_g2s(sb + p * BLK * 2, gA + p * pA + (int64_t)c * BLK, BLK * 2, &full[st]);
+            bulk_g2s(sb + (NS + p) * BLK * 2, gB + p * pB + (int64_t)c * BLK, BLK * 2, &full[st]);
+        }
+    };
+    if (tid == 0)
+        for (int c = 0; c < NST && c < nch; c++) issue(c);
+
+    const int wm = warp >> 2, wn = warp & 3;     // warp tile: rows wm*32.., cols wn*16..
+    // exact int32 sums for the diagonals 2 .. NI + 1; the lowest-weight diagonal (2^-48 of the
+    // leading one) goes to an FP32 sum, whose rounding stays below 2^-70 of the leading unit
+    constexpr int NI = ND - 2;
+    int32_t iacc[NI][2][2][4];
+    float tail[2][2][4];
+#pragma unroll
+    for (int a = 0; a < 2; a++)
+#pragma unroll
+        for (int b = 0; b < 2; b++)
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                tail[a][b][q] = 0.f;
+#pragma unroll
+                for (int d = 0; d < NI; d++) iacc[d][a][b][q] = 0;
+            }
+    // ldmatrix row / 16-byte chunk of this lane: A tiles (16 rows x 16 k), B pair of n8 tiles
+    const int arow = lane & 15, akc = lane >> 4;
+    const int brow = ((lane >> 4) << 3) + (lane & 7), bkc = (lane >> 3) & 1;
+
+    for (int c = 0; c < nch; c++) {
+        const int st = c % NST;
+        const uint32_t parity = (uint32_t)((c / NST) & 1);
+        if (tid == 0 && !mbar_wait_bounded(&full[st], parity, 2000000000ull)) s_bad = 1;
+        __syncthreads();
+        if (s_bad) {
+            if (tid == 0) {
+                flag_error(err, LSAMG_DEVICE_TIMEOUT, (int)blockIdx.x);
+                // let the copies already in flight land before the CTA's shared memory is released
+                for (int c2 = c; c2 < nch && c2 < c + NST; c2++)
+                    mbar_wait_bounded(&full[c2 % NST], (uint32_t)((c2 / NST) & 1), 1000000000ull);
+            }
+            return;
+        }
+        mbar_wait_bounded(&full[st], parity, 1000000000ull);   // completed: returns at once
+        const uint32_t sA = smem_u32(smem + st * STAGE_BYTES);
+        const uint32_t sB = sA + NS * BLK * 2;
+#pragma unroll
+        for (int d = 2; d <= ND; d++) {
+            float acc[2][2][4];
+#pragma unroll
+            for (int a = 0; a < 2; a++)
+#pragma unroll
+                for (int b = 0; b < 2; b++)
+#pragma unroll
+                    for (int q = 0; q < 4; q++) acc[a][b][q] = 0.f;
+            const int p0 = d - NS > 1 ? d - NS : 1, p1 = d - 1 < NS ? d - 1 : NS;
+#pragma unroll 1
+            for (int p = p0; p <= p1; p++) {
+                const int q = d - p;
+#pragma unroll
+                for (int ks = 0; ks < 2; ks++) {
+                    uint32_t af[2][4], bf[4];
+#pragma unroll
+                    for (int mt = 0; mt < 2; mt++) {
+                        const int r = wm * 32 + mt * 16 + arow, kc = ks * 2 + akc;
+                        ldsm_x4(af[mt], sA + (p - 1) * BLK * 2 + r * 64 + ((((kc ^ (r >> 1)) & 3)) << 4));
+                    }
+                    {
+                        const int r = wn * 16 + brow, kc = ks * 2 + bkc;
+                        ldsm_x4(bf, sB + (q - 1) * BLK * 2 + r * 64 + ((((kc ^ (r >> 1)) & 3)) << 4));
+                    }
+#pragma unroll
+                    for (int mt = 0; mt < 2; mt++)
+#pragma unroll
+                        for (int nt = 0; nt < 2; nt++) mma16816(acc[mt][nt], af[mt], bf[2 * nt], bf[2 * nt + 1]);
+                }
+            }
+            // exact FP32 -> int32 (the sums are integers below 2^22 in magnitude), or the tail
+#pragma unroll
+            for (int a = 0; a < 2; a++)
+#pragma unroll
+                for (int b = 0; b < 2; b++)
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        if (d - 2 < NI)
+                            iacc[d - 2][a][b][q] += __float_as_int(acc[a][b][q] + 12582912.0f) - 0x4B400000;
+                        else
+                            tail[a][b][q] += acc[a][b][q];
+                    }
+        }
+        __syncthreads();   // every warp is done with this stage
+        if (tid == 0 && c + NST < nch) issue(c + NST);
+    }
+    // epilogue: C = beta C + alpha 2^(ea + eb - 14) sum_d 2^-8(d-2) S_d, the sum formed exactly as
+    // a 128-bit integer in units of 2^-48 (FP64 instructions are scarce: one add per output)
+    const int g = lane >> 2, tg = lane & 3;
+    int ash = 0;
+    bool aneg = alpha < 0.0, apow2 = false;
+    {
+        int e2;
+        const double fr = frexp(fabs(alpha), &e2);
+        if (fr == 0.5) { apow2 = true; ash = e2 - 1; }
+    }
+#pragma unroll
+    for (int mt = 0; mt < 2; mt++)
+#pragma unroll
+        for (int nt = 0; nt < 2; nt++)
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int i = tm * TM + wm * 32 + mt * 16 + g + ((q >> 1) << 3);
+                const int jj = tn * TM + wn * 16 + nt * 8 + 2 * tg + (q & 1);
+                if (i >= J.M || jj >= J.N || (J.lower && i < jj)) continue;
+                const int64_t hi = ((int64_t)iacc[0][mt][nt][q] << 16) + ((int64_t)iacc[1][mt][nt][q] << 8) +
+                                   (int64_t)iacc[2][mt][nt][q];
+                const int64_t lo = ((int64_t)iacc[3][mt][nt][q] << 16) + ((int64_t)iacc[4][mt][nt][q] << 8) +
+                                   (int64_t)iacc[5][mt][nt][q];
+                const __int128 v = ((__int128)hi << 32) + ((__int128)lo << 8) + (__int128)__float2ll_rn(tail[mt][nt][q]);
+                const int e = ex[J.a_exp + i] + ex[J.b_exp + jj] - 62;
+                double val;
+                if (apow2) val = i128_to_double(v, e + ash, aneg);
+                else val = alpha * i128_to_double(v, e, false);
+                double *cp = C + J.c_off + (int64_t)i * J.crs + (int64_t)jj * J.ccs;
+                if (beta == 0.0) *cp = val;
+                else if (beta == 1.0) *cp = *cp + val;
+                else *cp = fma(beta, *cp, val);
+            }
+}
+
+// one device upload of a job array and the exclusive prefix of its CTA counts
+template <class Job>
+int64_t upload_jobs(const std::vector<Job> &jobs, const std::vector<int64_t> &cnt, DBuf<int64_t> &buf,
+                    const Job *&djobs, const int64_t *&dpre, cudaStream_t s) {
+    const size_t nj = jobs.size();
+    const size_t jw = (sizeof(Job) + 7) / 8;
+    std::vector<int64_t> h(nj * jw + nj + 1, 0);
+    std::memcpy(h.data(), jobs.data(), nj * sizeof(Job));
+    int64_t *pre = h.data() + nj * jw;
+    pre[0] = 0;
+    for (size_t i = 0; i < nj; i++) pre[i + 1] = pre[i] + cnt[i];
+    const int64_t total = pre[nj];
+    upload(buf, h, s);
+    djobs = reinterpret_cast<const Job *>(buf.p);
+    dpre = buf.p + nj * jw;
+    return total;
+}
+
+}  // namespace
+
+void split(const double *src, const std::vector<SplitJob> &jobs, __half *dst, int32_t *exps, cudaStream_t s) {
+    if (jobs.empty()) return;
+    static_assert(sizeof(SplitJob) % 8 == 0, "job layout");
+    std::vector<int64_t> cnt(jobs.size());
+    for (size_t i = 0; i < jobs.size(); i++) {
+        if (cdiv(std::max(jobs[i].K, 1), TK) > MAX_CHUNKS) fail(LSAMG_LIMIT, "tensor-core product longer than 16352");
+        cnt[i] = jobs[i].rows > 0 ? cdiv(jobs[i].rows, TM) : 0;
+    }
+    DBuf<int64_t> buf;
+    const SplitJob *dj = nullptr;
+    const int64_t *dp = nullptr;
+    const int64_t total = upload_jobs(jobs, cnt, buf, dj, dp, s);
+    if (total == 0) return;
+    if (total > 0x7fffffff) fail(LSAMG_LIMIT, "split grid too large");
+    k_split<<<(unsigned)total, 256, 0, s>>>(src, dj, dp, (int)jobs.size(), dst, exps);
+    CK_LAUNCH();
+}
+
+void gemm(const __half *slices, const int32_t *exps, double *C, const std::vector<GemmJob> &jobs, double alpha,
+          double beta, int *err, cudaStream_t s, const int32_t *skip) {
+    if (jobs.empty()) return;
+    static_assert(sizeof(GemmJob) % 8 == 0, "job layout");
+    std::vector<int64_t> cnt(jobs.size());
+    for (size_t i = 0; i < jobs.size(); i++) {
+        const GemmJob &J = jobs[i];
+        if (J.M <= 0 || J.N <= 0) { cnt[i] = 0; continue; }
+        if (cdiv(std::max(J.K, 1), TK) > MAX_CHUNKS) fail(LSAMG_LIMIT, "tensor-core product longer than 16352");
+        const int64_t tm = cdiv(J.M, TM), tn = cdiv(J.N, TM);
+        if (J.lower && tm != tn) fail(LSAMG_INVALID_ARG, "lower-triangular product of a non-square block");
+        cnt[i] = J.lower ? tm * (tm + 1) / 2 : tm * tn;
+    }
+    DBuf<int64_t> buf;
+    const GemmJob *dj = nullptr;
+    const int64_t *dp = nullptr;
+    const int64_t total = upload_jobs(jobs, cnt, buf, dj, dp, s);
+    if (total == 0) return;
+    if (total > 0x7fffffff) fail(LSAMG_LIMIT, "product grid too large");
+    CK(cudaFuncSetAttribute(k_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM));
+    k_gemm<<<(unsigned)total, 256, GEMM_SMEM, s>>>(slices, exps, C, dj, dp, (int)jobs.size(), alpha, beta, err,
+                                                   skip);
+    CK_LAUNCH();
+}
+
+}  // namespace oz
+}  // namespace lsamg

@@ -122,8 +122,27 @@ __global__ void k_elem_factor(const double *AT, const int64_t *aoff, const int32
     }
 }
 
-// CTAs per aggregate for the dense assemblies: one while the batch fills the GPU, more (each
-// taking an interleaved slice of the elements, with atomic adds) when it has few aggregates
+// Warp 0 lists, in ascending order, the element columns c < n with keep(c) into own[]; returns
+// the count through *cnt (visible after the caller's __syncthreads).
+template <class F>
+__device__ __forceinline__ void warp_compact(int n, int32_t *own, int *cnt, F keep) {
+    if (threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
+    int q = 0;
+    for (int c0 = 0; c0 < n; c0 += 32) {
+        const int c = c0 + lane;
+        const bool k = c < n && keep(c);
+        const unsigned m = __ballot_sync(0xffffffffu, k);
+        if (k) own[q + __popc(m & ((1u << lane) - 1u))] = c;
+        q += __popc(m);
+    }
+    if (lane == 0) *cnt = q;
+}
+
+// CTAs per aggregate for the dense assemblies: one while the batch fills the GPU, more when it
+// has few aggregates.  Each CTA of an aggregate owns the destination columns c with
+// c % slices == slice, so every entry is summed by one CTA, in element order: the assembled
+// blocks are the same bits on every run.
 static int assembly_slices(int64_t na) {
     const int64_t want = (148 * 4 + na - 1) / std::max<int64_t>(na, 1);
     return (int)std::max<int64_t>(1, std::min<int64_t>(want, 16));
@@ -131,14 +150,16 @@ static int assembly_slices(int64_t na) {
 
 // ---------------------------------------------------------------- local problem assembly
 // At (omega-first, column-major |Omega| x |Omega|) += A_T / mult(T) and Aww += A_T on
-// omega x omega, over the elements touching omega_i (eqs. 2.6-2.9).
+// omega x omega, over the elements touching omega_i (eqs. 2.6-2.9).  A_T is symmetric, so
+// entry (r, c) of the element is read as A_T[c][r] (consecutive threads, consecutive r).
 __global__ void k_assemble_gep(const int32_t *alist, int64_t na, const int64_t *aeptr, const int32_t *aeidx,
                                const int64_t *eptr, const int32_t *eidx, const double *AT,
                                const int64_t *aoff, const int32_t *mult, const int64_t *Optr,
                                const int32_t *Oidx, const int32_t *Olpos, const int64_t *wptr,
                                double *At, const int64_t *atoff, double *Aww,
                                const int64_t *awoff, int es) {
-    extern __shared__ int32_t pos[];
+    extern __shared__ int32_t pos[];   // [maxE] positions, then [maxE] owned element columns
+    __shared__ int ncols;
     int64_t li = blockIdx.x;
     if (li >= na) return;
     int64_t a = alist[li];
@@ -148,54 +169,56 @@ __global__ void k_assemble_gep(const int32_t *alist, int64_t na, const int64_t *
     int nw = (int)(wptr[a + 1] - wptr[a]);
     double *T1 = At + atoff[li];
     double *T2 = Aww + awoff[li];
-    // es CTAs per aggregate take interleaved element slices (atomics when es > 1)
-    for (int64_t j = aeptr[a] + blockIdx.y; j < aeptr[a + 1]; j += es) {
+    const int slice = blockIdx.y;
+    for (int64_t j = aeptr[a]; j < aeptr[a + 1]; j++) {
         int32_t e = aeidx[j];
         int64_t b = eptr[e];
         int n = (int)(eptr[e + 1] - b);
+        int32_t *own = pos + n;
         for (int t = threadIdx.x; t < n; t += blockDim.x) pos[t] = lp[lbound(Om, nO, eidx[b + t])];
         __syncthreads();
+        warp_compact(n, own, &ncols, [&](int c) { return pos[c] % es == slice; });   // owned columns
+        __syncthreads();
         const double *Ae = AT + aoff[e];
-        double w = 1.0 / (double)mult[e];
-        for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
-            int r = t / n, c = t % n;
-            double v = Ae[t];
-            int pr = pos[r], pc = pos[c];
-            if (es > 1) {
-                atomicAdd(&T1[pr + (int64_t)pc * nO], w * v);
-                if (pr < nw && pc < nw) atomicAdd(&T2[pr + (int64_t)pc * nw], v);
-            } else {
-                T1[pr + (int64_t)pc * nO] += w * v;
-                if (pr < nw && pc < nw) T2[pr + (int64_t)pc * nw] += v;
-            }
+        const double w = 1.0 / (double)mult[e];
+        const int nc = ncols;
+        for (int t = threadIdx.x; t < nc * n; t += blockDim.x) {
+            const int c = own[t / n], r = t % n;
+            const double v = Ae[(int64_t)c * n + r];
+            const int pr = pos[r], pc = pos[c];
+            T1[pr + (int64_t)pc * nO] += w * v;
+            if (pr < nw && pc < nw) T2[pr + (int64_t)pc * nw] += v;
         }
         __syncthreads();
     }
 }
 
-// A_Omega (sorted-Omega order, column-major) += A_T over the elements meeting Omega_i
+// A_Omega (sorted-Omega order, column-major) += A_T over the elements meeting Omega_i; the CTAs
+// of a subdomain own interleaved destination columns (deterministic, no atomics)
 __global__ void k_assemble_smoother(int64_t a0, int64_t na, const int64_t *oeptr,
                                     const int32_t *oeidx, const int64_t *eptr, const double *AT,
                                     const int64_t *aoff, const int64_t *locoff, const int32_t *loc,
                                     const int64_t *Optr, double *AO, const int64_t *ooff, int es) {
+    extern __shared__ int32_t own[];
+    __shared__ int ncols;
     int64_t li = blockIdx.x;
     if (li >= na) return;
     int64_t a = a0 + li;
     int64_t nO = Optr[a + 1] - Optr[a];
     double *M = AO + ooff[li];
-    // es CTAs per subdomain take interleaved element slices (atomics when es > 1)
-    for (int64_t j = oeptr[a] + blockIdx.y; j < oeptr[a + 1]; j += es) {
+    const int slice = blockIdx.y;
+    for (int64_t j = oeptr[a]; j < oeptr[a + 1]; j++) {
         int32_t e = oeidx[j];
         int n = (int)(eptr[e + 1] - eptr[e]);
         const int32_t *p = loc + locoff[j];
+        warp_compact(n, own, &ncols, [&](int c) { return p[c] >= 0 && p[c] % es == slice; });
+        __syncthreads();
         const double *Ae = AT + aoff[e];
-        for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
-            int r = t / n, c = t % n;
-            int pr = p[r], pc = p[c];
-            if (pr >= 0 && pc >= 0) {
-                if (es > 1) atomicAdd(&M[pr + (int64_t)pc * nO], Ae[t]);
-                else M[pr + (int64_t)pc * nO] += Ae[t];
-            }
+        const int nc = ncols;
+        for (int t = threadIdx.x; t < nc * n; t += blockDim.x) {
+            const int c = own[t / n], r = t % n;
+            const int pr = p[r];
+            if (pr >= 0) M[pr + (int64_t)p[c] * nO] += Ae[(int64_t)c * n + r];
         }
         __syncthreads();
     }
@@ -513,16 +536,25 @@ __global__ void k_symmetrize_sq(double *A, const int64_t *off, const int64_t *nn
     }
 }
 
-// dense coarsest matrix: D += R_T^T A_T R_T (column-major n x n)
-__global__ void k_assemble_dense(const int64_t *eptr, const int32_t *eidx, int64_t ne,
-                                 const double *AT, const int64_t *aoff, double *D, int64_t n) {
-    for (int64_t e = blockIdx.x; e < ne; e += gridDim.x) {
-        int64_t b = eptr[e];
-        int m = (int)(eptr[e + 1] - b);
-        const double *A = AT + aoff[e];
-        for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
-            int r = t / m, c = t % m;
-            atomicAdd(&D[eidx[b + r] + (int64_t)eidx[b + c] * n], A[t]);
+// dense coarsest matrix: D = sum_T R_T^T A_T R_T (column-major n x n).  A CTA owns column j and
+// adds, in the ascending element order of the DOF -> element map, column loc(j, T) of every
+// A_T containing j: each entry has one writer and a fixed summation order (no atomics).
+__global__ void k_assemble_dense(const int64_t *eptr, const int32_t *eidx, const int64_t *dptr,
+                                 const int32_t *didx, const double *AT, const int64_t *aoff, double *D,
+                                 int64_t n) {
+    __shared__ int cloc;
+    for (int64_t j = blockIdx.x; j < n; j += gridDim.x) {
+        double *col = D + j * n;
+        for (int64_t q = dptr[j]; q < dptr[j + 1]; q++) {
+            const int32_t e = didx[q];
+            const int64_t b = eptr[e];
+            const int m = (int)(eptr[e + 1] - b);
+            for (int t = threadIdx.x; t < m; t += blockDim.x)
+                if (eidx[b + t] == (int32_t)j) cloc = t;   // DOFs of an element are distinct
+            __syncthreads();
+            const double *A = AT + aoff[e] + (int64_t)cloc * m;
+            for (int t = threadIdx.x; t < m; t += blockDim.x) col[eidx[b + t]] += A[t];
+            __syncthreads();
         }
     }
 }
@@ -660,7 +692,10 @@ void local_spectral(Level &L, const lsamg_options &o, int *err, cudaStream_t s, 
         { LSAMG_PROF(lvl_name(g_prof_level, "ls: assemble"), s);
         KTime kt(KC_ASSEMBLE, s);
         const int es = assembly_slices(na);
-        k_assemble_gep<<<dim3((unsigned)na, (unsigned)es), 256, maxE * sizeof(int32_t), s>>>(
+        const size_t asm_smem = 2 * (size_t)maxE * sizeof(int32_t);
+        if (asm_smem > 200 * 1024) fail(LSAMG_LIMIT, "element map longer than the assembly staging (25,600)");
+        CK(cudaFuncSetAttribute(k_assemble_gep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)asm_smem));
+        k_assemble_gep<<<dim3((unsigned)na, (unsigned)es), 256, asm_smem, s>>>(
             dids.p, na, L.aeptr.p, L.aeidx.p, L.eptr.p, L.eidx.p, L.AT.p, L.aoff.p, L.mult.p, L.Optr.p,
             L.Oidx.p, L.Olpos.p, L.wptr.p, At.p, datoff.p, Aww.p, dawoff.p, es);
         CK_LAUNCH(); }
@@ -709,17 +744,17 @@ void local_spectral(Level &L, const lsamg_options &o, int *err, cudaStream_t s, 
             rank.alloc(na, s);
             int32_t maxG = 0;
             for (auto g : nGv) maxG = std::max(maxG, g);
-            pstrf_batched(At.p, bAt, db0.p, dbn.p, maxG, perm.p, dpoff.p, rank.p, s);
+            pstrf_batched(At.p, bAt, db0.p, dbn.p, nwv, nGv, maxG, perm.p, dpoff.p, rank.p, err, s);
         }
-        trsm_batched(At.p, bGG, At.p, bGw, false, s);                 // W = L_G^{-1} At_Gw
-        syrk_tn_batched(At.p, bww, At.p, bW, -1.0, false, s);          // S = At_ww - W^T W
+        trsm_batched(At.p, bGG, At.p, bGw, false, s, err);                 // W = L_G^{-1} At_Gw
+        syrk_tn_batched(At.p, bww, At.p, bW, -1.0, false, s, err);          // S = At_ww - W^T W
         }
         { LSAMG_PROF(lvl_name(g_prof_level, "ls: gep transform"), s);
         // 3. GEP S y = mu A_ww y -> C = L^{-1} S L^{-T}
         potrf_batched(Aww.p, bAww, POTRF_SPD, err, s);
-        trsm_batched(Aww.p, bAww, At.p, bY, false, s);                // Y = L^{-1} S
+        trsm_batched(Aww.p, bAww, At.p, bY, false, s, err);                // Y = L^{-1} S
         transpose_batched(At.p, bww, C.p, bC, s);                     // C = Y^T
-        trsm_batched(Aww.p, bAww, C.p, bC, false, s);                 // C = L^{-1} S L^{-T}
+        trsm_batched(Aww.p, bAww, C.p, bC, false, s, err);                 // C = L^{-1} S L^{-T}
         }
         // 4. tridiagonalise, count and bisect the eigenvalues below 1/tau_cut
         { LSAMG_PROF(lvl_name(g_prof_level, "ls: sytd2"), s); sytd2_batched(C.p, bC, dv.p, ev.p, tv.p, dtoff.p, s); }
@@ -758,8 +793,8 @@ void local_spectral(Level &L, const lsamg_options &o, int *err, cudaStream_t s, 
             stein_batched(dv.p, ev.p, dtoff.p, bC.n.p, wv.p, dk.p, ch.V.p, bV, work.p, dwk.p, s, false);
             cholqr2_batched(ch.V.p, bV, err, s);
         }
-        { LSAMG_PROF(lvl_name(g_prof_level, "ls: ormtr"), s); ormtr_batched(C.p, bC, tv.p, dtoff.p, ch.V.p, bV, s); }
-        { LSAMG_PROF(lvl_name(g_prof_level, "ls: trsm Z"), s); trsm_batched(Aww.p, bAww, ch.V.p, bV, true, s); }
+        { LSAMG_PROF(lvl_name(g_prof_level, "ls: ormtr"), s); ormtr_batched(C.p, bC, tv.p, dtoff.p, ch.V.p, bV, s, err); }
+        { LSAMG_PROF(lvl_name(g_prof_level, "ls: trsm Z"), s); trsm_batched(Aww.p, bAww, ch.V.p, bV, true, s, err); }
         CK(cudaStreamSynchronize(s));
         check_err(err, s, "local spectral problems");
         chunks.push_back(std::move(ch));
@@ -945,7 +980,7 @@ void build_coarse(Level &F, Level &C, int *err, cudaStream_t s, double *flops) {
         }
         bA.set(oa, nn, nn, {}, s);
         bG.set(og, ldg, kk, nn, s);
-        syrk_tn_batched(C.AT.p, bA, Gst.p, bG, 1.0, true, s);
+        syrk_tn_batched(C.AT.p, bA, Gst.p, bG, 1.0, true, s, err);
         DBuf<int64_t> dn;
         std::vector<int64_t> n64(hcols.begin(), hcols.end());
         upload(dn, n64, s);
@@ -977,7 +1012,7 @@ void build_coarse(Level &F, Level &C, int *err, cudaStream_t s, double *flops) {
         upload(dpoff, poff, s);
         perm.alloc(std::max<int64_t>(poff[ng], 1), s);
         rank.alloc(std::max<int64_t>(ng, 1), s);
-        pstrf_batched(Wf.p, bW, db0.p, dbn.p, maxn, perm.p, dpoff.p, rank.p, s);
+        pstrf_batched(Wf.p, bW, db0.p, dbn.p, zero, nn, maxn, perm.p, dpoff.p, rank.p, err, s);
         auto hr = to_host(rank.p, ng, s);
         std::vector<int64_t> ngoff(ng + 1, 0);
         std::vector<int32_t> nrows(ng);
@@ -1004,6 +1039,12 @@ void build_coarse(Level &F, Level &C, int *err, cudaStream_t s, double *flops) {
 
 void smoother_setup(Level &L, const lsamg_options &o, int *err, cudaStream_t s, double *flops) {
     const int64_t nagg = L.nagg;
+    int32_t maxE = 1;
+    {
+        auto ep = to_host(L.eptr.p, L.ne + 1, s);
+        for (int64_t e = 0; e < L.ne; e++) maxE = std::max<int32_t>(maxE, (int32_t)(ep[e + 1] - ep[e]));
+    }
+    if ((size_t)maxE * sizeof(int32_t) > 200 * 1024) fail(LSAMG_LIMIT, "element map longer than the assembly staging");
     std::vector<int64_t> loff(nagg + 1, 0);
     for (int64_t a = 0; a < nagg; a++) loff[a + 1] = loff[a] + (int64_t)L.h_nO[a] * (L.h_nO[a] + 1) / 2;
     upload(L.Loff, loff, s);
@@ -1040,7 +1081,10 @@ void smoother_setup(Level &L, const lsamg_options &o, int *err, cudaStream_t s, 
         {
             KTime kta(KC_ASSEMBLE, s);
             const int es = assembly_slices(na);
-            k_assemble_smoother<<<dim3((unsigned)na, (unsigned)es), 256, 0, s>>>(
+            const size_t asm_smem = (size_t)maxE * sizeof(int32_t);
+            CK(cudaFuncSetAttribute(k_assemble_smoother, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)asm_smem));
+            k_assemble_smoother<<<dim3((unsigned)na, (unsigned)es), 256, asm_smem, s>>>(
                 a0, na, L.oeptr.p, L.oeidx.p, L.eptr.p, L.AT.p, L.aoff.p, L.oelocoff.p, L.oeloc.p, L.Optr.p,
                 AO.p, dmo.p, es);
             CK_LAUNCH();
@@ -1067,8 +1111,8 @@ void coarsest_setup(Level &L, int *err, cudaStream_t s, double *flops) {
     D.alloc(std::max<int64_t>(n * n, 1), s);
     D.zero(s);
     if (L.ne > 0) {
-        k_assemble_dense<<<gridc(L.ne, 1, 148 * 16), 256, 0, s>>>(L.eptr.p, L.eidx.p, L.ne, L.AT.p,
-                                                                 L.aoff.p, D.p, n);
+        k_assemble_dense<<<gridc(n, 1, 148 * 16), 256, 0, s>>>(L.eptr.p, L.eidx.p, L.dptr.p, L.didx.p, L.AT.p,
+                                                              L.aoff.p, D.p, n);
         CK_LAUNCH();
     }
     MatBatch b;

@@ -1,16 +1,18 @@
 // Allocation-free element Gram SpMV, lsamg_gram_spmv_static (include/lsamg.h).  The paper has
-// no counterpart: it is an engineering variant of the Gram SpMV y = sum_T R_T^T G_T^T (G_T R_T x)
-// (Section 2 eq. 2.1, Prop. 5.1) for callers that must not allocate device memory: applications
-// whose GPU memory belongs to another allocator (a framework's caching pool), and latency-
-// critical loops where cudaMalloc / cudaFree would synchronise the device.  It reads the
-// element factors from caller buffers and keeps the intermediate t_T = G_T x_T in one file-scope
-// device array instead of shared memory, so the call allocates nothing: no cudaMalloc, no
-// cudaFree and no allocating library routine.
+// no counterpart: it is a library convenience that computes y = sum_T R_T^T G_T^T (G_T R_T x)
+// for callers that cannot allocate device memory: applications whose GPU memory belongs to
+// another allocator (a framework's caching pool), and latency-critical loops where
+// cudaMalloc / cudaFree would synchronise the device.  It reads the element factors from caller
+// buffers and keeps the intermediate t_T = G_T x_T in one file-scope device array instead of
+// shared memory, so the call allocates nothing: no cudaMalloc, no cudaFree and no allocating
+// library routine.
 //
 // The array's name is only a host-side stand-in in host code: the first call on each device
 // looks up its device address with cudaGetSymbolAddress (that device current) and passes that
-// address to the kernels; that first call should come before any stream capture.  The array
-// keeps the previous call's contents; only the error flag must start at zero and is cleared.
+// address to the kernels.  Every call reads the error flag back and synchronises its stream, so
+// it cannot be captured into a CUDA graph; a call on a capturing stream is rejected up front.
+// The array keeps the previous call's contents; only the error flag must start at zero and is
+// cleared.
 //
 // Scratch layout (per device): words [0, 32) a header whose first int is the error flag (set by
 // the kernels for a DOF index outside [0, n_dofs); cleared at the start of every call), words
@@ -74,6 +76,24 @@ __global__ void k_static_rows(const int32_t *dofs, const double *G, const double
     }
 }
 
+// the same with a thread per (element, row), for small elements (n_T <= 16), where a warp over
+// the columns would leave most lanes idle
+__global__ void k_static_rows_thread(const int32_t *dofs, const double *G, const double *x, int64_t n,
+                                     int64_t ne, int nT, int m, double *t, int *flag) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < ne * m;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = q / m;
+        const double *g = G + q * nT;
+        const int32_t *d = dofs + e * nT;
+        double s = 0.0;
+        for (int c = 0; c < nT; c++) {
+            const int32_t j = d[c];
+            if (j >= 0 && j < n) s += g[c] * x[j]; else atomicExch(flag, 1);
+        }
+        t[q] = s;
+    }
+}
+
 // y[dofs_e[c]] += sum_i G_e[i, c] t[e m + i]: a thread per (element, column)
 __global__ void k_static_cols(const int32_t *dofs, const double *G, const double *t, int64_t n, int64_t ne,
                               int nT, int m, double *y, int *flag) {
@@ -118,14 +138,25 @@ extern "C" int lsamg_gram_spmv_static(int64_t n_dofs, int64_t n_elems, int32_t n
     }
     try {
         cudaStream_t s = static_cast<cudaStream_t>(stream);
+        cudaStreamCaptureStatus capst = cudaStreamCaptureStatusNone;
+        CK(cudaStreamIsCapturing(s, &capst));
+        if (capst != cudaStreamCaptureStatusNone) {
+            set_last_error("lsamg_gram_spmv_static: the stream is capturing; this call synchronises and "
+                           "cannot be captured");
+            return LSAMG_INVALID_ARG;
+        }
         double *base = scratch_for_current_device();
         int *flag = reinterpret_cast<int *>(base);
         double *t = base + kHeaderWords;
         CK(cudaMemsetAsync(flag, 0, sizeof(int), s));
         if (n_dofs > 0) CK(cudaMemsetAsync(y, 0, (size_t)n_dofs * sizeof(double), s));
         if (n_elems > 0 && m > 0) {
-            k_static_rows<<<grid_for(n_elems * m * 32, 256), 256, 0, s>>>(elem_dofs, G, x, n_dofs, n_elems, n_T,
-                                                                          m, t, flag);
+            if (n_T <= 16)
+                k_static_rows_thread<<<grid_for(n_elems * m, 256), 256, 0, s>>>(elem_dofs, G, x, n_dofs, n_elems,
+                                                                              n_T, m, t, flag);
+            else
+                k_static_rows<<<grid_for(n_elems * m * 32, 256), 256, 0, s>>>(elem_dofs, G, x, n_dofs, n_elems, n_T,
+                                                                              m, t, flag);
             CK_LAUNCH();
             k_static_cols<<<grid_for(n_elems * n_T, 256), 256, 0, s>>>(elem_dofs, G, t, n_dofs, n_elems, n_T, m,
                                                                       y, flag);

@@ -1,0 +1,363 @@
+// Blocked Householder tridiagonalisation of batches of symmetric matrices (lower storage), the
+// reduction behind the local eigenproblems C y = mu y of eq. 2.9.
+//
+// Per panel of PNB columns (LAPACK's latrd/sytrd organisation):
+//   * column j is brought up to date with the panel's earlier reflectors
+//     (a -= V W(j,:)^T + W V(j,:)^T), its Householder reflector is formed (d_j, e_j, tau_j);
+//   * y = A22 v, A22 the trailing matrix as it stood before the panel, read once over its lower
+//     triangle by 64 x 64 tiles spread over the whole GPU; every tile writes its two partial
+//     products (the tile and its transpose) to its own slot and one CTA per matrix sums the
+//     slots in a fixed order, so the result does not depend on scheduling;
+//   * w = tau (y - V (W^T v) - W (V^T v)), w -= (tau/2)(w^T v) v;
+//   * after the panel, A22 -= V W^T + W V^T over the lower triangle as one FP64 product of
+//     K = 2 PNB on the tensor cores (ozaki.cuh).
+// Conventions follow LAPACK's sytd2 (lower): H_j = I - tau_j v v^T with v = (1, A(j+2:n, j)),
+// beta = -sign(alpha) ||(alpha, x)||, d_j = A(j, j), e_j = beta stored at A(j+1, j).
+#include "dense.cuh"
+#include "impl.cuh"
+#include "ozaki.cuh"
+
+namespace lsamg {
+namespace {
+
+constexpr int PNB = 32;   // reflectors per panel (the rank-2k update has K = 64)
+constexpr int ST = 64;    // tile of the symmetric product
+
+__device__ double trd_block_sum(double v, double *red) {
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int i = 0; i < nw; i++) r += red[i];
+    return r;
+}
+
+// column j: panel update, reflector, v into V / WV and into vbuf (absolute row index)
+__global__ void __launch_bounds__(256) k_trd_col(double *base, const int64_t *off, const int32_t *ld,
+                                                 const int32_t *nn, int64_t count, int j, int j0, double *dd,
+                                                 double *ee, double *tt, const int64_t *toff, double *VW, double *WV,
+                                                 const int64_t *vwoff, double *vbuf) {
+    __shared__ double red[32];
+    __shared__ double wj[PNB], vj[PNB];
+    __shared__ double sh_tau, sh_scale;
+    const int64_t b = blockIdx.x;
+    if (b >= count) return;
+    const int n = nn[b];
+    if (j >= n) return;
+    const int jj = j - j0, L = ld[b];
+    double *A = base + off[b];
+    double *V = VW + vwoff[b], *W = V + (int64_t)PNB * n;
+    double *W2 = WV + vwoff[b], *V2 = W2 + (int64_t)PNB * n;
+    for (int q = threadIdx.x; q < jj; q += blockDim.x) {
+        wj[q] = W[j + (int64_t)q * n];
+        vj[q] = V[j + (int64_t)q * n];
+    }
+    __syncthreads();
+    for (int r = j + threadIdx.x; r < n; r += blockDim.x) {
+        double a = A[r + (int64_t)j * L];
+        for (int q = 0; q < jj; q++) a -= V[r + (int64_t)q * n] * wj[q] + W[r + (int64_t)q * n] * vj[q];
+        A[r + (int64_t)j * L] = a;
+    }
+    __syncthreads();
+    double *d = dd + toff[b], *e = ee + toff[b], *tau = tt + toff[b];
+    if (j == n - 1) {
+        if (threadIdx.x == 0) d[j] = A[j + (int64_t)j * L];
+        return;
+    }
+    const int m = n - j - 1;
+    double *x = A + (j + 1) + (int64_t)j * L;
+    double sig = 0.0;
+    for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) sig += x[i] * x[i];
+    sig = trd_block_sum(sig, red);
+    if (threadIdx.x == 0) {
+        const double alpha = x[0];
+        d[j] = A[j + (int64_t)j * L];
+        if (sig == 0.0) {
+            sh_tau = 0.0;
+            sh_scale = 0.0;
+            e[j] = alpha;
+        } else {
+            const double beta = -copysign(sqrt(alpha * alpha + sig), alpha);
+            sh_tau = (beta - alpha) / beta;
+            sh_scale = 1.0 / (alpha - beta);
+            e[j] = beta;
+        }
+        tau[j] = sh_tau;
+    }
+    __syncthreads();
+    const double sc = sh_scale;
+    const bool refl = sh_tau != 0.0;
+    double *vb = vbuf + toff[b];
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        double vi = 1.0;
+        if (i > 0) {
+            vi = refl ? x[i] * sc : 0.0;
+            if (refl) x[i] = vi;
+        }
+        const int r = j + 1 + i;
+        vb[r] = vi;
+        V[r + (int64_t)jj * n] = vi;
+        V2[r + (int64_t)jj * n] = vi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) x[0] = e[j];
+}
+
+// per matrix: tiles of the trailing lower triangle that the symmetric product of column j needs
+// (none when the reflector is the identity); exclusive prefix over the batch in pre[0..count]
+__global__ void __launch_bounds__(1024) k_trd_sched(const int32_t *nn, int64_t count, int j, const double *tt,
+                                                    const int64_t *toff, int64_t *pre) {
+    __shared__ int64_t part[1024];
+    const int64_t per = (count + blockDim.x - 1) / blockDim.x;
+    const int64_t b0 = threadIdx.x * per, b1 = min(count, b0 + per);
+    int64_t s = 0;
+    for (int64_t b = b0; b < b1; b++) {
+        const int m = nn[b] - j - 1;
+        if (m > 0 && tt[toff[b] + j] != 0.0) {
+            const int64_t T = (m + ST - 1) / ST;
+            s += T * (T + 1) / 2;
+        }
+    }
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t acc = 0;
+        for (int t = 0; t < (int)blockDim.x; t++) {
+            const int64_t v = part[t];
+            part[t] = acc;
+            acc += v;
+        }
+        pre[count] = acc;
+    }
+    __syncthreads();
+    int64_t acc = part[threadIdx.x];
+    for (int64_t b = b0; b < b1; b++) {
+        pre[b] = acc;
+        const int m = nn[b] - j - 1;
+        if (m > 0 && tt[toff[b] + j] != 0.0) {
+            const int64_t T = (m + ST - 1) / ST;
+            acc += T * (T + 1) / 2;
+        }
+    }
+}
+
+__device__ __forceinline__ int trd_find(const int64_t *pre, int64_t count, int64_t w) {
+    int64_t lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (pre[mid] <= w) lo = mid; else hi = mid - 1;
+    }
+    return (int)lo;
+}
+
+__device__ __forceinline__ void trd_tri(int64_t t, int &ti, int &tj) {
+    int i = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while ((int64_t)(i + 1) * (i + 2) / 2 <= t) i++;
+    while ((int64_t)i * (i + 1) / 2 > t) i--;
+    ti = i;
+    tj = (int)(t - (int64_t)i * (i + 1) / 2);
+}
+
+// partial products of the 64 x 64 tiles of the trailing lower triangle with v: slot (ti, tj)
+// holds A22(ti, tj) v(tj) (the diagonal tile as the full symmetric block), slot (tj, ti) holds
+// A22(ti, tj)^T v(ti)
+__global__ void __launch_bounds__(256) k_trd_symv(const double *base, const int64_t *off, const int32_t *ld,
+                                                  const int32_t *nn, int64_t count, int j, const int64_t *toff,
+                                                  const double *vbuf, double *P, const int64_t *poff,
+                                                  const int64_t *pre) {
+    __shared__ double tile[ST][ST + 1];
+    __shared__ double vr[ST], vc[ST];
+    const int64_t total = pre[count];
+    const int lane4 = threadIdx.x & 3, idx = threadIdx.x >> 2;   // 64 groups of 4 threads
+    for (int64_t w = blockIdx.x; w < total; w += gridDim.x) {
+        const int b = trd_find(pre, count, w);
+        int ti, tj;
+        trd_tri(w - pre[b], ti, tj);
+        const int n = nn[b], L = ld[b], m = n - j - 1;
+        const int T = (m + ST - 1) / ST;
+        const double *A22 = base + off[b] + (j + 1) + (int64_t)(j + 1) * L;
+        const double *v = vbuf + toff[b] + (j + 1);
+        const int r0 = ti * ST, c0 = tj * ST;
+        for (int t = threadIdx.x; t < ST * ST; t += blockDim.x) {
+            const int rr = t % ST, cc = t / ST;
+            const int gr = r0 + rr, gc = c0 + cc;
+            double a = 0.0;
+            if (gr < m && gc < m && gr >= gc) a = A22[gr + (int64_t)gc * L];
+            tile[rr][cc] = a;
+        }
+        for (int t = threadIdx.x; t < ST; t += blockDim.x) {
+            vr[t] = (r0 + t < m) ? v[r0 + t] : 0.0;
+            vc[t] = (c0 + t < m) ? v[c0 + t] : 0.0;
+        }
+        __syncthreads();
+        const bool diag = (ti == tj);
+        // row part: row idx, 16 columns per thread of the group
+        double rs = 0.0, cs = 0.0;
+        for (int c = lane4; c < ST; c += 4) {
+            double a = tile[idx][c];
+            if (diag && c > idx) a = tile[c][idx];       // upper half of the diagonal tile by symmetry
+            rs += a * vc[c];
+        }
+        if (!diag)
+            for (int r = lane4; r < ST; r += 4) cs += tile[r][idx] * vr[r];
+        rs += __shfl_xor_sync(0xffffffffu, rs, 1);
+        rs += __shfl_xor_sync(0xffffffffu, rs, 2);
+        cs += __shfl_xor_sync(0xffffffffu, cs, 1);
+        cs += __shfl_xor_sync(0xffffffffu, cs, 2);
+        if (lane4 == 0) {
+            double *Pb = P + poff[b];
+            Pb[((int64_t)ti * T + tj) * ST + idx] = rs;
+            if (!diag) Pb[((int64_t)tj * T + ti) * ST + idx] = cs;
+        }
+        __syncthreads();
+    }
+}
+
+// w of column j: y = sum of the slots in fixed order, the panel corrections, the tau/2 term
+__global__ void __launch_bounds__(256) k_trd_w(const int32_t *nn, int64_t count, int j, int j0, const double *tt,
+                                               const int64_t *toff, const double *vbuf, const double *P,
+                                               const int64_t *poff, double *VW, double *WV, const int64_t *vwoff,
+                                               double *ybuf) {
+    __shared__ double red[32];
+    __shared__ double s1[PNB], s2[PNB];
+    const int64_t b = blockIdx.x;
+    if (b >= count) return;
+    const int n = nn[b];
+    const int m = n - j - 1;
+    if (m <= 0) return;
+    const int jj = j - j0;
+    double *V = VW + vwoff[b], *W = V + (int64_t)PNB * n;
+    double *W2 = WV + vwoff[b];
+    const double tau = tt[toff[b] + j];
+    if (tau == 0.0) {
+        for (int r = j + 1 + threadIdx.x; r < n; r += blockDim.x) {
+            W[r + (int64_t)jj * n] = 0.0;
+            W2[r + (int64_t)jj * n] = 0.0;
+        }
+        return;
+    }
+    const double *v = vbuf + toff[b];
+    const int T = (m + ST - 1) / ST;
+    const double *Pb = P + poff[b];
+    double *y = ybuf + toff[b];
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const int ti = i / ST, rr = i % ST;
+        double acc = 0.0;
+        for (int t = 0; t < T; t++) acc += Pb[((int64_t)ti * T + t) * ST + rr];
+        y[j + 1 + i] = acc;
+    }
+    // s1 = W^T v, s2 = V^T v over rows j+1 .. n-1 (a warp per panel column)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    for (int q = warp; q < jj; q += nwarp) {
+        double a1 = 0.0, a2 = 0.0;
+        for (int r = j + 1 + lane; r < n; r += 32) {
+            a1 += W[r + (int64_t)q * n] * v[r];
+            a2 += V[r + (int64_t)q * n] * v[r];
+        }
+        for (int o = 16; o; o >>= 1) {
+            a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+            a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+        }
+        if (lane == 0) {
+            s1[q] = a1;
+            s2[q] = a2;
+        }
+    }
+    __syncthreads();
+    double wv = 0.0;
+    for (int r = j + 1 + threadIdx.x; r < n; r += blockDim.x) {
+        double a = y[r];
+        for (int q = 0; q < jj; q++) a -= V[r + (int64_t)q * n] * s1[q] + W[r + (int64_t)q * n] * s2[q];
+        a *= tau;
+        y[r] = a;
+        wv += a * v[r];
+    }
+    wv = trd_block_sum(wv, red);
+    const double alpha = -0.5 * tau * wv;
+    for (int r = j + 1 + threadIdx.x; r < n; r += blockDim.x) {
+        const double w = y[r] + alpha * v[r];
+        W[r + (int64_t)jj * n] = w;
+        W2[r + (int64_t)jj * n] = w;
+    }
+}
+
+}  // namespace
+
+void sytd2_batched(double *base, const MatBatch &Ab, double *d, double *e, double *tau, const int64_t *toff,
+                   cudaStream_t s) {
+    if (Ab.count == 0 || Ab.maxn == 0) return;
+    double fl = 0.0;
+    for (auto v : Ab.h_n) fl += 4.0 / 3.0 * v * v * v;
+    KTime kt(KC_SYTD2, s, fl);
+    const int64_t cnt = Ab.count;
+    std::vector<int64_t> vwoff(cnt + 1, 0), poff(cnt + 1, 0);
+    for (int64_t b = 0; b < cnt; b++) {
+        const int64_t n = Ab.h_n[b];
+        vwoff[b + 1] = vwoff[b] + 2 * PNB * n;
+        const int64_t T = cdiv(std::max<int64_t>(n - 1, 1), ST);
+        poff[b + 1] = poff[b] + T * T * ST;
+    }
+    const int64_t tn = read1(toff + cnt, s);
+    DBuf<double> VW, WV, P, vbuf, ybuf;
+    DBuf<int64_t> dvw, dpo, pre;
+    VW.alloc(std::max<int64_t>(vwoff[cnt], 1), s);
+    WV.alloc(std::max<int64_t>(vwoff[cnt], 1), s);
+    P.alloc(std::max<int64_t>(poff[cnt], 1), s);
+    vbuf.alloc(std::max<int64_t>(tn, 1), s);
+    ybuf.alloc(std::max<int64_t>(tn, 1), s);
+    pre.alloc(cnt + 1, s);
+    upload(dvw, std::vector<int64_t>(vwoff.begin(), vwoff.end() - 1), s);
+    upload(dpo, std::vector<int64_t>(poff.begin(), poff.end() - 1), s);
+    DBuf<int> err;
+    err.alloc(2, s);
+    err.zero(s);
+    oz::Workspace ws;
+    const unsigned symv_grid = 148 * 8;
+    for (int j0 = 0; j0 < Ab.maxn; j0 += PNB) {
+        const int j1 = std::min(Ab.maxn, j0 + PNB);
+        for (int j = j0; j < j1; j++) {
+            k_trd_col<<<(unsigned)cnt, 256, 0, s>>>(base, Ab.off.p, Ab.ld.p, Ab.n.p, cnt, j, j0, d, e, tau, toff,
+                                                     VW.p, WV.p, dvw.p, vbuf.p);
+            CK_LAUNCH();
+            if (j >= Ab.maxn - 1) break;
+            k_trd_sched<<<1, 1024, 0, s>>>(Ab.n.p, cnt, j, tau, toff, pre.p);
+            CK_LAUNCH();
+            k_trd_symv<<<symv_grid, 256, 0, s>>>(base, Ab.off.p, Ab.ld.p, Ab.n.p, cnt, j, toff, vbuf.p, P.p, dpo.p,
+                                                 pre.p);
+            CK_LAUNCH();
+            k_trd_w<<<(unsigned)cnt, 256, 0, s>>>(Ab.n.p, cnt, j, j0, tau, toff, vbuf.p, P.p, dpo.p, VW.p, WV.p,
+                                                  dvw.p, ybuf.p);
+            CK_LAUNCH();
+        }
+        // trailing update A22 -= V W^T + W V^T over rows / columns >= j1, K = 2 PNB
+        std::vector<oz::SplitJob> sa, sb;
+        std::vector<oz::GemmJob> gj;
+        int64_t h = 0, ex = 0;
+        for (int64_t b = 0; b < cnt; b++) {
+            const int64_t n = Ab.h_n[b];
+            const int m = (int)(n - j1);
+            if (m <= 0) continue;
+            const int64_t L = Ab.h_ld[b];
+            sa.push_back(oz::SplitJob{vwoff[b] + j1, 1, n, h, ex, m, 2 * PNB});
+            const int64_t ha = h, ea = ex;
+            h += oz::slice_halves(m, 2 * PNB);
+            ex += oz::exp_ints(m);
+            sb.push_back(oz::SplitJob{vwoff[b] + j1, 1, n, h, ex, m, 2 * PNB});
+            const int64_t hb = h, eb = ex;
+            h += oz::slice_halves(m, 2 * PNB);
+            ex += oz::exp_ints(m);
+            gj.push_back(oz::GemmJob{ha, hb, ea, eb, Ab.h_off[b] + j1 + (int64_t)j1 * L, 1, L, m, m, 2 * PNB, 1, 0, 0});
+        }
+        if (gj.empty()) continue;
+        ws.reserve(h, ex, s);
+        oz::split(VW.p, sa, ws.sl.p, ws.ex.p, s);
+        oz::split(WV.p, sb, ws.sl.p, ws.ex.p, s);
+        oz::gemm(ws.sl.p, ws.ex.p, base, gj, -1.0, 1.0, err.p, s);
+    }
+    check_err(err.p, s, "tridiagonal reduction");
+}
+
+}  // namespace lsamg

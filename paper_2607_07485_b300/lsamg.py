@@ -74,6 +74,8 @@ _lib.lsamg_query.argtypes = [_H, C.c_int32, C.c_int32, C.c_void_p, C.c_int64, C.
 _lib.lsamg_destroy.argtypes = [_H]
 _lib.lsamg_gram_spmv_static.argtypes = [C.c_int64, C.c_int64, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
                                         C.c_void_p, C.c_void_p, C.c_void_p]
+_lib.lsamg_dgemm_nt.argtypes = [C.c_int64, C.c_int64, C.c_int64, C.c_double, C.c_void_p, C.c_int64, C.c_void_p,
+                                C.c_int64, C.c_double, C.c_void_p, C.c_int64, C.c_void_p]
 _lib.lsamg_last_error.restype = C.c_char_p
 _lib.lsamg_kernel_classes.restype = C.c_int32
 _lib.lsamg_kernel_name.restype = C.c_char_p
@@ -84,7 +86,7 @@ _lib.lsamg_launch_count.restype = C.c_int64
 EXPORTS = ["lsamg_options_default", "lsamg_setup", "lsamg_apply", "lsamg_solve", "lsamg_solve_host",
            "lsamg_gram_spmv", "lsamg_elem_grad", "lsamg_get_stats", "lsamg_stage_name", "lsamg_query",
            "lsamg_destroy", "lsamg_last_error", "lsamg_kernel_classes", "lsamg_kernel_name",
-           "lsamg_kernel_stats_all", "lsamg_launch_count", "lsamg_gram_spmv_static"]
+           "lsamg_kernel_stats_all", "lsamg_launch_count", "lsamg_gram_spmv_static", "lsamg_dgemm_nt"]
 
 
 def kernel_stats():
@@ -100,18 +102,66 @@ def kernel_stats():
     return out
 
 
+def _check_static_args(elem_dofs, G, x, y):
+    """Reject every input the allocation-free Gram SpMV cannot take safely.  The C entry point
+    only sees raw pointers, so a wrong dtype, a strided view, a short output or a tensor on
+    another device would make its kernels read or write past the buffers; it must not copy or
+    convert either (that would allocate), so it refuses instead.  Raises ValueError."""
+    import torch
+    for name, t, dt in (("elem_dofs", elem_dofs, torch.int32), ("G", G, torch.float64),
+                        ("x", x, torch.float64), ("y", y, torch.float64)):
+        if not isinstance(t, torch.Tensor):
+            raise ValueError(f"{name} must be a torch tensor")
+        if t.dtype != dt:
+            raise ValueError(f"{name} must be {dt}, got {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    if elem_dofs.dim() != 2:
+        raise ValueError("elem_dofs must be 2-D [n_elems, n_T]")
+    ne, nT = elem_dofs.shape
+    if nT < 1:
+        raise ValueError("elem_dofs must have n_T >= 1 columns")
+    if G.dim() != 3 or G.shape[0] != ne or G.shape[2] != nT:
+        raise ValueError(f"G must be [n_elems={ne}, m, n_T={nT}], got {tuple(G.shape)}")
+    if x.dim() != 1 or y.dim() != 1 or y.numel() != x.numel():
+        raise ValueError("x and y must be 1-D with the same length")
+    if not torch.cuda.is_available():
+        raise ValueError("the tensors must be CUDA tensors (no CUDA device is available)")
+    cur = torch.cuda.current_device()
+    for name, t in (("elem_dofs", elem_dofs), ("G", G), ("x", x), ("y", y)):
+        if not t.is_cuda or t.device.index != cur:
+            raise ValueError(f"{name} must be on the current CUDA device cuda:{cur}, got {t.device}")
+
+
 def gram_spmv_static(elem_dofs, G, x, y, stream=None):
     """y = sum_T R_T^T G_T^T (G_T x_T) through the allocation-free entry point (no handle), for
-    callers that must not allocate device memory (GPU memory owned by another allocator, or a
+    callers that cannot allocate device memory (GPU memory owned by another allocator, or a
     latency-critical loop where cudaMalloc would synchronise the device).
-    elem_dofs: int32 [ne, nT], G: float64 [ne, m, nT], x, y: float64 [n] device tensors (y is
-    overwritten; nothing is allocated here or in the library).  Make the first call on a device
-    before any stream capture: it looks up the library's static scratch array."""
+    elem_dofs: int32 [ne, nT], G: float64 [ne, m, nT], x, y: float64 [n], all contiguous on the
+    current CUDA device (y is overwritten; nothing is allocated here or in the library; any
+    other input raises ValueError before the library is called).  The call synchronises its
+    stream, so it cannot be recorded into a CUDA graph; on a capturing stream it is refused."""
+    _check_static_args(elem_dofs, G, x, y)
     ne, nT = elem_dofs.shape
-    m = G.shape[1] if G.dim() == 3 else 0
+    m = G.shape[1]
     _check(_lib.lsamg_gram_spmv_static(int(x.numel()), int(ne), int(nT), int(m), _ptr(elem_dofs), _ptr(G),
                                        _ptr(x), _ptr(y), _stream(stream)))
     return y
+
+
+def dgemm_nt(A, B, C=None, alpha=1.0, beta=0.0, stream=None):
+    """C = alpha A B^T + beta C in FP64 on the tensor cores (lsamg_dgemm_nt).  A: [M, K], B: [N, K],
+    C: [M, N] float64 CUDA tensors (row-major torch layout; transposed copies give the library its
+    column-major operands)."""
+    import torch
+    M, K = A.shape
+    N = B.shape[0]
+    At = A.t().contiguous()
+    Bt = B.t().contiguous()
+    Ct = (torch.zeros(N, M, dtype=torch.float64, device=A.device) if C is None else C.t().contiguous())
+    _check(_lib.lsamg_dgemm_nt(M, N, K, float(alpha), _ptr(At), max(M, 1), _ptr(Bt), max(N, 1), float(beta), _ptr(Ct),
+                               max(M, 1), _stream(stream)))
+    return Ct.t()
 
 
 def launch_count():

@@ -8,7 +8,7 @@ import pytest
 
 import oracle as O
 
-pytestmark = [pytest.mark.gpu, pytest.mark.skip(reason="not yet run on a B300; enable once it passes there")]
+pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
@@ -36,24 +36,31 @@ def test_additive_vcycle_matches_oracle(name):
     amg.close()
 
 
+# Residual-reduction target per case, above the FP64 evaluation floor 64 eps || |A| |x| || / ||r_0||
+# of its data (rt1_beta1: ~1e-13; cfg1, beta = 1e-4: 5.5e-8, where the oracle's iteration
+# stagnates near 2e-10 and never reaches 1e-10).
+STATIONARY_RTOL = {"rt1_beta1": 1e-10, "cfg1": 1e-8}
+
+
 @pytest.mark.parametrize("name", ["rt1_beta1", "cfg1"])
 @pytest.mark.parametrize("smoother", [0, 1])
 def test_stationary_mode_matches_oracle(name, smoother):
     import scipy.sparse.linalg as spla
-    p, H, amg, vtol = _handle(name, smoother=smoother, rtol=1e-10, maxit=300)
+    rtol = STATIONARY_RTOL[name]
+    p, H, amg, vtol = _handle(name, smoother=smoother, rtol=rtol, maxit=300)
     n = p["n"]
     b = p["b"][0]
     x0 = np.random.default_rng(22).standard_normal(n)
     x, its, rel, rc = amg.solve(torch.from_numpy(b).to(DEV), x0=torch.from_numpy(x0).to(DEV), mode=2)
-    assert rc == 0 and rel[0] <= 1e-10
+    assert rc == 0 and rel[0] <= rtol
     A = H.levels[0].A
     xs = spla.spsolve(A.tocsc(), b)
     xg = x.cpu().numpy()
-    # the residual reduction of 1e-10 bounds the error by kappa(A) times it; compare residuals
-    assert np.linalg.norm(b - A @ xg) <= 1e-10 * np.linalg.norm(b - A @ x0) * 1.01 + 64 * np.finfo(float).eps * \
+    # the residual reduction bounds the error by kappa(A) times it; compare residuals
+    assert np.linalg.norm(b - A @ xg) <= rtol * np.linalg.norm(b - A @ x0) * 1.01 + 64 * np.finfo(float).eps * \
         np.linalg.norm(abs(A) @ abs(xs))
-    xo, ito, _ = O.stationary(H, b, x0, rtol=1e-10, smoother="additive" if smoother else "multiplicative")
-    assert abs(int(its[0]) - ito) <= 1
+    xo, ito, _ = O.stationary(H, b, x0, rtol=rtol, smoother="additive" if smoother else "multiplicative")
+    assert ito < 500 and abs(int(its[0]) - ito) <= 1
     amg.close()
 
 
