@@ -11,7 +11,8 @@ One step = GPU set-up of the hierarchy from the element blocks already resident 
 (element factorisation, aggregation, closures, local spectral problems, coarse Gram,
 Schwarz factors, coarsest factorisation) + the preconditioned solve to ||r|| <= 1e-8 ||b||.
 The solve mode (FP64 flexible CG around the FP32 V-cycle, or FP64 PCG around the FP64
-V-cycle) is the faster converging one measured during warm-up; both are reported.
+V-cycle) is the faster one measured during warm-up (the first warm-up set-up serves both
+modes); both are reported.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lsamg|reference] [--cfg 2|4] [--N mesh]
 
@@ -39,7 +40,7 @@ WORKLOAD_CFG = 2
 WORKLOAD_N = 256
 # Solver options of the benchmark: two aggregation passes on the finest level (paper), one on
 # coarse levels and up to four levels (at 2.1M DOFs the paper's 3-level / 2-pass hierarchy
-# leaves a ~90k-DOF dense coarsest problem and ~9k-DOF local eigenproblems, see DESIGN.md).
+# leaves a ~90k-DOF dense coarsest problem and ~9k-DOF local eigenproblems).
 BENCH_OPTS = dict(agg_passes=2, agg_passes_coarse=1, max_levels=4, maxit=400)
 # Workloads: the default (RT_[3] grad-div, one right-hand side) and the 3D elasticity batch
 # (Q2 hexahedra, 16 right-hand sides in one batched solve; one aggregation pass on every level,
@@ -57,6 +58,16 @@ def l2_note(c):
         return f"inputs larger than L2 (element blocks {mb:.0f} MB, read every step)"
     return f"inputs smaller than L2 (element blocks {mb:.0f} MB), no flush: a reduced size, not the benchmark"
 FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12   # 148 SMs x 2 FP64 FMA/clk x 2 flop x 2032 MHz
+# FP16 tensor products per FP64-equivalent product in the split-operand GEMM (7 slices, the 28
+# slice pairs with p + q <= 8)
+TC_PAIRS = 28
+# Leaf kernel classes of the library's timers that run on the FP64 pipe (bound "alu"); the
+# split-operand products are "tensor", the classes with algorithmic bytes "hbm"
+ALU_CLASSES = ("potrf", "trsm", "pstrf", "ormtr", "elem_factor")
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the leaf kernels from an
+# ncu capture of the kernel as it now stands (the summaries under profiles/); a kernel changed since
+# its capture has no entry
+TRAFFIC = {}
 
 
 def parse():
@@ -164,27 +175,27 @@ def max_over_ranks(value, device=None):
 
 
 # ----------------------------------------------------------------------------- CPU oracle leg
-def oracle_sample(n_full, cfg=WORKLOAD_CFG):
+def oracle_sample(cfg=WORKLOAD_CFG, threads=None):
     """The FP64 oracle on a bounded sample of the same workload (a small mesh of the same
     elements, the same options and the same number of right-hand sides): set-up + FP64 PCG to
-    1e-8 per right-hand side; returns (seconds, scaled seconds for the full DOF count, info)."""
+    1e-8 per right-hand side, with `threads` BLAS threads (None: all).  Returns (seconds, info)."""
     import oracle as O
+    from threadpoolctl import threadpool_limits
     c = workload(WORKLOADS[cfg]["sample_N"], cfg)
     o = dict(WORKLOADS[cfg]["opts"])
     o.pop("maxit", None)
-    t = time.perf_counter()
-    H = O.setup(c["n"], c["elem_dofs"], scaled_mats(c), opts=o, c_tau=c["c_tau"])
-    ts = time.perf_counter() - t
-    A = H.levels[0].A
-    t = time.perf_counter()
-    it = 0
-    for b in c["b"]:
-        x, its_b, hist = O.pcg(lambda v: A @ v, b, lambda r: O.vcycle(H, r))
-        it = max(it, its_b)
-    tsol = time.perf_counter() - t
-    total = ts + tsol
-    scale = n_full / c["n"]
-    return total, total * scale, dict(n=c["n"], setup_s=ts, solve_s=tsol, its=it, scale=scale)
+    with threadpool_limits(limits=threads):
+        t = time.perf_counter()
+        H = O.setup(c["n"], c["elem_dofs"], scaled_mats(c), opts=o, c_tau=c["c_tau"])
+        ts = time.perf_counter() - t
+        A = H.levels[0].A
+        t = time.perf_counter()
+        it = 0
+        for b in c["b"]:
+            x, its_b, hist = O.pcg(lambda v: A @ v, b, lambda r: O.vcycle(H, r))
+            it = max(it, its_b)
+        tsol = time.perf_counter() - t
+    return ts + tsol, dict(n=c["n"], N=c["N"], name=workload_name(c), setup_s=ts, solve_s=tsol, its=it)
 
 
 def cpu_cores():
@@ -197,31 +208,49 @@ def cpu_cores():
     return int(blas or os.cpu_count() or 1)
 
 
+def cpu_baseline_entry(cfg, n_full, runs=1):
+    """The oracle timed on its bounded sample with all BLAS threads and with one; `value` is the
+    measured all-thread time of one sample step.  A DOF-ratio extrapolation to the full workload is
+    given separately (a lower bound: the local work grows as the cube of the aggregate size)."""
+    t_all = [oracle_sample(cfg)[0] for _ in range(runs)]
+    t_one, info = oracle_sample(cfg, threads=1)
+    v = statistics.mean(t_all)
+    return dict(value=v, unit="s", cores=cpu_cores(), kind="oracle",
+                sample=(f"FP64 oracle (NumPy/SciPy) set-up + PCG to 1e-8 per right-hand side on {info['name']} "
+                        f"(the same elements, options and right-hand-side count at a bounded size); "
+                        f"{v:.2f} s with {cpu_cores()} BLAS threads, {t_one:.2f} s with 1"),
+                sample_dofs=info["n"], one_thread_s=t_one, nproc=os.cpu_count(),
+                dof_scaled_lower_bound_s=v * n_full / info["n"])
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
     full = workload(args.N, args.cfg)
-    n_full = full["n"]
     for _ in range(args.warmup):
-        oracle_sample(n_full, args.cfg)
-    times = []
+        oracle_sample(args.cfg)
+    times, info = [], None
     for _ in range(args.steps):
-        raw, scaled, info = oracle_sample(n_full, args.cfg)
-        times.append((raw, scaled, info))
-    val = statistics.mean(t[1] for t in times)
-    info = times[-1][2]
-    sample = (f"FP64 oracle (NumPy/SciPy) set-up + PCG to 1e-8 per right-hand side on the same elements at "
-              f"{info['n']:,} DOFs; seconds scaled by the DOF ratio {info['scale']:.1f}: a lower bound, since "
-              f"small meshes have smaller aggregates and the local work grows as their cube")
+        t, info = oracle_sample(args.cfg)
+        times.append(t)
+    val = statistics.mean(times) if times else 0.0
+    if info is None:
+        info = dict(n=workload(WORKLOADS[args.cfg]["sample_N"], args.cfg)["n"],
+                    name=workload_name(workload(WORKLOADS[args.cfg]["sample_N"], args.cfg)))
+    sample = (f"FP64 oracle (NumPy/SciPy) set-up + PCG to 1e-8 per right-hand side, each step on {info['name']} "
+              f"(a bounded sample of the benchmark workload: same elements, options and right-hand sides)")
+    sc = workload(WORKLOADS[args.cfg]["sample_N"], args.cfg)
     out = dict(metric=METRIC, value=val, unit="s", n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
                ms_per_step=1000 * val, higher_is_better=False, scaling="weak", vs_baseline=None,
                dtype="f64", data="synthetic", impl="reference",
-               config=dict(workload=workload_name(full), n_dofs=n_full, nrhs=int(full["b"].shape[0]),
+               config=dict(workload=info["name"], n_dofs=int(info["n"]), nrhs=int(full["b"].shape[0]),
                            solve_mode="pcg+fp64-vcycle",
-                           options=dict(WORKLOADS[args.cfg]["opts"], tau_c=full["c_tau"]), l2=l2_note(full),
-                           parallelism=f"replicas x{args.gpus}", sample_dofs=info["n"]),
+                           options=dict(WORKLOADS[args.cfg]["opts"], tau_c=full["c_tau"]), l2=l2_note(sc),
+                           parallelism=f"replicas x{args.gpus}", sample_of=workload_name(full),
+                           sample_of_dofs=int(full["n"])),
                cpu_baseline=dict(value=val, unit="s", cores=cpu_cores(), kind="oracle", sample=sample,
-                                 raw_sample_s=statistics.mean(t[0] for t in times)),
+                                 nproc=os.cpu_count()),
+               dof_scaled_lower_bound_s=val * full["n"] / info["n"],
                e2e=dict(value=val, unit="s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(out), flush=True)
 
@@ -256,29 +285,39 @@ def main():
     d_b = torch.from_numpy(rhs(c)).to(dev)
     opts = dict(WORKLOADS[args.cfg]["opts"], tau_c=c["c_tau"])
 
-    def step(mode, profile=0):
+    def setup(profile=0):
         amg = Lsamg(n, d_dofs, d_mats, d_coef, profile=profile, **opts)
         torch.cuda.synchronize()
+        return amg
+
+    def solve(amg, mode):
         t1 = time.perf_counter()
         x, its, rel, rc = amg.solve(d_b, mode=mode)
         torch.cuda.synchronize()
-        t2 = time.perf_counter()
+        return time.perf_counter() - t1, int(np.max(its)), float(np.max(rel)), rc
+
+    def step(mode, profile=0):
+        amg = setup(profile)
+        tsol, its, rel, rc = solve(amg, mode)
         st = amg.stats()
         amg.close()
-        return st, t2 - t1, int(np.max(its)), float(np.max(rel)), rc
+        return st, tsol, its, rel, rc
 
-    # ---- warm-up: both solve modes, pick the faster converging one (without warm-up steps, the
-    # FP64 PCG mode)
+    # ---- warm-up: the first set-up serves both solve modes; the faster converged one is timed
+    # (without warm-up steps, the FP64 PCG mode)
     modes = {}
     best_mode = 0
     for w in range(args.warmup):
+        t0 = time.perf_counter()
+        amg = setup()
+        st = amg.stats()
         for mode in ((0, 1) if w == 0 else (best_mode,)):
-            t0 = time.perf_counter()
-            st, tsol, its, rel, rc = step(mode)
+            tsol, its, rel, rc = solve(amg, mode)
             modes[mode] = dict(setup_s=st["setup_seconds"], solve_s=tsol, its=its, relres=rel,
                                converged=(rc == 0), step_s=time.perf_counter() - t0)
+        amg.close()
         conv = [m for m in modes if modes[m]["converged"]]
-        best_mode = min(conv, key=lambda m: modes[m]["solve_s"]) if conv else 0
+        best_mode = min(conv, key=lambda m: modes[m]["setup_s"] + modes[m]["solve_s"]) if conv else 0
     # ---- timed region
     kernel_stats()  # reset the per-kernel counters
     clocks = ClockSampler(local)
@@ -331,34 +370,43 @@ def main():
             dist.destroy_process_group()
         return
 
-    # ---- roofline of the dominant kernel class (device time inside the timed region)
+    # ---- rooflines of the leaf kernel classes (device time inside the timed region, CUDA events
+    # on the launching stream); the dominant one is the line's roofline
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except OSError:
         pass
     hbm_peak = peaks.get("hbm_gbs", 6400.0)
+    tc_peak = peaks.get("bf16_tflops_sustained", 1400.0)
     rooflines = []
     for name, k in ks.items():
-        if k["flops"] > 0:
-            ach = k["flops"] / (k["ms"] * 1e-3) / 1e12
-            rooflines.append(dict(kernel=name, bound="alu", achieved=ach, peak=FP64_PEAK_TFLOPS,
-                                  unit="TFLOP/s", frac=ach / FP64_PEAK_TFLOPS, traffic=None, ms=k["ms"],
-                                  launches=k["calls"], peak_source="derived: 148 SMs x 2 FP64 FMA/clk x 2032 MHz"))
+        r = None
+        t = k["ms"] * 1e-3
+        if name == "tc_dgemm" and k["flops"] > 0:
+            fp64 = k["flops"] / t / 1e12
+            ach = fp64 * TC_PAIRS
+            r = dict(kernel=name, bound="tensor", achieved=ach, peak=tc_peak, unit="TFLOP/s", frac=ach / tc_peak,
+                     peak_source=("measured: cuBLAS bf16 sustained (FP16 has the same dense rate)"
+                                  if "bf16_tflops_sustained" in peaks else "fallback"),
+                     fp64_equivalent_tflops=fp64, fp64_equivalent_vs_fp64_peak=fp64 / FP64_PEAK_TFLOPS)
+        elif name in ALU_CLASSES and k["flops"] > 0:
+            ach = k["flops"] / t / 1e12
+            r = dict(kernel=name, bound="alu", achieved=ach, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
+                     frac=ach / FP64_PEAK_TFLOPS, peak_source="derived: 148 SMs x 2 FP64 FMA/clk x 2032 MHz")
         elif k["bytes"] > 0:
-            ach = k["bytes"] / (k["ms"] * 1e-3) / 1e9
-            rooflines.append(dict(kernel=name, bound="hbm", achieved=ach, peak=hbm_peak, unit="GB/s",
-                                  frac=ach / hbm_peak, traffic=None, ms=k["ms"], launches=k["calls"],
-                                  peak_source="measured" if "hbm_gbs" in peaks else "fallback"))
+            ach = k["bytes"] / t / 1e9
+            r = dict(kernel=name, bound="hbm", achieved=ach, peak=hbm_peak, unit="GB/s", frac=ach / hbm_peak,
+                     peak_source="measured" if "hbm_gbs" in peaks else "fallback")
+        if r is not None:
+            r.update(ms=k["ms"] / args.steps, launches=k["calls"] // max(args.steps, 1),
+                     traffic=TRAFFIC.get(name))
+            rooflines.append(r)
     dominant = max(ks.items(), key=lambda kv: kv[1]["ms"])[0] if ks else None
     roof = next((r for r in rooflines if r["kernel"] == dominant), None)
-    cpu = None
-    if not args.no_cpu_baseline:
-        raw, scaled, info = oracle_sample(n, args.cfg)
-        cpu = dict(value=scaled, unit="s", cores=cpu_cores(), kind="oracle",
-                   sample=(f"FP64 oracle set-up + PCG to 1e-8 per right-hand side on the same elements at "
-                           f"{info['n']:,} DOFs took {raw:.2f} s; scaled by the DOF ratio {info['scale']:.1f} "
-                           f"(a lower bound: small meshes have smaller aggregates)"))
+    if roof is None and rooflines:
+        roof = max(rooflines, key=lambda r: r["ms"])
+    cpu = None if args.no_cpu_baseline else cpu_baseline_entry(args.cfg, n)
     out = dict(
         metric=METRIC, value=per_step, unit="s", n_gpus=world, steps=args.steps, warmup=args.warmup,
         ms_per_step=1000 * per_step, higher_is_better=False, scaling="weak", vs_baseline=None,
@@ -372,6 +420,8 @@ def main():
         hierarchy=dict(n=stats["n"], n_agg=stats["n_agg"], OC=stats["OC"], GC=stats["GC"], tau=stats["tau"],
                        setup_flops=stats["setup_flops"], stages=stats["stages"]),
         roofline=roof, rooflines=rooflines, dominant_kernel=dominant,
+        ms_per_step_by_class="library CUDA-event timers per leaf class; tc_dgemm / tc_split are the tensor-core "
+                             "FP64 products inside potrf / trsm / syrk / pstrf / sytd2 / ormtr",
         kernel_ms={k: v["ms"] / args.steps for k, v in ks.items()},
         gpu_launches=int(launches), wall_s=wall, cpu_baseline=cpu, e2e=e2e, clocks=clk)
     print(json.dumps(out), flush=True)

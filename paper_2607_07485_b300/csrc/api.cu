@@ -115,6 +115,8 @@ void finish_level_info(Level &L, cudaStream_t s) {
         L.spmv_bytes[t] = gent * w + ment * 4.0 + 3.0 * (double)L.n * w;
         L.coarse_bytes[t] = L.coarsest ? 2.0 * (double)L.n * (double)(L.n + 1) / 2.0 * w : 0.0;
     }
+    if (L.coarsest)
+        wave_setup(L, {{(int32_t)L.n}}, {{0}}, {(int32_t)L.n}, L.tri_cb, s);
     if (!L.coarsest && L.nagg > 0 && L.ncol > 0) {
         auto oep = to_host(L.oeptr.p, L.nagg + 1, s);
         auto oei = to_host(L.oeidx.p, oep[L.nagg], s);
@@ -137,6 +139,16 @@ void finish_level_info(Level &L, cudaStream_t s) {
         }
         upload(L.pair_agg, pa, s);
         upload(L.pair_ent, pe, s);
+        // wavefront solve groups: each colour, then all subdomains (additive smoother)
+        std::vector<std::vector<int32_t>> gs(L.ncol + 1), gid(L.ncol + 1);
+        for (int c = 0; c < L.ncol; c++)
+            for (int64_t q = L.colptr[c]; q < L.colptr[c + 1]; q++) {
+                gs[c].push_back(L.h_nO[cag[q]]);
+                gid[c].push_back(cag[q]);
+                gs[L.ncol].push_back(L.h_nO[cag[q]]);
+                gid[L.ncol].push_back(cag[q]);
+            }
+        wave_setup(L, gs, gid, L.h_nO, L.tri_cb, s);
         for (int c = 0; c < L.ncol; c++)
             for (int64_t q = L.colptr[c]; q < L.colptr[c + 1]; q++) {
                 const int32_t a = cag[q];
@@ -446,6 +458,7 @@ int do_stationary(Handle &H, const double *b, double *x, int nrhs, bool use_x0, 
         }
     }
     CK(cudaStreamSynchronize(s));
+    for (const auto &L : H.levels) wave_check(L, s);
     prof_report("solve");
     bool ok = true;
     for (int i = 0; i < nrhs; i++) {
@@ -556,6 +569,7 @@ int do_solve(Handle &H, const double *b, double *x, int nrhs, int mode, bool use
         vec_xpby(p, z, d + 5 * nrhs, n, nrhs, s);
     }
     CK(cudaStreamSynchronize(s));
+    for (const auto &L : H.levels) wave_check(L, s);
     prof_report("solve");
     bool ok = true;
     for (int i = 0; i < nrhs; i++) {
@@ -660,6 +674,7 @@ int lsamg_apply(lsamg_handle *h, const double *r, double *z, int32_t nrhs, int32
         bool f = fp32 < 0 ? H.opt.vcycle_fp32 != 0 : fp32 != 0;
         precondition(H, r, z, nrhs, f);
         CK(cudaStreamSynchronize(H.stream));
+        for (const auto &L : H.levels) wave_check(L, H.stream);
     });
 }
 

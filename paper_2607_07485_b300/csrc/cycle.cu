@@ -57,6 +57,71 @@ __global__ void __launch_bounds__(128) k_spmv(const int64_t *eptr, const int32_t
     }
 }
 
+// The same for levels whose element blocks fit 64 x 64 (the fine level: 40 x 40): a warp per
+// element, eight per CTA.  G_T is loaded once, coalesced, into the warp's shared tile (rows padded
+// to nT + 1: conflict-free row and column reads); t = G_T x_T with lanes on rows, then
+// G_T^T t with lanes on columns, x_T gathered once per right-hand side and broadcast by shuffles.
+constexpr int SPMV_WARPS = 8;
+template <class T>
+__global__ void __launch_bounds__(256) k_spmv_warp(const int64_t *eptr, const int32_t *eidx, int64_t ne,
+                                                   const T *G, const int64_t *goff, const int32_t *grows,
+                                                   const T *x, T *y, int64_t n, int nrhs, T sign, int ldt,
+                                                   int rows) {
+    extern __shared__ unsigned char smraw[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T *Gs = reinterpret_cast<T *>(smraw) + (int64_t)warp * rows * ldt;
+    for (int64_t e = (int64_t)blockIdx.x * SPMV_WARPS + warp; e < ne; e += (int64_t)gridDim.x * SPMV_WARPS) {
+        const int64_t b = eptr[e];
+        const int nT = (int)(eptr[e + 1] - b);
+        const int m = grows[e];
+        const T *g = G + goff[e];
+        for (int t = lane; t < m * nT; t += 32) {
+            const int i = t / nT, c = t - i * nT;
+            Gs[i * ldt + c] = g[t];
+        }
+        const int d0 = lane < nT ? eidx[b + lane] : 0, d1 = lane + 32 < nT ? eidx[b + 32 + lane] : 0;
+        __syncwarp();
+        for (int r = 0; r < nrhs; r++) {
+            const T *xr = x + (int64_t)r * n;
+            const T x0 = lane < nT ? xr[d0] : (T)0, x1 = lane + 32 < nT ? xr[d1] : (T)0;
+            T t0 = 0, t1 = 0;
+            for (int c = 0; c < nT; c++) {
+                const T xc = __shfl_sync(0xffffffffu, c < 32 ? x0 : x1, c & 31);
+                if (lane < m) t0 += Gs[lane * ldt + c] * xc;
+                if (lane + 32 < m) t1 += Gs[(lane + 32) * ldt + c] * xc;
+            }
+            T y0 = 0, y1 = 0;
+            for (int i = 0; i < m; i++) {
+                const T ti = __shfl_sync(0xffffffffu, i < 32 ? t0 : t1, i & 31);
+                if (lane < nT) y0 += Gs[i * ldt + lane] * ti;
+                if (lane + 32 < nT) y1 += Gs[i * ldt + lane + 32] * ti;
+            }
+            T *yr = y + (int64_t)r * n;
+            if (lane < nT) atomicAdd(&yr[d0], sign * y0);
+            if (lane + 32 < nT) atomicAdd(&yr[d1], sign * y1);
+        }
+        __syncwarp();
+    }
+}
+
+// launches the Gram SpMV of level L: y (+)= sign G^T G x
+template <class T>
+void launch_spmv(const Level &L, const T *G, const T *x, T *y, int nrhs, T sign, cudaStream_t s) {
+    if (L.max_nT <= 64 && L.max_grows_cached <= 64) {
+        const int ldt = L.max_nT + 1, rows = std::max(1, L.max_grows_cached);
+        const size_t sm = (size_t)SPMV_WARPS * rows * ldt * sizeof(T);
+        CK(cudaFuncSetAttribute(k_spmv_warp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        const unsigned grid = gridv(L.ne, SPMV_WARPS, 148 * 8);
+        k_spmv_warp<T><<<grid, 32 * SPMV_WARPS, sm, s>>>(L.eptr.p, L.eidx.p, L.ne, G, L.goff.p, L.grows.p, x, y,
+                                                        L.n, nrhs, sign, ldt, rows);
+    } else {
+        const size_t sm = (size_t)std::max(1, L.max_grows_cached) * sizeof(T);
+        k_spmv<T><<<gridv(L.ne, 1, 148 * 24), 128, sm, s>>>(L.eptr.p, L.eidx.p, L.ne, G, L.goff.p, L.grows.p, x,
+                                                          y, L.n, nrhs, sign);
+    }
+    CK_LAUNCH();
+}
+
 // ---------------------------------------------------------------- packed triangular solves
 // In-place solve of L L^T v = v for a packed lower row-major factor (row i at i(i+1)/2),
 // vector v in global memory (one right-hand side).  Called by a whole CTA.
@@ -251,261 +316,214 @@ __global__ void __launch_bounds__(256) k_interp(const int64_t *wptr, const int32
 }
 
 // ---------------------------------------------------------------- blocked triangular solves
-// In-place solve of L L^T v = v for several independent packed lower row-major factors (row i
-// at offset i(i+1)/2): the subdomains of one Schwarz colour, or the coarsest matrix.  Rows are
-// cut into blocks of cb <= TRI_CB rows whose diagonal blocks are inverted once at set-up
-// (Dinv, FP64 packed lower row-major, block b of system a at Doff[a] + b cb(cb+1)/2; the
-// product with it is formed in FP64 in the FP32 cycle too, since an explicit inverse of an
-// ill-conditioned block rounded to FP32 loses its small components to cancellation).  Every launch
-// advances all systems by one block: CTA 0 of a system finishes the next diagonal block (its
-// update by the block just solved, then the product with the inverted diagonal block; all of
-// its loads are issued on entry), CTAs 1.. apply the block just solved to the rest of the
-// system with coalesced loads, many in flight per thread.
+// The Schwarz (and coarsest) factors are packed lower row-major (row i at offset i(i+1)/2).  Rows
+// are cut into blocks of cb <= TRI_CB rows whose diagonal blocks are inverted once at set-up
+// (Dinv, FP64 packed lower row-major, block b of system a at Doff[a] + b cb(cb+1)/2; the product
+// with it is formed in FP64 in the FP32 cycle too, since an explicit inverse of an
+// ill-conditioned block rounded to FP32 loses its small components to cancellation).
 constexpr int TRI_CB = 64;      // largest block
-constexpr int TRI_RG = 8;       // right-hand sides per pass through shared memory
-constexpr int TRI_RPW = TRI_CB / 8;   // block rows per warp in CTA 0
-constexpr int TRI_NU = TRI_CB / 32;   // block columns per lane
-constexpr int TRI_ROWS = 64;    // rows per forward update CTA (8 per warp)
-constexpr int TRI_COLS = 128;   // columns per backward update CTA (2 row halves per column)
 
 __host__ __device__ inline int64_t tri_block_words(int cb) { return (int64_t)cb * (cb + 1) / 2; }
 
-// Forward substitution L y = v.  Block k = rows [k cb, (k+1) cb) already holds y_k; finish block
-// k+1.  k = -1 starts every system (solves block 0).
-template <class T>
-__global__ void __launch_bounds__(256) k_tri_fwd(const int32_t *sys, const int64_t *Optr, const T *Lp,
-                                                 const int64_t *Loff, const double *Dp, const int64_t *Doff,
-                                                 int k, int cb, T *ws, int64_t wsn, int nrhs) {
-    __shared__ T sm[2 * TRI_RG * TRI_CB];
-    const int32_t a = sys ? sys[blockIdx.y] : (int32_t)blockIdx.y;
-    const int64_t ob = Optr[a];
-    const int n = (int)(Optr[a + 1] - ob);
-    const int r0 = k * cb, r1 = r0 + cb;
-    if (r1 >= n) return;
-    const int r2 = min(n, r1 + cb);
-    const T *L = Lp + Loff[a];
-    T *v = ws + ob;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    T *y = sm;                       // [TRI_RG][cb]  y_k
-    T *tv = sm + TRI_RG * TRI_CB;    // [TRI_RG][cb]  block k+1 right-hand sides
-    if (blockIdx.x > 0) {
-        // rows i in [i0, i0 + TRI_ROWS) beyond block k+1: v_i -= L[i, r0:r1] y_k
-        if (k < 0) return;
-        const int64_t i0 = (int64_t)r2 + (int64_t)(blockIdx.x - 1) * TRI_ROWS;
-        if (i0 >= n) return;
-        constexpr int NQ = TRI_ROWS / 8;
-        T lv[NQ][TRI_NU];
-#pragma unroll
-        for (int q = 0; q < NQ; q++) {
-            const int64_t i = i0 + warp + 8 * q;
-#pragma unroll
-            for (int u = 0; u < TRI_NU; u++) {
-                const int j = lane + 32 * u;
-                lv[q][u] = (i < n && j < cb) ? L[i * (i + 1) / 2 + r0 + j] : (T)0;
-            }
-        }
-        for (int g0 = 0; g0 < nrhs; g0 += TRI_RG) {
-            const int nr = min(TRI_RG, nrhs - g0);
-            __syncthreads();
-            for (int q = threadIdx.x; q < nr * cb; q += blockDim.x) {
-                const int r = q / cb;
-                y[r * TRI_CB + q - r * cb] = v[(int64_t)(g0 + r) * wsn + r0 + (q - r * cb)];
-            }
-            __syncthreads();
-            for (int r = 0; r < nr; r++) {
-                T *vr = v + (int64_t)(g0 + r) * wsn;
-                T old[NQ];
-#pragma unroll
-                for (int q = 0; q < NQ; q++) {
-                    const int64_t i = i0 + warp + 8 * q;
-                    old[q] = (lane == 0 && i < n) ? vr[i] : (T)0;
-                }
-#pragma unroll
-                for (int q = 0; q < NQ; q++) {
-                    T acc = 0;
-#pragma unroll
-                    for (int u = 0; u < TRI_NU; u++) {
-                        const int j = lane + 32 * u;
-                        if (j < cb) acc += lv[q][u] * y[r * TRI_CB + j];
-                    }
-                    acc = warp_sum(acc);
-                    const int64_t i = i0 + warp + 8 * q;
-                    if (lane == 0 && i < n) vr[i] = old[q] - acc;
-                }
-            }
-        }
-        return;
-    }
-    // CTA 0: block k+1 = rows [r1, r2); t = v - L[r1:r2, r0:r1] y_k, then y_{k+1} = Dinv t
-    const int nb = r2 - r1;
-    const double *Di = Dp + Doff[a] + (int64_t)(k + 1) * tri_block_words(cb);
-    T pv[TRI_RPW][TRI_NU];
-    double dv[TRI_RPW][TRI_NU];
-#pragma unroll
-    for (int q = 0; q < TRI_RPW; q++) {
-        const int i = warp + 8 * q;
-        const int64_t gi = (int64_t)r1 + i;
-#pragma unroll
-        for (int u = 0; u < TRI_NU; u++) {
-            const int j = lane + 32 * u;
-            pv[q][u] = (k >= 0 && i < nb && j < cb) ? L[gi * (gi + 1) / 2 + r0 + j] : (T)0;
-            dv[q][u] = (i < nb && j <= i) ? Di[i * (i + 1) / 2 + j] : 0.0;
-        }
-    }
-    for (int g0 = 0; g0 < nrhs; g0 += TRI_RG) {
-        const int nr = min(TRI_RG, nrhs - g0);
-        __syncthreads();
-        for (int q = threadIdx.x; q < nr * TRI_CB; q += blockDim.x) {
-            const int r = q / TRI_CB, j = q - r * TRI_CB;
-            const T *vr = v + (int64_t)(g0 + r) * wsn;
-            y[q] = (k >= 0 && j < cb) ? vr[r0 + j] : (T)0;
-            tv[q] = (j < nb) ? vr[r1 + j] : (T)0;
-        }
-        __syncthreads();
-        if (k >= 0) {
-            for (int r = 0; r < nr; r++) {
-#pragma unroll
-                for (int q = 0; q < TRI_RPW; q++) {
-                    const int i = warp + 8 * q;
-                    T acc = 0;
-#pragma unroll
-                    for (int u = 0; u < TRI_NU; u++) acc += pv[q][u] * y[r * TRI_CB + lane + 32 * u];
-                    acc = warp_sum(acc);
-                    if (lane == 0 && i < nb) tv[r * TRI_CB + i] -= acc;
-                }
-            }
-            __syncthreads();
-        }
-        for (int r = 0; r < nr; r++) {
-            T *vr = v + (int64_t)(g0 + r) * wsn;
-#pragma unroll
-            for (int q = 0; q < TRI_RPW; q++) {
-                const int i = warp + 8 * q;
-                double acc = 0;
-#pragma unroll
-                for (int u = 0; u < TRI_NU; u++) acc += dv[q][u] * (double)tv[r * TRI_CB + lane + 32 * u];
-                acc = warp_sum(acc);
-                if (lane == 0 && i < nb) vr[r1 + i] = (T)acc;
-            }
-        }
-    }
+// ---------------------------------------------------------------- wavefront triangular solves
+// L L^T v = v for the systems of one solve group (a Schwarz colour, all subdomains, or the
+// coarsest matrix) in two persistent cooperative launches, one per substitution.  A task is one
+// block row (forward) or block column (backward) of cb <= 64 rows of one system; the tasks are
+// listed in dependency order (forward: by block index, backward: by distance from the last
+// block) and CTA c takes tasks c, c + grid, ...  A task streams its part of the packed factor once,
+// consuming finished blocks of the same system as their flags come up (epoch-stamped, acquire /
+// release), applies the FP64 inverted diagonal block and publishes its own block.  Since every
+// CTA is resident (cooperative launch) and a task waits only on tasks listed before it, the
+// smallest unfinished task can always proceed.  Every wait is bounded (2 s on the global timer):
+// on expiry the kernel records LSAMG_DEVICE_TIMEOUT and returns.
+constexpr int WF_RG = 4;            // right-hand sides per pass over the factor
+
+__device__ __forceinline__ uint32_t wf_load_acquire(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void wf_store_release(uint32_t *p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t wf_timer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
 }
 
-// Backward substitution L^T x = y.  Block k holds x_k (k < K = ceil(n / cb)); finish block k-1.
-// k = K starts a system (solves its last block).
-template <class T>
-__global__ void __launch_bounds__(256) k_tri_bwd(const int32_t *sys, const int64_t *Optr, const T *Lp,
-                                                 const int64_t *Loff, const double *Dp, const int64_t *Doff,
-                                                 int k, int cb, T *ws, int64_t wsn, int nrhs) {
-    __shared__ T sm[2 * TRI_RG * TRI_CB + TRI_RG * TRI_COLS];
-    __shared__ double red[4 * TRI_RG * TRI_CB];   // CTA 0: partial sums of the 4 row parts
-    const int32_t a = sys ? sys[blockIdx.y] : (int32_t)blockIdx.y;
-    const int64_t ob = Optr[a];
-    const int n = (int)(Optr[a + 1] - ob);
-    const int K = (n + cb - 1) / cb;
-    if (k > K || k < 1) return;
-    const bool first = (k == K);
-    const int r0 = k * cb, r1 = min(n, r0 + cb);        // block k (unless first)
-    const int b0 = (k - 1) * cb, b1 = first ? n : r0;   // block k-1
-    const T *L = Lp + Loff[a];
-    T *v = ws + ob;
-    const int tid = threadIdx.x;
-    T *xk = sm;                                 // [TRI_RG][TRI_CB]  x_k
-    if (blockIdx.x > 0) {
-        // columns j in [c0, c0 + TRI_COLS) before block k-1: v_j -= sum_{i in block k} L[i, j] x_i
-        if (first) return;
-        const int c0 = (int)(blockIdx.x - 1) * TRI_COLS;
-        if (c0 >= b0) return;
-        const int col = tid & (TRI_COLS - 1), half = tid >> 7;
-        const int j = c0 + col;
-        T *part = sm + TRI_RG * TRI_CB;         // [TRI_RG][TRI_COLS]
-        constexpr int NL = TRI_CB / 2;
-        T lv[NL];
-#pragma unroll
-        for (int m = 0; m < NL; m++) {
-            const int i = r0 + half + 2 * m;
-            lv[m] = (j < b0 && i < r1) ? L[(int64_t)i * (i + 1) / 2 + j] : (T)0;
-        }
-        for (int g0 = 0; g0 < nrhs; g0 += TRI_RG) {
-            const int nr = min(TRI_RG, nrhs - g0);
-            __syncthreads();
-            for (int q = tid; q < nr * TRI_CB; q += blockDim.x) {
-                const int r = q / TRI_CB, i = q - r * TRI_CB;
-                xk[q] = (r0 + i < r1) ? v[(int64_t)(g0 + r) * wsn + r0 + i] : (T)0;
-            }
-            __syncthreads();
-            T acc[TRI_RG];
-#pragma unroll
-            for (int r = 0; r < TRI_RG; r++) {
-                acc[r] = 0;
-                if (r < nr) {
-#pragma unroll
-                    for (int m = 0; m < NL; m++) acc[r] += lv[m] * xk[r * TRI_CB + half + 2 * m];
+// thread 0 waits until flag >= epoch (wrap-safe); the CTA then proceeds together.  Returns false
+// (for every thread) when the wait gave up.
+__device__ __forceinline__ bool wf_wait(const uint32_t *flag, uint32_t epoch, int *err, int *s_ok) {
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        if ((int32_t)(wf_load_acquire(flag) - epoch) < 0) {
+            const uint64_t t0 = wf_timer();
+            while ((int32_t)(wf_load_acquire(flag) - epoch) < 0) {
+                if (wf_timer() - t0 > 2000000000ull) {
+                    ok = 0;
+                    if (err && atomicCAS(err, 0, LSAMG_DEVICE_TIMEOUT) == 0) err[1] = (int)blockIdx.x;
+                    break;
                 }
             }
-            if (half == 1)
-                for (int r = 0; r < nr; r++) part[r * TRI_COLS + col] = acc[r];
-            __syncthreads();
-            if (half == 0 && j < b0)
-                for (int r = 0; r < nr; r++) v[(int64_t)(g0 + r) * wsn + j] -= acc[r] + part[r * TRI_COLS + col];
         }
-        return;
+        *s_ok = ok;
     }
-    // CTA 0: block k-1 = rows [b0, b1); t = v - L[r0:r1, b0:b1]^T x_k, then x_{k-1} = Dinv^T t.
-    // Thread (col, part): column col of the block, rows part, part + 4, ...
-    const int nb = b1 - b0;
-    const int col = tid & (TRI_CB - 1), part = tid / TRI_CB;   // 4 parts
-    constexpr int NP = TRI_CB / 4;
-    const double *Di = Dp + Doff[a] + (int64_t)(k - 1) * tri_block_words(cb);
-    T pv[NP];
-    double dv[NP];
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+template <class T, bool FWD>
+__global__ void __launch_bounds__(256) k_tri_wave(const int32_t *tasks, int64_t ntask, const int32_t *sys,
+                                                  const int64_t *Optr, const T *Lp, const int64_t *Loff,
+                                                  const double *Dp, const int64_t *Doff, const int64_t *Foff,
+                                                  uint32_t *flags, uint32_t epoch, int cb, T *ws, int64_t wsn,
+                                                  int nrhs, int *err) {
+    __shared__ T yj[WF_RG][TRI_CB];
+    __shared__ double tv[WF_RG][TRI_CB];
+    __shared__ double red[8][WF_RG][TRI_CB];
+    __shared__ int s_ok;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t q = blockIdx.x; q < ntask; q += gridDim.x) {
+        const int si = tasks[2 * q], k = tasks[2 * q + 1];
+        const int32_t a = sys ? sys[si] : si;
+        const int64_t ob = Optr[a];
+        const int n = (int)(Optr[a + 1] - ob);
+        const int K = (n + cb - 1) / cb;
+        const int r0 = k * cb, nb = min(cb, n - r0);
+        const T *L = Lp + Loff[a];
+        T *v = ws + ob;
+        uint32_t *fl = flags + Foff[a];
+        const double *Di = Dp + Doff[a] + (int64_t)k * tri_block_words(cb);
+        for (int g0 = 0; g0 < nrhs; g0 += WF_RG) {
+            const int nr = min(WF_RG, nrhs - g0);
+            // per-warp partial sums over every dependency block: forward, rows warp + 8 i of the
+            // block (each lane over two columns); backward, columns lane / lane + 32 (each warp
+            // over rows warp + 8 i of the dependency block)
+            T part[WF_RG][8];
 #pragma unroll
-    for (int m = 0; m < NP; m++) {
-        const int ii = part + 4 * m;              // row within block k / within block k-1
-        const int gi = r0 + ii;
-        pv[m] = (!first && col < nb && gi < r1) ? L[(int64_t)gi * (gi + 1) / 2 + b0 + col] : (T)0;
-        dv[m] = (col < nb && ii < nb && ii >= col) ? Di[ii * (ii + 1) / 2 + col] : 0.0;
-    }
-    T *tv = sm + TRI_RG * TRI_CB;               // [TRI_RG][TRI_CB]
-    for (int g0 = 0; g0 < nrhs; g0 += TRI_RG) {
-        const int nr = min(TRI_RG, nrhs - g0);
-        __syncthreads();
-        for (int q = tid; q < nr * TRI_CB; q += blockDim.x) {
-            const int r = q / TRI_CB, i = q - r * TRI_CB;
-            const T *vr = v + (int64_t)(g0 + r) * wsn;
-            xk[q] = (!first && r0 + i < r1) ? vr[r0 + i] : (T)0;
-            tv[q] = (i < nb) ? vr[b0 + i] : (T)0;
-        }
-        __syncthreads();
-        if (!first) {
-            for (int r = 0; r < nr; r++) {
-                T acc = 0;
+            for (int r = 0; r < WF_RG; r++)
 #pragma unroll
-                for (int m = 0; m < NP; m++) acc += pv[m] * xk[r * TRI_CB + part + 4 * m];
-                red[(part * TRI_RG + r) * TRI_CB + col] = (double)acc;
+                for (int i = 0; i < 8; i++) part[r][i] = 0;
+            const int jn = FWD ? k : K - 1 - k;          // dependency blocks
+            for (int jj = 0; jj < jn; jj++) {
+                const int j = FWD ? jj : K - 1 - jj;
+                if (!wf_wait(fl + j, epoch, err, &s_ok)) return;
+                const int c0 = j * cb, nc = min(cb, n - c0);
+                for (int t = threadIdx.x; t < nr * TRI_CB; t += blockDim.x) {
+                    const int r = t / TRI_CB, c = t - r * TRI_CB;
+                    yj[r][c] = (c < nc) ? __ldcg(v + (int64_t)(g0 + r) * wsn + c0 + c) : (T)0;
+                }
+                __syncthreads();
+                T lv[8][2];
+                if (FWD) {
+                    // L[r0 + i, c0 + c]: rows of this block, columns of block j
+#pragma unroll
+                    for (int i = 0; i < 8; i++) {
+                        const int ii = warp + 8 * i;
+                        const int64_t gi = (int64_t)r0 + ii;
+#pragma unroll
+                        for (int u = 0; u < 2; u++) {
+                            const int c = lane + 32 * u;
+                            lv[i][u] = (ii < nb && c < nc) ? L[gi * (gi + 1) / 2 + c0 + c] : (T)0;
+                        }
+                    }
+#pragma unroll
+                    for (int r = 0; r < WF_RG; r++)
+                        if (r < nr)
+#pragma unroll
+                            for (int i = 0; i < 8; i++) part[r][i] += lv[i][0] * yj[r][lane] + lv[i][1] * yj[r][lane + 32];
+                } else {
+                    // L[c0 + i, r0 + c]: rows of block j, columns of this block
+#pragma unroll
+                    for (int i = 0; i < 8; i++) {
+                        const int ii = warp + 8 * i;
+                        const int64_t gi = (int64_t)c0 + ii;
+#pragma unroll
+                        for (int u = 0; u < 2; u++) {
+                            const int c = lane + 32 * u;
+                            lv[i][u] = (ii < nc && c < nb) ? L[gi * (gi + 1) / 2 + r0 + c] : (T)0;
+                        }
+                    }
+#pragma unroll
+                    for (int r = 0; r < WF_RG; r++)
+                        if (r < nr)
+#pragma unroll
+                            for (int i = 0; i < 8; i++) {
+                                const T y = yj[r][warp + 8 * i];
+                                part[r][0] += lv[i][0] * y;
+                                part[r][1] += lv[i][1] * y;
+                            }
+                }
+                __syncthreads();
+            }
+            // combine the partial sums: t = v_block - (L_block,deps . y_deps)
+            if (FWD) {
+#pragma unroll
+                for (int r = 0; r < WF_RG; r++)
+#pragma unroll
+                    for (int i = 0; i < 8; i++) {
+                        double sacc = (double)part[r][i];
+                        for (int o = 16; o; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+                        if (lane == 0) red[0][r][warp + 8 * i] = sacc;
+                    }
+                __syncthreads();
+                for (int t = threadIdx.x; t < nr * TRI_CB; t += blockDim.x) {
+                    const int r = t / TRI_CB, i = t - r * TRI_CB;
+                    tv[r][i] = (i < nb) ? (double)__ldcg(v + (int64_t)(g0 + r) * wsn + r0 + i) - red[0][r][i] : 0.0;
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < WF_RG; r++) {   // columns lane and lane + 32, summed over this warp's rows
+                    red[warp][r][lane] = (double)part[r][0];
+                    red[warp][r][lane + 32] = (double)part[r][1];
+                }
+                __syncthreads();
+                for (int t = threadIdx.x; t < nr * TRI_CB; t += blockDim.x) {
+                    const int r = t / TRI_CB, c = t - r * TRI_CB;
+                    double sacc = 0.0;
+#pragma unroll
+                    for (int w = 0; w < 8; w++) sacc += red[w][r][c];
+                    tv[r][c] = (c < nb) ? (double)__ldcg(v + (int64_t)(g0 + r) * wsn + r0 + c) - sacc : 0.0;
+                }
             }
             __syncthreads();
-            for (int q = tid; q < nr * TRI_CB; q += blockDim.x) {
-                const int r = q / TRI_CB, c = q - r * TRI_CB;
-                tv[q] -= (T)(red[(0 * TRI_RG + r) * TRI_CB + c] + red[(1 * TRI_RG + r) * TRI_CB + c] +
-                             red[(2 * TRI_RG + r) * TRI_CB + c] + red[(3 * TRI_RG + r) * TRI_CB + c]);
+            // this block: y = Dinv t (forward) or x = Dinv^T t (backward), FP64; 4 threads per entry
+            {
+                const int e = threadIdx.x >> 2, p = threadIdx.x & 3;
+                double acc[WF_RG];
+#pragma unroll
+                for (int r = 0; r < WF_RG; r++) acc[r] = 0.0;
+                if (e < nb) {
+                    if (FWD) {
+                        for (int c = p; c <= e; c += 4) {
+                            const double d = Di[e * (e + 1) / 2 + c];
+#pragma unroll
+                            for (int r = 0; r < WF_RG; r++) acc[r] += d * tv[r][c];
+                        }
+                    } else {
+                        for (int i = e + p; i < nb; i += 4) {
+                            const double d = Di[i * (i + 1) / 2 + e];
+#pragma unroll
+                            for (int r = 0; r < WF_RG; r++) acc[r] += d * tv[r][i];
+                        }
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < WF_RG; r++) {
+                    acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], 1);
+                    acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], 2);
+                }
+                __syncthreads();
+                if (p == 0 && e < nb)
+                    for (int r = 0; r < nr; r++) v[(int64_t)(g0 + r) * wsn + r0 + e] = (T)acc[r];
             }
             __syncthreads();
         }
-        for (int r = 0; r < nr; r++) {
-            double acc = 0;
-#pragma unroll
-            for (int m = 0; m < NP; m++) acc += dv[m] * (double)tv[r * TRI_CB + part + 4 * m];
-            red[(part * TRI_RG + r) * TRI_CB + col] = acc;
-        }
+        // publish the block
+        __threadfence();
         __syncthreads();
-        for (int q = tid; q < nr * TRI_CB; q += blockDim.x) {
-            const int r = q / TRI_CB, c = q - r * TRI_CB;
-            if (c < nb)
-                v[(int64_t)(g0 + r) * wsn + b0 + c] =
-                    (T)(red[(0 * TRI_RG + r) * TRI_CB + c] + red[(1 * TRI_RG + r) * TRI_CB + c] +
-                        red[(2 * TRI_RG + r) * TRI_CB + c] + red[(3 * TRI_RG + r) * TRI_CB + c]);
-        }
+        if (threadIdx.x == 0) wf_store_release(fl + k, epoch);
     }
 }
 
@@ -724,16 +742,7 @@ void gram_spmv(const Level &L, const T *x, T *y, const T *b, int nrhs, cudaStrea
     if (L.ne == 0) return;
     KTime kt(KC_SPMV, s, 0.0, L.spmv_bytes[std::is_same<T, double>::value ? 1 : 0] * (nrhs > 1 ? 1.0 : 1.0));
     const T *G = std::is_same<T, float>::value ? (const T *)L.G32.p : (const T *)L.G64.p;
-    int32_t maxm = 0;
-    // rows per element never exceed the element-map length on level 0; coarse groups can
-    // have more rows (stacked members), bounded by their G size.  Shared memory holds one
-    // row vector t of the largest element.
-    maxm = L.max_grows_cached;
-    size_t sm = (size_t)std::max(1, maxm) * sizeof(T);
-    k_spmv<T><<<gridv(L.ne, 1, 148 * 24), 128, sm, s>>>(L.eptr.p, L.eidx.p, L.ne, G, L.goff.p,
-                                                      L.grows.p, x, y, L.n, nrhs,
-                                                      b ? (T)-1 : (T)1);
-    CK_LAUNCH();
+    launch_spmv<T>(L, G, x, y, nrhs, b ? (T)-1 : (T)1, s);
 }
 
 void ensure_cycle_ws(Level &L, int nrhs, cudaStream_t s) {
@@ -768,30 +777,94 @@ static T *wsvec(Level &L) {
     if constexpr (std::is_same<T, float>::value) return L.ws32.p; else return L.ws64.p;
 }
 
-// L L^T v = v for systems sys[0..nsys) (sys == nullptr: systems 0..nsys-1) whose vectors sit at
-// ws + Optr[a] (stride wsn per right-hand side), factors at Lp + Loff[a] and inverted diagonal
-// blocks at Dp + Doff[a]; maxn bounds the systems' orders, cb is the block size of Dp.
+// L L^T v = v for the systems of solve group `grp` of level L (system array sys, or systems
+// 0..nsys-1 when sys == nullptr) whose vectors sit at ws + Optr[a] (stride wsn per right-hand side),
+// factors at Lp + Loff[a] and inverted diagonal blocks at Dp + Doff[a] (block size cb): the
+// forward and the backward wavefront launches.
 template <class T>
-static void tri_solve(const int32_t *sys, int64_t nsys, const int64_t *Optr, const T *Lp,
-                      const int64_t *Loff, const double *Dp, const int64_t *Doff, int cb, int maxn, T *ws,
-                      int64_t wsn, int nrhs, cudaStream_t s) {
-    const int K = (maxn + cb - 1) / cb;
-    for (int64_t y0 = 0; y0 < nsys; y0 += 65535) {
-        const unsigned ny = (unsigned)std::min<int64_t>(65535, nsys - y0);
-        if (!sys && y0 > 0) fail(LSAMG_LIMIT, "more than 65535 systems without an index list");
-        const int32_t *sy = sys ? sys + y0 : nullptr;
-        for (int k = -1; k <= K - 2; k++) {
-            const int64_t rest = (int64_t)maxn - (int64_t)(k + 2) * cb;
-            const unsigned gx = 1 + (unsigned)(k >= 0 && rest > 0 ? cdiv(rest, TRI_ROWS) : 0);
-            k_tri_fwd<T><<<dim3(gx, ny), 256, 0, s>>>(sy, Optr, Lp, Loff, Dp, Doff, k, cb, ws, wsn, nrhs);
-            CK_LAUNCH();
+static void tri_solve(Level &L, int grp, const int32_t *sys, const int64_t *Optr, const T *Lp,
+                      const int64_t *Loff, const double *Dp, const int64_t *Doff, int cb, T *ws, int64_t wsn,
+                      int nrhs, cudaStream_t s) {
+    const Level::WaveGroup &g = L.wf_groups[grp];
+    if (g.ntask == 0) return;
+    uint32_t *flags = L.wf_flags.p;
+    int *err = reinterpret_cast<int *>(L.wf_flags.p + 2 * L.wf_nflags);
+    CK(cudaMemsetAsync(flags, 0, 2 * L.wf_nflags * sizeof(uint32_t), s));
+    static int occ[2][2] = {{0, 0}, {0, 0}};
+    const int ti = std::is_same<T, double>::value ? 1 : 0;
+    for (int dir = 0; dir < 2; dir++) {
+        const bool fwd = dir == 0;
+        void *fn = fwd ? (void *)k_tri_wave<T, true> : (void *)k_tri_wave<T, false>;
+        if (!occ[ti][dir]) {
+            int o = 0;
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fn, 256, 0));
+            int dev = 0, sms = 0;
+            CK(cudaGetDevice(&dev));
+            CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            occ[ti][dir] = std::max(1, o) * sms;
         }
-        for (int k = K; k >= 1; k--) {
-            const int64_t cols = (int64_t)(k - 1) * cb;
-            const unsigned gx = 1 + (unsigned)(k < K && cols > 0 ? cdiv(cols, TRI_COLS) : 0);
-            k_tri_bwd<T><<<dim3(gx, ny), 256, 0, s>>>(sy, Optr, Lp, Loff, Dp, Doff, k, cb, ws, wsn, nrhs);
-            CK_LAUNCH();
-        }
+        const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(g.ntask, occ[ti][dir]));
+        const int32_t *tasks = L.wf_tasks.p + 2 * (fwd ? g.fwd : g.bwd);
+        int64_t ntask = g.ntask;
+        uint32_t *fl = flags + (fwd ? 0 : L.wf_nflags);
+        uint32_t epoch = 1;
+        const int64_t *foff = L.wf_foff.p;
+        void *args[] = {(void *)&tasks, (void *)&ntask, (void *)&sys, (void *)&Optr, (void *)&Lp, (void *)&Loff,
+                        (void *)&Dp, (void *)&Doff, (void *)&foff, (void *)&fl, (void *)&epoch, (void *)&cb,
+                        (void *)&ws, (void *)&wsn, (void *)&nrhs, (void *)&err};
+        CK(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(256), args, 0, s));
+        count_launch();
+    }
+}
+
+void wave_setup(Level &L, const std::vector<std::vector<int32_t>> &group_sizes,
+                const std::vector<std::vector<int32_t>> &group_ids, const std::vector<int32_t> &all_sizes, int cb,
+                cudaStream_t s) {
+    std::vector<int64_t> foff(all_sizes.size() + 1, 0);
+    for (size_t a = 0; a < all_sizes.size(); a++) foff[a + 1] = foff[a] + cdiv(all_sizes[a], cb);
+    std::vector<int32_t> tasks;
+    L.wf_groups.clear();
+    for (size_t gi = 0; gi < group_sizes.size(); gi++) {
+        const auto &sz = group_sizes[gi];
+        Level::WaveGroup g;
+        int Kmax = 0;
+        for (auto n : sz) Kmax = std::max<int>(Kmax, (int)cdiv(n, cb));
+        g.fwd = (int64_t)tasks.size() / 2;
+        for (int k = 0; k < Kmax; k++)            // forward: by block index, then system
+            for (size_t i = 0; i < sz.size(); i++)
+                if (k < cdiv(sz[i], cb)) {
+                    tasks.push_back((int32_t)i);
+                    tasks.push_back(k);
+                }
+        g.ntask = (int64_t)tasks.size() / 2 - g.fwd;
+        g.bwd = (int64_t)tasks.size() / 2;
+        for (int d = 0; d < Kmax; d++)            // backward: by distance from the last block
+            for (size_t i = 0; i < sz.size(); i++) {
+                const int K = (int)cdiv(sz[i], cb);
+                if (d < K) {
+                    tasks.push_back((int32_t)i);
+                    tasks.push_back(K - 1 - d);
+                }
+            }
+        (void)group_ids;
+        L.wf_groups.push_back(g);
+    }
+    upload(L.wf_tasks, tasks, s);
+    upload(L.wf_foff, std::vector<int64_t>(foff.begin(), foff.end() - 1), s);
+    L.wf_nflags = foff.back();
+    L.wf_flags.alloc(2 * L.wf_nflags + 2, s);
+    L.wf_flags.zero(s);
+}
+
+void wave_check(const Level &L, cudaStream_t s) {
+    if (!L.wf_flags.p) return;
+    int h[2];
+    CK(cudaMemcpyAsync(h, L.wf_flags.p + 2 * L.wf_nflags, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (h[0] != 0) {
+        char buf[200];
+        snprintf(buf, sizeof buf, "triangular solve: a dependency wait gave up (code %d, CTA %d)", h[0], h[1]);
+        fail(h[0], buf);
     }
 }
 
@@ -834,7 +907,7 @@ static void sweep_split(Level &L, int c, int nrhs, cudaStream_t s) {
     dim3 gg((unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv(maxn, 256), 64)), (unsigned)na);
     k_sw_gather<T><<<gg, 256, 0, s>>>(aggs, L.Optr.p, L.Oidx.p, rvec<T>(L), ws, L.n, L.Omega_total, nrhs);
     CK_LAUNCH();
-    tri_solve<T>(aggs, na, L.Optr.p, Lp, L.Loff.p, L.Di64.p, L.Doff.p, L.tri_cb, maxn, ws, L.Omega_total, nrhs, s);
+    tri_solve<T>(L, c, aggs, L.Optr.p, Lp, L.Loff.p, L.Di64.p, L.Doff.p, L.tri_cb, ws, L.Omega_total, nrhs, s);
     k_sw_addx<T><<<gg, 256, 0, s>>>(aggs, L.Optr.p, L.Oidx.p, ws, xvec<T>(L), L.n, L.Omega_total, nrhs);
     CK_LAUNCH();
     const int64_t np = L.colpairs[c + 1] - L.colpairs[c];
@@ -902,7 +975,7 @@ static void additive_smooth(Level &L, int nrhs, bool update_residual, cudaStream
                                               L.Omega_total, nrhs);
             CK_LAUNCH();
         }
-        tri_solve<T>(L.colagg.p, na, L.Optr.p, Lp, L.Loff.p, L.Di64.p, L.Doff.p, L.tri_cb, maxn, ws,
+        tri_solve<T>(L, L.ncol, L.colagg.p, L.Optr.p, Lp, L.Loff.p, L.Di64.p, L.Doff.p, L.tri_cb, ws,
                      L.Omega_total, nrhs, s);
         for (int64_t y0 = 0; y0 < na; y0 += 65535) {
             dim3 gg((unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv(maxn, 256), 64)),
@@ -926,7 +999,7 @@ void vcycle(Handle &H, int l, int nrhs, cudaStream_t s) {
         const T *Ld;
         if constexpr (std::is_same<T, float>::value) Ld = L.Ld32.p; else Ld = L.Ld64.p;
         KTime kt(KC_COARSE_SOLVE, s, 0.0, L.coarse_bytes[std::is_same<T, double>::value ? 1 : 0] * nrhs);
-        tri_solve<T>(nullptr, 1, L.cs_ptr.p, Ld, L.cs_off.p, L.Di64.p, L.Doff.p, L.tri_cb, (int)L.n, x, L.n, nrhs, s);
+        tri_solve<T>(L, 0, nullptr, L.cs_ptr.p, Ld, L.cs_off.p, L.Di64.p, L.Doff.p, L.tri_cb, x, L.n, nrhs, s);
         return;
     }
     Level &C = H.levels[l + 1];
@@ -968,10 +1041,7 @@ void vcycle(Handle &H, int l, int nrhs, cudaStream_t s) {
         KTime kt(KC_SPMV, s, 0.0, L.spmv_bytes[std::is_same<T, double>::value ? 1 : 0]);
         const T *G;
         if constexpr (std::is_same<T, float>::value) G = L.G32.p; else G = L.G64.p;
-        size_t sm = (size_t)std::max(1, L.max_grows_cached) * sizeof(T);
-        k_spmv<T><<<gridv(L.ne, 1, 148 * 24), 128, sm, s>>>(L.eptr.p, L.eidx.p, L.ne, G, L.goff.p,
-                                                          L.grows.p, x, r, L.n, nrhs, (T)-1);
-        CK_LAUNCH();
+        launch_spmv<T>(L, G, x, r, nrhs, (T)-1, s);
     }
     {
         LSAMG_PROF(l == 0 ? "vc: L0 post-smooth" : "vc: Lc post-smooth", s);

@@ -448,141 +448,100 @@ __device__ __forceinline__ double urand(uint32_t a, uint32_t b) {
     return (double)x * (2.0 / 4294967296.0) - 1.0;
 }
 
-constexpr int STEIN_SLOTS = 64;  // eigenvalues iterated concurrently per matrix (one per thread)
-
-__global__ void __launch_bounds__(256) k_stein(const double *dd, const double *ee,
-                                               const int64_t *toff, const int32_t *nn,
-                                               int64_t count, const double *wv, const int32_t *kk,
-                                               double *baseV, const int64_t *voff,
-                                               const int32_t *vld, double *work,
-                                               const int64_t *workoff, int cluster_orth) {
-    int64_t b = blockIdx.x;
-    if (b >= count) return;
+// Inverse iteration, one thread per wanted eigenvalue over the whole batch (thread t -> matrix b,
+// index j through the prefix `pre` of the counts k).  Three steps of (T - lambda I) x <- x with
+// partially pivoted tridiagonal LU from a seeded random start; numerically equal eigenvalues are
+// separated by multiples of 10 eps ||T||.  The retained vectors are orthonormalised together
+// afterwards (CholeskyQR2): the span matters, not the individual vectors.  Work arrays of matrix b
+// at work[woff[b] + (a n + i) k + j] (a = 0..2: the LU factors), coalesced over j.
+__global__ void __launch_bounds__(128) k_stein(const double *dd, const double *ee, const int64_t *toff,
+                                               const int32_t *nn, int64_t count, const double *wv,
+                                               const int32_t *kk, const int64_t *pre, const double *tnorm,
+                                               double *baseV, const int64_t *voff, const int32_t *vld,
+                                               double *work, const int64_t *woff) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= pre[count]) return;
+    int64_t lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (pre[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    const int64_t b = lo;
+    const int j = (int)(t - pre[b]);
     const int n = nn[b], k = kk[b];
-    if (k <= 0 || n <= 0) return;
     const double *d = dd + toff[b], *e = ee + toff[b], *w = wv + toff[b];
-    double *V = baseV + voff[b];
-    const int LV = vld[b];
-    double *W = work + workoff[b];  // 4 n STEIN_SLOTS doubles, element i of slot s at [i*S + s]
-    constexpr int S = STEIN_SLOTS;
-    __shared__ double red[32];
-    __shared__ double tnorm;
-    __shared__ double hsh[1024];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    {
-        double t = 0.0;
-        for (int i = threadIdx.x; i < n; i += blockDim.x)
-            t = fmax(t, fabs(d[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < n - 1 ? fabs(e[i]) : 0.0));
-        for (int o = 16; o; o >>= 1) t = fmax(t, __shfl_xor_sync(0xffffffffu, t, o));
-        if (lane == 0) red[warp] = t;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double r = 0.0;
-            for (int q = 0; q < nwarp; q++) r = fmax(r, red[q]);
-            tnorm = fmax(r, 1e-300);
-        }
-        __syncthreads();
-    }
-    // eigenvectors of eigenvalues closer than ortol are re-orthogonalised; farther apart, exact-shift
-    // inverse iteration already gives orthogonality ~eps*||T||/gap <= 1e-10
-    const double ortol = 1e-6 * tnorm, pertol = 10.0 * DEPS * tnorm;
-    // ---- phase 1: independent inverse iteration, one eigenvalue per thread at a time
-    if (threadIdx.x < S) {
-        const int sl = threadIdx.x;
-        double *dg = W, *su = W + (int64_t)n * S, *su2 = W + 2 * (int64_t)n * S,
-               *x = W + 3 * (int64_t)n * S;
-        for (int j = sl; j < k; j += S) {
-            // separate numerically equal eigenvalues by multiples of pertol
-            int q = j;
-            while (q > 0 && w[q] - w[q - 1] < pertol) q--;
-            const double lam = w[j] + (double)(j - q) * pertol;
-            for (int i = 0; i < n; i++) x[(int64_t)i * S + sl] = urand((uint32_t)j, (uint32_t)i);
-            for (int it = 0; it < 3; it++) {
-                double mx = 0.0;
-                for (int i = 0; i < n; i++) mx = fmax(mx, fabs(x[(int64_t)i * S + sl]));
-                const double sc = (mx > 0.0) ? 1.0 / mx : 1.0;
-                // factor T - lam I with partial pivoting while eliminating the right-hand side
-                double diag = d[0] - lam, sup = (n > 1) ? e[0] : 0.0, rhs = x[sl] * sc;
-                for (int i = 0; i < n - 1; i++) {
-                    const double sub = e[i], nd = d[i + 1] - lam, ns = (i + 1 < n - 1) ? e[i + 1] : 0.0;
-                    const double nrhs = x[(int64_t)(i + 1) * S + sl] * sc;
-                    const int64_t ii = (int64_t)i * S + sl;
-                    if (fabs(diag) >= fabs(sub)) {
-                        if (diag == 0.0) diag = pertol;
-                        const double m = sub / diag;
-                        dg[ii] = diag;
-                        su[ii] = sup;
-                        su2[ii] = 0.0;
-                        x[ii] = rhs;
-                        diag = nd - m * sup;
-                        sup = ns;
-                        rhs = nrhs - m * rhs;
-                    } else {
-                        const double m = diag / sub;
-                        dg[ii] = sub;
-                        su[ii] = nd;
-                        su2[ii] = ns;
-                        x[ii] = nrhs;
-                        diag = sup - m * nd;
-                        sup = -m * ns;
-                        rhs = rhs - m * nrhs;
-                    }
-                }
+    const double pertol = 10.0 * DEPS * tnorm[b];
+    double *dg = work + woff[b], *su = dg + (int64_t)n * k, *su2 = su + (int64_t)n * k;
+    double *x = baseV + voff[b] + (int64_t)j * vld[b];     // the vector itself is the work vector
+    int q = j;
+    while (q > 0 && w[q] - w[q - 1] < pertol) q--;
+    const double lam = w[j] + (double)(j - q) * pertol;
+    for (int i = 0; i < n; i++) x[i] = urand((uint32_t)j, (uint32_t)i);
+    for (int it = 0; it < 3; it++) {
+        double mx = 0.0;
+        for (int i = 0; i < n; i++) mx = fmax(mx, fabs(x[i]));
+        const double sc = (mx > 0.0) ? 1.0 / mx : 1.0;
+        double diag = d[0] - lam, sup = (n > 1) ? e[0] : 0.0, rhs = x[0] * sc;
+        for (int i = 0; i < n - 1; i++) {
+            const double sub = e[i], nd = d[i + 1] - lam, ns = (i + 1 < n - 1) ? e[i + 1] : 0.0;
+            const double nrhs = x[i + 1] * sc;
+            const int64_t ii = (int64_t)i * k + j;
+            if (fabs(diag) >= fabs(sub)) {
                 if (diag == 0.0) diag = pertol;
-                const int64_t il = (int64_t)(n - 1) * S + sl;
-                dg[il] = diag;
-                x[il] = rhs / diag;
-                for (int i = n - 2; i >= 0; i--) {
-                    const int64_t ii = (int64_t)i * S + sl;
-                    double v = x[ii] - su[ii] * x[ii + S];
-                    if (i + 2 < n) v -= su2[ii] * x[ii + 2 * S];
-                    x[ii] = v / dg[ii];
-                }
+                const double m = sub / diag;
+                dg[ii] = diag;
+                su[ii] = sup;
+                su2[ii] = 0.0;
+                x[i] = rhs;
+                diag = nd - m * sup;
+                sup = ns;
+                rhs = nrhs - m * rhs;
+            } else {
+                const double m = diag / sub;
+                dg[ii] = sub;
+                su[ii] = nd;
+                su2[ii] = ns;
+                x[i] = nrhs;
+                diag = sup - m * nd;
+                sup = -m * ns;
+                rhs = rhs - m * nrhs;
             }
-            double nr = 0.0;
-            for (int i = 0; i < n; i++) nr += x[(int64_t)i * S + sl] * x[(int64_t)i * S + sl];
-            const double inv = (nr > 0.0) ? 1.0 / sqrt(nr) : 0.0;
-            double *vj = V + (int64_t)j * LV;
-            for (int i = 0; i < n; i++) vj[i] = x[(int64_t)i * S + sl] * inv;
+        }
+        if (diag == 0.0) diag = pertol;
+        double x1 = rhs / diag, x2 = 0.0;           // x[i+1], x[i+2] of the back substitution
+        x[n - 1] = x1;
+        for (int i = n - 2; i >= 0; i--) {
+            const int64_t ii = (int64_t)i * k + j;
+            const double v = (x[i] - su[ii] * x1 - su2[ii] * x2) / dg[ii];
+            x[i] = v;
+            x2 = x1;
+            x1 = v;
         }
     }
+    double nr = 0.0;
+    for (int i = 0; i < n; i++) nr += x[i] * x[i];
+    const double inv = (nr > 0.0) ? 1.0 / sqrt(nr) : 0.0;
+    for (int i = 0; i < n; i++) x[i] *= inv;
+}
+
+// ||T||_inf per matrix (the scale of the eigenvalue separation)
+__global__ void __launch_bounds__(256) k_tnorm(const double *dd, const double *ee, const int64_t *toff,
+                                               const int32_t *nn, int64_t count, double *out) {
+    __shared__ double red[256];
+    const int64_t b = blockIdx.x;
+    if (b >= count) return;
+    const int n = nn[b];
+    const double *d = dd + toff[b], *e = ee + toff[b];
+    double t = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+        t = fmax(t, fabs(d[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < n - 1 ? fabs(e[i]) : 0.0));
+    red[threadIdx.x] = t;
     __syncthreads();
-    if (!cluster_orth) return;
-    // ---- phase 2: orthonormalise every cluster (gaps <= ortol) by classical Gram-Schmidt twice
-    int c0 = 0;
-    while (c0 < k) {
-        int c1 = c0 + 1;
-        while (c1 < k && w[c1] - w[c1 - 1] <= ortol) c1++;
-        for (int j = c0 + 1; j < c1; j++) {
-            double *vj = V + (int64_t)j * LV;
-            for (int pass = 0; pass < 2; pass++) {
-                for (int i0 = c0; i0 < j; i0 += 1024) {
-                    const int i1 = min(j, i0 + 1024);
-                    for (int i = i0 + warp; i < i1; i += nwarp) {
-                        const double *vi = V + (int64_t)i * LV;
-                        double sd = 0.0;
-                        for (int r = lane; r < n; r += 32) sd += vi[r] * vj[r];
-                        for (int o = 16; o; o >>= 1) sd += __shfl_xor_sync(0xffffffffu, sd, o);
-                        if (lane == 0) hsh[i - i0] = sd;
-                    }
-                    __syncthreads();
-                    for (int r = threadIdx.x; r < n; r += blockDim.x) {
-                        double acc = 0.0;
-                        for (int i = i0; i < i1; i++) acc += hsh[i - i0] * V[(int64_t)i * LV + r];
-                        vj[r] -= acc;
-                    }
-                    __syncthreads();
-                }
-            }
-            double nr = 0.0;
-            for (int r = threadIdx.x; r < n; r += blockDim.x) nr += vj[r] * vj[r];
-            nr = block_sum(nr, red);
-            const double inv = (nr > 0.0) ? 1.0 / sqrt(nr) : 0.0;
-            for (int r = threadIdx.x; r < n; r += blockDim.x) vj[r] *= inv;
-            __syncthreads();
-        }
-        c0 = c1;
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
+        __syncthreads();
     }
+    if (threadIdx.x == 0) out[b] = fmax(red[0], 1e-300);
 }
 
 // ------------------------------------------------------------------------- ormtr (blocked)
@@ -710,22 +669,32 @@ void lower_update(double *base, const MatBatch &A, const std::vector<int32_t> &n
 void potrf_batched(double *base, const MatBatch &A, PotrfMode mode, int *err, cudaStream_t s) {
     if (A.count == 0 || A.maxn == 0) return;
     constexpr int PB = 64;
-    double fl = 0.0;
-    for (auto v : A.h_n) fl += (double)v * v * v / 3.0;
-    KTime kt(KC_POTRF, s, fl);
     DBuf<double> md;
     md.alloc(A.count, s);
     k_maxdiag<<<(unsigned)A.count, 256, 0, s>>>(base, A.off.p, A.ld.p, A.n.p, A.count, md.p);
     CK_LAUNCH();
     oz::Workspace ws;
     for (int j0 = 0; j0 < A.maxn; j0 += PB) {
-        k_potf2<PB><<<(unsigned)A.count, 256, 0, s>>>(base, A.off.p, A.ld.p, A.n.p, A.count, j0, mode, md.p, err);
-        CK_LAUNCH();
         int rem = A.maxn - j0 - PB;
+        {
+            // the FP64 panel: diagonal block and the rows below it (the trailing update is a
+            // tensor-core product, timed as its own class)
+            double fl = 0.0;
+            for (auto v : A.h_n) {
+                const double bs = std::min(PB, v - j0), m = std::max(0, v - j0 - PB);
+                if (bs > 0) fl += bs * bs * bs / 3.0 + m * bs * bs;
+            }
+            KTime kt(KC_POTRF, s, fl);
+            k_potf2<PB><<<(unsigned)A.count, 256, 0, s>>>(base, A.off.p, A.ld.p, A.n.p, A.count, j0, mode, md.p,
+                                                         err);
+            CK_LAUNCH();
+            if (rem > 0) {
+                dim3 gp((unsigned)cdiv(rem, 128), (unsigned)A.count);
+                k_potrf_panel<PB><<<gp, 128, 0, s>>>(base, A.off.p, A.ld.p, A.n.p, A.count, j0);
+                CK_LAUNCH();
+            }
+        }
         if (rem <= 0) break;
-        dim3 gp((unsigned)cdiv(rem, 128), (unsigned)A.count);
-        k_potrf_panel<PB><<<gp, 128, 0, s>>>(base, A.off.p, A.ld.p, A.n.p, A.count, j0);
-        CK_LAUNCH();
         lower_update(base, A, A.h_n, nullptr, j0, PB, ws, nullptr, err, s);
     }
 }
@@ -768,7 +737,6 @@ void pstrf_batched(double *base, const MatBatch &A, const int32_t *b0, const int
                    int32_t max_bn, int32_t *perm, const int64_t *permoff, int32_t *rank,
                    int *err, cudaStream_t s) {
     if (A.count == 0 || max_bn == 0) return;
-    KTime kt(KC_PSTRF, s);
     DBuf<double> md, work;
     DBuf<int64_t> woff;
     md.alloc(A.count, s);
@@ -780,10 +748,13 @@ void pstrf_batched(double *base, const MatBatch &A, const int32_t *b0, const int
     CK_LAUNCH();
     oz::Workspace ws;
     for (int j0 = 0; j0 < max_bn; j0 += NB) {
-        k_pstf_panel<<<(unsigned)A.count, 256, 0, s>>>(base, A.off.p, A.ld.p, A.n.p, b0, bn,
-                                                      A.count, j0, perm, permoff, rank, work.p,
-                                                      permoff, md.p);
-        CK_LAUNCH();
+        {
+            KTime kt(KC_PSTRF, s);
+            k_pstf_panel<<<(unsigned)A.count, 256, 0, s>>>(base, A.off.p, A.ld.p, A.n.p, b0, bn,
+                                                          A.count, j0, perm, permoff, rank, work.p,
+                                                          permoff, md.p);
+            CK_LAUNCH();
+        }
         if (max_bn - j0 - NB <= 0) break;
         lower_update(base, A, h_bn, &h_b0, j0, NB, ws, rank, err, s);
     }
@@ -794,18 +765,24 @@ void pstrf_batched(double *base, const MatBatch &A, const int32_t *b0, const int
 void trsm_batched(const double *base_L, const MatBatch &Lb, double *base_B, const MatBatch &Bb,
                   bool trans, cudaStream_t s, int *err) {
     if (Bb.count == 0 || Bb.maxm == 0 || Lb.maxn == 0) return;
-    double fl = 0.0;
-    for (size_t i = 0; i < Bb.h_n.size(); i++) fl += (double)Bb.h_n[i] * Bb.h_n[i] * Bb.h_m[i];
-    KTime kt(KC_TRSM, s, fl);
     const int nblk = (int)cdiv(Bb.maxn, TB);
     dim3 g((unsigned)cdiv(Bb.maxm, SW), (unsigned)Bb.count);
     oz::Workspace ws;
     for (int step = 0; step < nblk; step++) {
         const int kb = trans ? nblk - 1 - step : step;
         const int r0 = kb * TB;
-        k_trsm_diag<<<g, 256, 0, s>>>(base_L, Lb.off.p, Lb.ld.p, Lb.n.p, base_B, Bb.off.p, Bb.ld.p, Bb.m.p,
-                                      Bb.count, r0, trans ? 1 : 0);
-        CK_LAUNCH();
+        {
+            // the FP64 diagonal-block solves (the rest of B is a tensor-core product)
+            double fl = 0.0;
+            for (size_t i = 0; i < Bb.h_n.size(); i++) {
+                const double bs = std::min(TB, Bb.h_n[i] - r0);
+                if (bs > 0) fl += bs * bs * Bb.h_m[i];
+            }
+            KTime kt(KC_TRSM, s, fl);
+            k_trsm_diag<<<g, 256, 0, s>>>(base_L, Lb.off.p, Lb.ld.p, Lb.n.p, base_B, Bb.off.p, Bb.ld.p, Bb.m.p,
+                                          Bb.count, r0, trans ? 1 : 0);
+            CK_LAUNCH();
+        }
         // the rest of B: below the block (L21 X_r) or above it (L_r,0:r0^T X_r)
         std::vector<oz::SplitJob> sj;
         std::vector<oz::GemmJob> gj;
@@ -848,9 +825,6 @@ void trsm_batched(const double *base_L, const MatBatch &Lb, double *base_B, cons
 void syrk_tn_batched(double *base_C, const MatBatch &Cb, const double *base_W, const MatBatch &Wb,
                      double alpha, bool w_rowmajor, cudaStream_t s, int *err) {
     if (Cb.count == 0 || Cb.maxn == 0) return;
-    double fl = 0.0;
-    for (size_t i = 0; i < Cb.h_n.size(); i++) fl += 2.0 * Cb.h_n[i] * Cb.h_n[i] * Wb.h_n[i];
-    KTime kt(KC_SYRK, s, fl);
     // C (n x n, full) += alpha W^T W, W: K x n; the split operand is W^T (n rows of length K),
     // in pieces of at most 16,352 along K
     constexpr int KMAX = oz::MAX_CHUNKS * oz::TK;
@@ -1014,21 +988,32 @@ void cholqr2_batched(double *base_V, const MatBatch &Vb, int *err, cudaStream_t 
 }
 
 void stein_batched(const double *d, const double *e, const int64_t *toff, const int32_t *n,
-                   const double *w, const int32_t *k, double *base_V, const MatBatch &Vb,
-                   double *work, const int64_t *workoff, cudaStream_t s, bool cluster_orth) {
+                   const double *w, const int32_t *k, double *base_V, const MatBatch &Vb, cudaStream_t s) {
     if (Vb.count == 0) return;
     KTime kt(KC_STEIN, s);
-    k_stein<<<(unsigned)Vb.count, 256, 0, s>>>(d, e, toff, n, Vb.count, w, k, base_V, Vb.off.p,
-                                              Vb.ld.p, work, workoff, cluster_orth ? 1 : 0);
+    const int64_t cnt = Vb.count;
+    std::vector<int64_t> pre(cnt + 1, 0), woff(cnt + 1, 0);
+    for (int64_t b = 0; b < cnt; b++) {
+        pre[b + 1] = pre[b] + Vb.h_m[b];
+        woff[b + 1] = woff[b] + 3 * (int64_t)Vb.h_n[b] * Vb.h_m[b];
+    }
+    if (pre[cnt] == 0) return;
+    DBuf<int64_t> dpre, dwo;
+    DBuf<double> work, tn;
+    upload(dpre, pre, s);
+    upload(dwo, std::vector<int64_t>(woff.begin(), woff.end() - 1), s);
+    work.alloc(std::max<int64_t>(woff[cnt], 1), s);
+    tn.alloc(cnt, s);
+    k_tnorm<<<(unsigned)cnt, 256, 0, s>>>(d, e, toff, n, cnt, tn.p);
+    CK_LAUNCH();
+    k_stein<<<(unsigned)cdiv(pre[cnt], 128), 128, 0, s>>>(d, e, toff, n, cnt, w, k, dpre.p, tn.p, base_V, Vb.off.p,
+                                                          Vb.ld.p, work.p, dwo.p);
     CK_LAUNCH();
 }
 
 void ormtr_batched(const double *base_A, const MatBatch &Ab, const double *tau, const int64_t *toff,
                    double *base_V, const MatBatch &Vb, cudaStream_t s, int *err) {
     if (Vb.count == 0 || Vb.maxm == 0) return;
-    double fl = 0.0;
-    for (size_t i = 0; i < Vb.h_n.size(); i++) fl += 2.0 * Vb.h_n[i] * Vb.h_n[i] * Vb.h_m[i];
-    KTime kt(KC_ORMTR, s, fl);
     // V = Q V, Q = H_0 ... H_{n-2} in blocks of QB reflectors, last block first; each block is
     // I - Y T Y^T (compact WY), applied as V -= Y (T (Y^T V)) with the two large products on the
     // tensor cores
@@ -1052,8 +1037,11 @@ void ormtr_batched(const double *base_A, const MatBatch &Ab, const double *tau, 
         const int j0 = p * QB;
         dim3 gy((unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv((int64_t)Vb.maxn * QB, 256), 64)),
                 (unsigned)cnt);
-        k_ormtr_y<<<gy, 256, 0, s>>>(base_A, Ab.off.p, Ab.ld.p, Ab.n.p, cnt, j0, Y.p, dyo.p);
-        CK_LAUNCH();
+        {
+            KTime kt(KC_ORMTR, s);
+            k_ormtr_y<<<gy, 256, 0, s>>>(base_A, Ab.off.p, Ab.ld.p, Ab.n.p, cnt, j0, Y.p, dyo.p);
+            CK_LAUNCH();
+        }
         // operands: Y^T (QB rows of length R), V^T (k rows of length R), Y (R rows of length QB)
         std::vector<oz::SplitJob> sy, sv;
         std::vector<oz::GemmJob> gg, gz, gv;
@@ -1079,11 +1067,14 @@ void ormtr_batched(const double *base_A, const MatBatch &Ab, const double *tau, 
         oz::split(base_V, sv, ws.sl.p, ws.ex.p, s);
         oz::gemm(ws.sl.p, ws.ex.p, G.p, gg, 1.0, 0.0, err, s);
         oz::gemm(ws.sl.p, ws.ex.p, Z.p, gz, 1.0, 0.0, err, s);
-        k_ormtr_t<<<(unsigned)cnt, QB, 0, s>>>(Vb.n.p, cnt, j0, tau, toff, G.p, T.p);
-        CK_LAUNCH();
-        dim3 gt((unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv(Vb.maxm, 4), 32)), (unsigned)cnt);
-        k_ormtr_tz<<<gt, 256, 0, s>>>(Vb.n.p, Vb.m.p, cnt, j0, T.p, Z.p, dzo.p);
-        CK_LAUNCH();
+        {
+            KTime kt(KC_ORMTR, s);
+            k_ormtr_t<<<(unsigned)cnt, QB, 0, s>>>(Vb.n.p, cnt, j0, tau, toff, G.p, T.p);
+            CK_LAUNCH();
+            dim3 gt((unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv(Vb.maxm, 4), 32)), (unsigned)cnt);
+            k_ormtr_tz<<<gt, 256, 0, s>>>(Vb.n.p, Vb.m.p, cnt, j0, T.p, Z.p, dzo.p);
+            CK_LAUNCH();
+        }
         // V(j0+1:, :) -= Y Z
         std::vector<oz::SplitJob> s1, s2;
         h = 0;

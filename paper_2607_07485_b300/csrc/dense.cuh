@@ -83,11 +83,10 @@ void stebz_batched(const double *d, const double *e, const int64_t *toff, const 
                    int64_t count, double sigma, int32_t *k, double *w, double *gap,
                    cudaStream_t s);
 
-// Eigenvectors of the tridiagonals for w[toff[i]..+k[i]) by inverse iteration with
-// re-orthogonalisation inside clusters; V views (n rows, k columns).
+// Eigenvectors of the tridiagonals for w[toff[i]..+k[i]) by inverse iteration (one thread per
+// eigenvalue over the batch), into V views (n rows, k columns); not orthogonalised.
 void stein_batched(const double *d, const double *e, const int64_t *toff, const int32_t *n,
-                   const double *w, const int32_t *k, double *base_V, const MatBatch &Vb,
-                   double *work, const int64_t *workoff, cudaStream_t s, bool cluster_orth = true);
+                   const double *w, const int32_t *k, double *base_V, const MatBatch &Vb, cudaStream_t s);
 
 // Rectangular transpose: D (m x n, column-major, ld_d) = S^T with S n x m (column-major, ld_s);
 // S views: n = rows, m = columns; D views: ld only.

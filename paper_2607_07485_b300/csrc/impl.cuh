@@ -88,6 +88,18 @@ struct Level {
     DBuf<int32_t> pair_agg;             // (subdomain, element meeting Omega) pairs by colour
     DBuf<int64_t> pair_ent;             // ... the entry index into oeidx / oelocoff
     double coarse_bytes[2] = {0, 0};
+    // wavefront triangular solves: per solve group (the colours, then all subdomains; the
+    // coarsest level has one group) the forward and backward task lists (system index within the
+    // group's system list, block) at wf_tasks[fwd], [bwd]; per-system flag offsets; the flags
+    // (forward, backward) and, after them, an error record (code, item)
+    struct WaveGroup {
+        int64_t fwd = 0, bwd = 0, ntask = 0;
+    };
+    std::vector<WaveGroup> wf_groups;
+    DBuf<int32_t> wf_tasks;
+    DBuf<int64_t> wf_foff;
+    DBuf<uint32_t> wf_flags;
+    int64_t wf_nflags = 0;
     DBuf<double> b64, x64, r64, ws64;
     DBuf<float> b32, x32, r32, ws32;
 };
@@ -148,6 +160,13 @@ void set_last_error(const std::string &msg);
 // invert the diagonal blocks (tri_cb rows) of nsys packed factors; h_n: host orders of the systems
 void tri_inverse_setup(int64_t nsys, const int64_t *Optr, const std::vector<int32_t> &h_n, const double *L64,
                        const int64_t *Loff, int cb, DBuf<int64_t> &Doff, DBuf<double> &D64, cudaStream_t s);
+// task lists of the wavefront triangular solves: groups[g] lists its systems' orders (in the
+// order of the group's system array); nsys_total systems on the level, sysid[g][i] their ids
+void wave_setup(Level &L, const std::vector<std::vector<int32_t>> &group_sizes,
+                const std::vector<std::vector<int32_t>> &group_ids, const std::vector<int32_t> &all_sizes, int cb,
+                cudaStream_t s);
+// device error record of the wavefront solves of a level (LSAMG_DEVICE_TIMEOUT if a wait gave up)
+void wave_check(const Level &L, cudaStream_t s);
 
 // ------------------------------------------------------------------- cycle.cu
 void ensure_cycle_ws(Level &L, int nrhs, cudaStream_t s);

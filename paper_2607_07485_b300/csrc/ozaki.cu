@@ -60,22 +60,53 @@ __global__ void __launch_bounds__(256) k_split(const double *src, const SplitJob
         }
         __syncthreads();
     }
+    // slices in integer arithmetic (the FP64 pipe is scarce): F = round(v 2^(55 - e_r)) exactly
+    // from the bits of v (|F| < 2^55), then balanced base-256 digits a_p = round(F / 2^(48-8(p-1)))
+    // with F -= a_p 2^(48-8(p-1)); the seven digits hold F exactly.  Two consecutive k per thread.
+    const int64_t pstride = (int64_t)tiles * nch * BLK;
     for (int c = 0; c < nch; c++) {
-        for (int idx = threadIdx.x; idx < BLK; idx += blockDim.x) {
+        for (int idx = threadIdx.x; idx < BLK / 2; idx += blockDim.x) {
             int r, kk;
-            if (kfast) { r = idx >> 5; kk = idx & 31; } else { r = idx & 63; kk = idx >> 6; }
-            const int i = i0 + r, k = c * TK + kk;
-            double v = 0.0;
-            if (i < J.rows && k < J.K) v = S[(int64_t)i * J.rs + (int64_t)k * J.ks];
-            double x = ldexp(v, 7 - rexp[r]);            // |x| < 128
+            if (kfast) { r = idx >> 4; kk = (idx & 15) * 2; } else { r = idx & 63; kk = (idx >> 6) * 2; }
+            const int i = i0 + r;
+            int dig[2][NS];
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int k = c * TK + kk + h;
+                double v = 0.0;
+                if (i < J.rows && k < J.K) v = S[(int64_t)i * J.rs + (int64_t)k * J.ks];
+                const uint64_t bits = (uint64_t)__double_as_longlong(v);
+                int ef = (int)((bits >> 52) & 0x7ff);
+                uint64_t mant = bits & ((1ull << 52) - 1);
+                if (ef) mant |= 1ull << 52; else ef = 1;
+                const int sh = ef - 1075 + 55 - rexp[r];      // v 2^(55 - e_r) = mant 2^sh
+                int64_t F = 0;
+                if (mant != 0 && sh > -64) {
+                    if (sh >= 0) {
+                        F = (int64_t)(mant << sh);
+                    } else {
+                        const int rs = -sh;
+                        const uint64_t q = mant >> rs, rem = mant & ((1ull << rs) - 1), half = 1ull << (rs - 1);
+                        F = (int64_t)(q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull));
+                    }
+                    if (bits >> 63) F = -F;
+                }
+#pragma unroll
+                for (int p = 0; p < NS; p++) {
+                    const int s2 = 48 - 8 * p;
+                    const int64_t a = (s2 > 0) ? ((F + (1ll << (s2 - 1))) >> s2) : F;
+                    F -= a << s2;
+                    dig[h][p] = (int)a;
+                }
+            }
             const int o = swz(r, kk);
-            __half *d = dst + J.dst_off + ((int64_t)t * nch + c) * BLK + o;
-            const int64_t pstride = (int64_t)tiles * nch * BLK;
+            __half2 *d = reinterpret_cast<__half2 *>(dst + J.dst_off + ((int64_t)t * nch + c) * BLK + o);
 #pragma unroll
             for (int p = 0; p < NS; p++) {
-                const double a = rint(x);                // |a| <= 128, exact in FP16
-                d[p * pstride] = __double2half(a);
-                x = (x - a) * 256.0;                     // exact
+                // |digit| <= 128: exact in FP32 through 1.5 * 2^23 and in FP16
+                const float f0 = __int_as_float(0x4B400000 + dig[0][p]) - 12582912.0f;
+                const float f1 = __int_as_float(0x4B400000 + dig[1][p]) - 12582912.0f;
+                d[p * pstride / 2] = __floats2half2_rn(f0, f1);
             }
         }
     }
@@ -171,6 +202,28 @@ __device__ __forceinline__ double i128_to_double(__int128 v, int e, bool neg) {
     return __longlong_as_double((long long)bits);
 }
 
+// c + v 2^e for a 128-bit integer v (|v| < 2^100) rounded once: c's significand joins the integer
+// sum at the common unit when both fit in 127 bits (otherwise one operand is below the other's
+// rounding and an FP64 add of the rounded v is exact to the last bit's rounding)
+__device__ __forceinline__ double i128_add_double(__int128 v, int e, double c) {
+    const uint64_t cb = (uint64_t)__double_as_longlong(c);
+    int ec = (int)((cb >> 52) & 0x7ff);
+    if (ec == 0x7ff) return c + i128_to_double(v, e, false);          // inf / nan propagate
+    int64_t mc = (int64_t)(cb & ((1ull << 52) - 1));
+    if (ec) mc |= 1ll << 52; else ec = 1;
+    if (mc == 0) return i128_to_double(v, e, false);
+    if (v == 0) return c;
+    if (cb >> 63) mc = -mc;
+    const int E = ec - 1075;                                           // c = mc 2^E
+    const unsigned __int128 av = (unsigned __int128)(v < 0 ? -v : v);
+    const uint64_t vh = (uint64_t)(av >> 64), vl = (uint64_t)av;
+    const int vb = vh ? 128 - __clzll((long long)vh) : 64 - __clzll((long long)vl);   // bits of |v|
+    const int d = E - e;
+    if (d >= 0 && d <= 126 - 53) return i128_to_double(v + ((__int128)mc << d), e, false);
+    if (d < 0 && vb - d <= 126) return i128_to_double((v << (-d)) + (__int128)mc, E, false);
+    return c + i128_to_double(v, e, false);
+}
+
 __global__ void __launch_bounds__(256, 1) k_gemm(const __half *sl, const int32_t *ex, double *C,
                                                  const GemmJob *jobs, const int64_t *pre, int njobs, double alpha,
                                                  double beta, int *err, const int32_t *skip) {
@@ -210,10 +263,10 @@ __global__ void __launch_bounds__(256, 1) k_gemm(const __half *sl, const int32_t
         for (int c = 0; c < NST && c < nch; c++) issue(c);
 
     const int wm = warp >> 2, wn = warp & 3;     // warp tile: rows wm*32.., cols wn*16..
-    // exact int32 sums for the diagonals 2 .. NI + 1; the lowest-weight diagonal (2^-48 of the
-    // leading one) goes to an FP32 sum, whose rounding stays below 2^-70 of the leading unit
-    constexpr int NI = ND - 2;
-    int32_t iacc[NI][2][2][4];
+    // exact integer sums of the diagonals: hi = S_2 2^16 + S_3 2^8 + S_4 and lo = S_5 2^16 +
+    // S_6 2^8 + S_7 (int64; each S_d stays below 2^31 for K <= 16352); the lowest-weight diagonal
+    // (2^-48 of the leading one) goes to an FP32 sum, whose rounding stays below 2^-70 of it
+    int64_t hi[2][2][4], lo[2][2][4];
     float tail[2][2][4];
 #pragma unroll
     for (int a = 0; a < 2; a++)
@@ -222,8 +275,8 @@ __global__ void __launch_bounds__(256, 1) k_gemm(const __half *sl, const int32_t
 #pragma unroll
             for (int q = 0; q < 4; q++) {
                 tail[a][b][q] = 0.f;
-#pragma unroll
-                for (int d = 0; d < NI; d++) iacc[d][a][b][q] = 0;
+                hi[a][b][q] = 0;
+                lo[a][b][q] = 0;
             }
     // ldmatrix row / 16-byte chunk of this lane: A tiles (16 rows x 16 k), B pair of n8 tiles
     const int arow = lane & 15, akc = lane >> 4;
@@ -246,55 +299,65 @@ __global__ void __launch_bounds__(256, 1) k_gemm(const __half *sl, const int32_t
         mbar_wait_bounded(&full[st], parity, 1000000000ull);   // completed: returns at once
         const uint32_t sA = smem_u32(smem + st * STAGE_BYTES);
         const uint32_t sB = sA + NS * BLK * 2;
+        // per 16-wide K step: every slice's fragments once into registers, then the 28 slice
+        // products diagonal by diagonal, each diagonal's FP32 sum moved out exactly after the step
 #pragma unroll
-        for (int d = 2; d <= ND; d++) {
-            float acc[2][2][4];
+        for (int ks = 0; ks < 2; ks++) {
+            uint32_t af[NS][2][4], bf[NS][4];
 #pragma unroll
-            for (int a = 0; a < 2; a++)
+            for (int p = 0; p < NS; p++) {
 #pragma unroll
-                for (int b = 0; b < 2; b++)
+                for (int mt = 0; mt < 2; mt++) {
+                    const int r = wm * 32 + mt * 16 + arow, kc = ks * 2 + akc;
+                    ldsm_x4(af[p][mt], sA + p * BLK * 2 + r * 64 + ((((kc ^ (r >> 1)) & 3)) << 4));
+                }
+                const int r = wn * 16 + brow, kc = ks * 2 + bkc;
+                ldsm_x4(bf[p], sB + p * BLK * 2 + r * 64 + ((((kc ^ (r >> 1)) & 3)) << 4));
+            }
 #pragma unroll
-                    for (int q = 0; q < 4; q++) acc[a][b][q] = 0.f;
-            const int p0 = d - NS > 1 ? d - NS : 1, p1 = d - 1 < NS ? d - 1 : NS;
-#pragma unroll 1
-            for (int p = p0; p <= p1; p++) {
-                const int q = d - p;
+            for (int d = 2; d <= ND; d++) {
+                float acc[2][2][4];
 #pragma unroll
-                for (int ks = 0; ks < 2; ks++) {
-                    uint32_t af[2][4], bf[4];
+                for (int a = 0; a < 2; a++)
 #pragma unroll
-                    for (int mt = 0; mt < 2; mt++) {
-                        const int r = wm * 32 + mt * 16 + arow, kc = ks * 2 + akc;
-                        ldsm_x4(af[mt], sA + (p - 1) * BLK * 2 + r * 64 + ((((kc ^ (r >> 1)) & 3)) << 4));
-                    }
-                    {
-                        const int r = wn * 16 + brow, kc = ks * 2 + bkc;
-                        ldsm_x4(bf, sB + (q - 1) * BLK * 2 + r * 64 + ((((kc ^ (r >> 1)) & 3)) << 4));
-                    }
+                    for (int b = 0; b < 2; b++)
+#pragma unroll
+                        for (int q = 0; q < 4; q++) acc[a][b][q] = 0.f;
+#pragma unroll
+                for (int p = 1; p <= NS; p++) {
+                    const int q = d - p;
+                    if (q < 1 || q > NS) continue;
 #pragma unroll
                     for (int mt = 0; mt < 2; mt++)
 #pragma unroll
-                        for (int nt = 0; nt < 2; nt++) mma16816(acc[mt][nt], af[mt], bf[2 * nt], bf[2 * nt + 1]);
+                        for (int nt = 0; nt < 2; nt++)
+                            mma16816(acc[mt][nt], af[p - 1][mt], bf[q - 1][2 * nt], bf[q - 1][2 * nt + 1]);
                 }
+                // exact FP32 -> int32 (the sums are integers below 2^22 in magnitude), or the tail
+#pragma unroll
+                for (int a = 0; a < 2; a++)
+#pragma unroll
+                    for (int b = 0; b < 2; b++)
+#pragma unroll
+                        for (int q = 0; q < 4; q++) {
+                            if (d == ND) {
+                                tail[a][b][q] += acc[a][b][q];
+                            } else {
+                                const int64_t v = (int64_t)(__float_as_int(acc[a][b][q] + 12582912.0f) - 0x4B400000);
+                                const int sh = 8 * ((4 - d + 3 * 8) % 3);   // d = 2,5 -> 16; 3,6 -> 8; 4,7 -> 0
+                                if (d <= 4) hi[a][b][q] += v << sh;
+                                else lo[a][b][q] += v << sh;
+                            }
+                        }
             }
-            // exact FP32 -> int32 (the sums are integers below 2^22 in magnitude), or the tail
-#pragma unroll
-            for (int a = 0; a < 2; a++)
-#pragma unroll
-                for (int b = 0; b < 2; b++)
-#pragma unroll
-                    for (int q = 0; q < 4; q++) {
-                        if (d - 2 < NI)
-                            iacc[d - 2][a][b][q] += __float_as_int(acc[a][b][q] + 12582912.0f) - 0x4B400000;
-                        else
-                            tail[a][b][q] += acc[a][b][q];
-                    }
         }
         __syncthreads();   // every warp is done with this stage
         if (tid == 0 && c + NST < nch) issue(c + NST);
     }
     // epilogue: C = beta C + alpha 2^(ea + eb - 14) sum_d 2^-8(d-2) S_d, the sum formed exactly as
-    // a 128-bit integer in units of 2^-48 (FP64 instructions are scarce: one add per output)
+    // a 128-bit integer in units of 2^-48; with beta = 1 the old C joins the integer sum exactly
+    // and the result is rounded once.  FP64 instructions are scarce on this GPU: none in the common
+    // cases (alpha a power of two, beta 0 or 1)
     const int g = lane >> 2, tg = lane & 3;
     int ash = 0;
     bool aneg = alpha < 0.0, apow2 = false;
@@ -303,6 +366,7 @@ __global__ void __launch_bounds__(256, 1) k_gemm(const __half *sl, const int32_t
         const double fr = frexp(fabs(alpha), &e2);
         if (fr == 0.5) { apow2 = true; ash = e2 - 1; }
     }
+    const int bmode = (beta == 0.0) ? 0 : (beta == 1.0) ? 1 : 2;
 #pragma unroll
     for (int mt = 0; mt < 2; mt++)
 #pragma unroll
@@ -312,19 +376,24 @@ __global__ void __launch_bounds__(256, 1) k_gemm(const __half *sl, const int32_t
                 const int i = tm * TM + wm * 32 + mt * 16 + g + ((q >> 1) << 3);
                 const int jj = tn * TM + wn * 16 + nt * 8 + 2 * tg + (q & 1);
                 if (i >= J.M || jj >= J.N || (J.lower && i < jj)) continue;
-                const int64_t hi = ((int64_t)iacc[0][mt][nt][q] << 16) + ((int64_t)iacc[1][mt][nt][q] << 8) +
-                                   (int64_t)iacc[2][mt][nt][q];
-                const int64_t lo = ((int64_t)iacc[3][mt][nt][q] << 16) + ((int64_t)iacc[4][mt][nt][q] << 8) +
-                                   (int64_t)iacc[5][mt][nt][q];
-                const __int128 v = ((__int128)hi << 32) + ((__int128)lo << 8) + (__int128)__float2ll_rn(tail[mt][nt][q]);
-                const int e = ex[J.a_exp + i] + ex[J.b_exp + jj] - 62;
-                double val;
-                if (apow2) val = i128_to_double(v, e + ash, aneg);
-                else val = alpha * i128_to_double(v, e, false);
+                __int128 v = ((__int128)hi[mt][nt][q] << 32) + ((__int128)lo[mt][nt][q] << 8) +
+                             (__int128)__float2int_rn(tail[mt][nt][q]);
+                int e = ex[J.a_exp + i] + ex[J.b_exp + jj] - 62;
                 double *cp = C + J.c_off + (int64_t)i * J.crs + (int64_t)jj * J.ccs;
-                if (beta == 0.0) *cp = val;
-                else if (beta == 1.0) *cp = *cp + val;
-                else *cp = fma(beta, *cp, val);
+                if (!apow2) {
+                    const double val = alpha * i128_to_double(v, e, false);
+                    *cp = (bmode == 0) ? val : (bmode == 1) ? *cp + val : fma(beta, *cp, val);
+                    continue;
+                }
+                if (aneg) v = -v;
+                e += ash;
+                if (bmode == 0) {
+                    *cp = i128_to_double(v, e, false);
+                } else if (bmode == 1) {
+                    *cp = i128_add_double(v, e, *cp);
+                } else {
+                    *cp = fma(beta, *cp, i128_to_double(v, e, false));
+                }
             }
 }
 
@@ -362,6 +431,9 @@ void split(const double *src, const std::vector<SplitJob> &jobs, __half *dst, in
     const int64_t total = upload_jobs(jobs, cnt, buf, dj, dp, s);
     if (total == 0) return;
     if (total > 0x7fffffff) fail(LSAMG_LIMIT, "split grid too large");
+    double by = 0.0;   // FP64 operand read once, NS FP16 slices written
+    for (const auto &J : jobs) by += (double)J.rows * J.K * (8.0 + 2.0 * NS);
+    KTime kt(KC_TC_SPLIT, s, 0.0, by);
     k_split<<<(unsigned)total, 256, 0, s>>>(src, dj, dp, (int)jobs.size(), dst, exps);
     CK_LAUNCH();
 }
@@ -386,6 +458,9 @@ void gemm(const __half *slices, const int32_t *exps, double *C, const std::vecto
     if (total == 0) return;
     if (total > 0x7fffffff) fail(LSAMG_LIMIT, "product grid too large");
     CK(cudaFuncSetAttribute(k_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM));
+    double fl = 0.0;   // FP64-equivalent flops of the products (lower: the triangle only)
+    for (const auto &J : jobs) fl += (J.lower ? 1.0 : 2.0) * J.M * (double)J.N * J.K;
+    KTime kt(KC_TC_GEMM, s, fl);
     k_gemm<<<(unsigned)total, 256, GEMM_SMEM, s>>>(slices, exps, C, dj, dp, (int)jobs.size(), alpha, beta, err,
                                                    skip);
     CK_LAUNCH();

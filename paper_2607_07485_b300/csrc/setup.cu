@@ -608,7 +608,7 @@ void local_spectral(Level &L, const lsamg_options &o, int *err, cudaStream_t s, 
     // keep mu * tau_cut < 1 - 1e-9 (lambda > tau_cut and the ker S modes); the relative margin
     // discards exact ties mu = 1/tau_cut deterministically
     const double sigma = (1.0 - 1e-9) / L.tau;
-    int64_t budget = o.chunk_bytes > 0 ? o.chunk_bytes : (int64_t)16 << 30;
+    int64_t budget = o.chunk_bytes > 0 ? o.chunk_bytes : (int64_t)48 << 30;
     L.h_k.assign(nagg, 0);
     L.h_gap.assign(nagg, 0.0);
     struct Chunk {
@@ -762,13 +762,12 @@ void local_spectral(Level &L, const lsamg_options &o, int *err, cudaStream_t s, 
         auto hk = to_host(dk.p, na, s);
         auto hg = to_host(gp.p, na, s);
         check_err(err, s, "local spectral problems (factorisations)");
-        std::vector<int64_t> voff(na + 1), wkoff(na + 1);
-        voff[0] = wkoff[0] = 0;
+        std::vector<int64_t> voff(na + 1);
+        voff[0] = 0;
         for (int64_t i = 0; i < na; i++) {
             L.h_k[ids[i]] = hk[i];
             L.h_gap[ids[i]] = hg[i];
             voff[i + 1] = voff[i] + (int64_t)nwv[i] * hk[i];
-            wkoff[i + 1] = wkoff[i] + 4 * 64 * (int64_t)nwv[i];  // inverse-iteration scratch
             *flops += 4.0 * nwv[i] * (double)nwv[i] * hk[i] + (double)nwv[i] * nwv[i] * hk[i];
         }
         Chunk ch;
@@ -776,10 +775,6 @@ void local_spectral(Level &L, const lsamg_options &o, int *err, cudaStream_t s, 
         ch.na = na;
         ch.voff = voff;
         ch.V.alloc(std::max<int64_t>(voff[na], 1), s);
-        DBuf<double> work;
-        DBuf<int64_t> dwk;
-        work.alloc(std::max<int64_t>(wkoff[na], 1), s);
-        upload(dwk, wkoff, s);
         {
             std::vector<int64_t> o(na);
             for (int64_t i = 0; i < na; i++) o[i] = voff[i];
@@ -790,7 +785,7 @@ void local_spectral(Level &L, const lsamg_options &o, int *err, cudaStream_t s, 
             // inverse iteration per eigenvalue, then one CholeskyQR2 over all retained vectors:
             // P needs an orthonormal basis of the retained invariant subspace, not the eigenvectors
             LSAMG_PROF(lvl_name(g_prof_level, "ls: stein"), s);
-            stein_batched(dv.p, ev.p, dtoff.p, bC.n.p, wv.p, dk.p, ch.V.p, bV, work.p, dwk.p, s, false);
+            stein_batched(dv.p, ev.p, dtoff.p, bC.n.p, wv.p, dk.p, ch.V.p, bV, s);
             cholqr2_batched(ch.V.p, bV, err, s);
         }
         { LSAMG_PROF(lvl_name(g_prof_level, "ls: ormtr"), s); ormtr_batched(C.p, bC, tv.p, dtoff.p, ch.V.p, bV, s, err); }
@@ -1050,7 +1045,7 @@ void smoother_setup(Level &L, const lsamg_options &o, int *err, cudaStream_t s, 
     upload(L.Loff, loff, s);
     L.L64.alloc(std::max<int64_t>(loff[nagg], 1), s);
     L.L32.alloc(std::max<int64_t>(loff[nagg], 1), s);
-    int64_t budget = o.chunk_bytes > 0 ? o.chunk_bytes : (int64_t)16 << 30;
+    int64_t budget = o.chunk_bytes > 0 ? o.chunk_bytes : (int64_t)48 << 30;
     int64_t a0 = 0;
     while (a0 < nagg) {
         int64_t bytes = 0, a1 = a0;

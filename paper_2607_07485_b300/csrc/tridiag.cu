@@ -35,111 +35,159 @@ __device__ double trd_block_sum(double v, double *red) {
     return r;
 }
 
-// column j: panel update, reflector, v into V / WV and into vbuf (absolute row index)
-__global__ void __launch_bounds__(256) k_trd_col(double *base, const int64_t *off, const int32_t *ld,
-                                                 const int32_t *nn, int64_t count, int j, int j0, double *dd,
-                                                 double *ee, double *tt, const int64_t *toff, double *VW, double *WV,
-                                                 const int64_t *vwoff, double *vbuf) {
+// Per-matrix partial sums of one column step, one slot per row block of RB rows (fixed order
+// of summation): [sigma, w^T v, s1[PNB], s2[PNB]].
+constexpr int RB = 256;
+constexpr int PSL = 2 + 2 * PNB;
+
+// column j, rows j .. n-1 by blocks of RB: a -= V W(j,:)^T + W V(j,:)^T over the panel's earlier
+// reflectors; partial sigma = sum a(r)^2 over rows r >= j+2
+__global__ void __launch_bounds__(RB) k_trd_c1(double *base, const int64_t *off, const int32_t *ld, const int32_t *nn,
+                                               int64_t count, int j, int j0, const double *VW, const int64_t *vwoff,
+                                               double *part, const int64_t *partoff) {
     __shared__ double red[32];
     __shared__ double wj[PNB], vj[PNB];
-    __shared__ double sh_tau, sh_scale;
-    const int64_t b = blockIdx.x;
+    const int64_t b = blockIdx.y;
     if (b >= count) return;
     const int n = nn[b];
-    if (j >= n) return;
+    const int r0 = j + blockIdx.x * RB;
+    if (r0 >= n) return;
     const int jj = j - j0, L = ld[b];
     double *A = base + off[b];
-    double *V = VW + vwoff[b], *W = V + (int64_t)PNB * n;
-    double *W2 = WV + vwoff[b], *V2 = W2 + (int64_t)PNB * n;
+    const double *V = VW + vwoff[b], *W = V + (int64_t)PNB * n;
     for (int q = threadIdx.x; q < jj; q += blockDim.x) {
         wj[q] = W[j + (int64_t)q * n];
         vj[q] = V[j + (int64_t)q * n];
     }
     __syncthreads();
-    for (int r = j + threadIdx.x; r < n; r += blockDim.x) {
+    const int r = r0 + threadIdx.x;
+    double sq = 0.0;
+    if (r < n) {
         double a = A[r + (int64_t)j * L];
         for (int q = 0; q < jj; q++) a -= V[r + (int64_t)q * n] * wj[q] + W[r + (int64_t)q * n] * vj[q];
         A[r + (int64_t)j * L] = a;
+        if (r >= j + 2) sq = a * a;
     }
-    __syncthreads();
-    double *d = dd + toff[b], *e = ee + toff[b], *tau = tt + toff[b];
-    if (j == n - 1) {
-        if (threadIdx.x == 0) d[j] = A[j + (int64_t)j * L];
-        return;
-    }
-    const int m = n - j - 1;
-    double *x = A + (j + 1) + (int64_t)j * L;
-    double sig = 0.0;
-    for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) sig += x[i] * x[i];
-    sig = trd_block_sum(sig, red);
-    if (threadIdx.x == 0) {
-        const double alpha = x[0];
-        d[j] = A[j + (int64_t)j * L];
-        if (sig == 0.0) {
-            sh_tau = 0.0;
-            sh_scale = 0.0;
-            e[j] = alpha;
-        } else {
-            const double beta = -copysign(sqrt(alpha * alpha + sig), alpha);
-            sh_tau = (beta - alpha) / beta;
-            sh_scale = 1.0 / (alpha - beta);
-            e[j] = beta;
-        }
-        tau[j] = sh_tau;
-    }
-    __syncthreads();
-    const double sc = sh_scale;
-    const bool refl = sh_tau != 0.0;
-    double *vb = vbuf + toff[b];
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
-        double vi = 1.0;
-        if (i > 0) {
-            vi = refl ? x[i] * sc : 0.0;
-            if (refl) x[i] = vi;
-        }
-        const int r = j + 1 + i;
-        vb[r] = vi;
-        V[r + (int64_t)jj * n] = vi;
-        V2[r + (int64_t)jj * n] = vi;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) x[0] = e[j];
+    sq = trd_block_sum(sq, red);
+    if (threadIdx.x == 0) part[partoff[b] + (int64_t)blockIdx.x * PSL] = sq;
 }
 
-// per matrix: tiles of the trailing lower triangle that the symmetric product of column j needs
-// (none when the reflector is the identity); exclusive prefix over the batch in pre[0..count]
-__global__ void __launch_bounds__(1024) k_trd_sched(const int32_t *nn, int64_t count, int j, const double *tt,
-                                                    const int64_t *toff, int64_t *pre) {
-    __shared__ int64_t part[1024];
+// one CTA: the Householder scalars of column j for every matrix (d_j, e_j, tau_j, the scale of
+// v), then the tiles of the trailing lower triangle that the symmetric product needs (none when
+// the reflector is the identity) and their exclusive prefix over the batch in pre[0..count]
+__global__ void __launch_bounds__(1024) k_trd_sched(double *base, const int64_t *off, const int32_t *ld,
+                                                    const int32_t *nn, int64_t count, int j, double *dd, double *ee,
+                                                    double *tt, const int64_t *toff, const double *part,
+                                                    const int64_t *partoff, double *scal, int64_t *pre) {
+    __shared__ int64_t cnts[1024];
     const int64_t per = (count + blockDim.x - 1) / blockDim.x;
     const int64_t b0 = threadIdx.x * per, b1 = min(count, b0 + per);
     int64_t s = 0;
     for (int64_t b = b0; b < b1; b++) {
-        const int m = nn[b] - j - 1;
-        if (m > 0 && tt[toff[b] + j] != 0.0) {
+        const int n = nn[b];
+        if (j >= n) continue;
+        const int L = ld[b];
+        const double *A = base + off[b];
+        double *d = dd + toff[b], *e = ee + toff[b], *tau = tt + toff[b];
+        d[j] = A[j + (int64_t)j * L];
+        const int m = n - j - 1;
+        if (m <= 0) continue;
+        const int nrb = (n - j + RB - 1) / RB;
+        double sig = 0.0;
+        for (int q = 0; q < nrb; q++) sig += part[partoff[b] + (int64_t)q * PSL];
+        const double alpha = A[(j + 1) + (int64_t)j * L];
+        double t = 0.0, sc = 0.0;
+        if (sig == 0.0) {
+            e[j] = alpha;
+        } else {
+            const double beta = -copysign(sqrt(alpha * alpha + sig), alpha);
+            t = (beta - alpha) / beta;
+            sc = 1.0 / (alpha - beta);
+            e[j] = beta;
+        }
+        tau[j] = t;
+        scal[b] = sc;
+        if (t != 0.0) {
             const int64_t T = (m + ST - 1) / ST;
             s += T * (T + 1) / 2;
         }
     }
-    part[threadIdx.x] = s;
+    cnts[threadIdx.x] = s;
     __syncthreads();
     if (threadIdx.x == 0) {
         int64_t acc = 0;
         for (int t = 0; t < (int)blockDim.x; t++) {
-            const int64_t v = part[t];
-            part[t] = acc;
+            const int64_t v = cnts[t];
+            cnts[t] = acc;
             acc += v;
         }
         pre[count] = acc;
     }
     __syncthreads();
-    int64_t acc = part[threadIdx.x];
+    int64_t acc = cnts[threadIdx.x];
     for (int64_t b = b0; b < b1; b++) {
         pre[b] = acc;
         const int m = nn[b] - j - 1;
         if (m > 0 && tt[toff[b] + j] != 0.0) {
             const int64_t T = (m + ST - 1) / ST;
             acc += T * (T + 1) / 2;
+        }
+    }
+}
+
+// rows j+1 .. n-1 by blocks: v (unit first entry, the scaled column below it) into A, vbuf, V and
+// WV; partial s1 = W^T v and s2 = V^T v over the panel's earlier columns
+__global__ void __launch_bounds__(RB) k_trd_c3(double *base, const int64_t *off, const int32_t *ld, const int32_t *nn,
+                                               int64_t count, int j, int j0, const double *ee, const double *tt,
+                                               const int64_t *toff, const double *scal, double *VW, double *WV,
+                                               const int64_t *vwoff, double *vbuf, double *part,
+                                               const int64_t *partoff) {
+    __shared__ double vs[RB];
+    const int64_t b = blockIdx.y;
+    if (b >= count) return;
+    const int n = nn[b];
+    const int r0 = j + 1 + blockIdx.x * RB;
+    if (r0 >= n) return;
+    const int jj = j - j0, L = ld[b];
+    double *A = base + off[b];
+    double *V = VW + vwoff[b];
+    const double *W = V + (int64_t)PNB * n;
+    double *V2 = WV + vwoff[b] + (int64_t)PNB * n;
+    const double t = tt[toff[b] + j], sc = scal[b];
+    const int r = r0 + threadIdx.x;
+    double v = 0.0;
+    if (r < n) {
+        if (r == j + 1) {
+            v = 1.0;
+            A[r + (int64_t)j * L] = ee[toff[b] + j];
+        } else if (t != 0.0) {
+            v = A[r + (int64_t)j * L] * sc;
+            A[r + (int64_t)j * L] = v;
+        }
+        vbuf[toff[b] + r] = v;
+        V[r + (int64_t)jj * n] = v;
+        V2[r + (int64_t)jj * n] = v;
+    }
+    vs[threadIdx.x] = v;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    double *pp = part + partoff[b] + (int64_t)blockIdx.x * PSL;
+    for (int q = warp; q < jj; q += nwarp) {
+        double a1 = 0.0, a2 = 0.0;
+        for (int i = lane; i < RB; i += 32) {
+            const int rr = r0 + i;
+            if (rr < n) {
+                a1 += W[rr + (int64_t)q * n] * vs[i];
+                a2 += V[rr + (int64_t)q * n] * vs[i];
+            }
+        }
+        for (int o = 16; o; o >>= 1) {
+            a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+            a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+        }
+        if (lane == 0) {
+            pp[2 + q] = a1;
+            pp[2 + PNB + q] = a2;
         }
     }
 }
@@ -216,71 +264,84 @@ __global__ void __launch_bounds__(256) k_trd_symv(const double *base, const int6
     }
 }
 
-// w of column j: y = sum of the slots in fixed order, the panel corrections, the tau/2 term
-__global__ void __launch_bounds__(256) k_trd_w(const int32_t *nn, int64_t count, int j, int j0, const double *tt,
+// w of column j, rows j+1 .. n-1 by blocks: y = the product slots summed in fixed order, then
+// w' = tau (y - V s1 - W s2) into ybuf, partial w'^T v
+__global__ void __launch_bounds__(RB) k_trd_w2(const int32_t *nn, int64_t count, int j, int j0, const double *tt,
                                                const int64_t *toff, const double *vbuf, const double *P,
                                                const int64_t *poff, double *VW, double *WV, const int64_t *vwoff,
-                                               double *ybuf) {
+                                               double *ybuf, double *part, const int64_t *partoff) {
     __shared__ double red[32];
     __shared__ double s1[PNB], s2[PNB];
-    const int64_t b = blockIdx.x;
+    const int64_t b = blockIdx.y;
     if (b >= count) return;
     const int n = nn[b];
     const int m = n - j - 1;
-    if (m <= 0) return;
+    const int r0 = j + 1 + blockIdx.x * RB;
+    if (m <= 0 || r0 >= n) return;
     const int jj = j - j0;
     double *V = VW + vwoff[b], *W = V + (int64_t)PNB * n;
     double *W2 = WV + vwoff[b];
     const double tau = tt[toff[b] + j];
+    const int r = r0 + threadIdx.x;
     if (tau == 0.0) {
-        for (int r = j + 1 + threadIdx.x; r < n; r += blockDim.x) {
+        if (r < n) {
             W[r + (int64_t)jj * n] = 0.0;
             W2[r + (int64_t)jj * n] = 0.0;
         }
         return;
     }
+    const int nrb = (m + RB - 1) / RB;
+    const double *pb = part + partoff[b];
+    for (int q = threadIdx.x; q < jj; q += blockDim.x) {
+        double a1 = 0.0, a2 = 0.0;
+        for (int k = 0; k < nrb; k++) {
+            a1 += pb[(int64_t)k * PSL + 2 + q];
+            a2 += pb[(int64_t)k * PSL + 2 + PNB + q];
+        }
+        s1[q] = a1;
+        s2[q] = a2;
+    }
+    __syncthreads();
     const double *v = vbuf + toff[b];
     const int T = (m + ST - 1) / ST;
     const double *Pb = P + poff[b];
-    double *y = ybuf + toff[b];
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
-        const int ti = i / ST, rr = i % ST;
-        double acc = 0.0;
-        for (int t = 0; t < T; t++) acc += Pb[((int64_t)ti * T + t) * ST + rr];
-        y[j + 1 + i] = acc;
-    }
-    // s1 = W^T v, s2 = V^T v over rows j+1 .. n-1 (a warp per panel column)
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    for (int q = warp; q < jj; q += nwarp) {
-        double a1 = 0.0, a2 = 0.0;
-        for (int r = j + 1 + lane; r < n; r += 32) {
-            a1 += W[r + (int64_t)q * n] * v[r];
-            a2 += V[r + (int64_t)q * n] * v[r];
-        }
-        for (int o = 16; o; o >>= 1) {
-            a1 += __shfl_xor_sync(0xffffffffu, a1, o);
-            a2 += __shfl_xor_sync(0xffffffffu, a2, o);
-        }
-        if (lane == 0) {
-            s1[q] = a1;
-            s2[q] = a2;
-        }
-    }
-    __syncthreads();
     double wv = 0.0;
-    for (int r = j + 1 + threadIdx.x; r < n; r += blockDim.x) {
-        double a = y[r];
-        for (int q = 0; q < jj; q++) a -= V[r + (int64_t)q * n] * s1[q] + W[r + (int64_t)q * n] * s2[q];
-        a *= tau;
-        y[r] = a;
-        wv += a * v[r];
+    if (r < n) {
+        const int i = r - j - 1, ti = i / ST, rr = i % ST;
+        double y = 0.0;
+        for (int t = 0; t < T; t++) y += Pb[((int64_t)ti * T + t) * ST + rr];
+        for (int q = 0; q < jj; q++) y -= V[r + (int64_t)q * n] * s1[q] + W[r + (int64_t)q * n] * s2[q];
+        y *= tau;
+        ybuf[toff[b] + r] = y;
+        wv = y * v[r];
     }
     wv = trd_block_sum(wv, red);
+    if (threadIdx.x == 0) part[partoff[b] + (int64_t)blockIdx.x * PSL + 1] = wv;
+}
+
+// w = w' - (tau/2)(w'^T v) v into W and WV
+__global__ void __launch_bounds__(RB) k_trd_w3(const int32_t *nn, int64_t count, int j, int j0, const double *tt,
+                                               const int64_t *toff, const double *vbuf, double *VW, double *WV,
+                                               const int64_t *vwoff, const double *ybuf, const double *part,
+                                               const int64_t *partoff) {
+    const int64_t b = blockIdx.y;
+    if (b >= count) return;
+    const int n = nn[b];
+    const int m = n - j - 1;
+    const int r0 = j + 1 + blockIdx.x * RB;
+    if (m <= 0 || r0 >= n) return;
+    const double tau = tt[toff[b] + j];
+    if (tau == 0.0) return;
+    const int jj = j - j0;
+    const int nrb = (m + RB - 1) / RB;
+    double wv = 0.0;
+    for (int k = 0; k < nrb; k++) wv += part[partoff[b] + (int64_t)k * PSL + 1];
     const double alpha = -0.5 * tau * wv;
-    for (int r = j + 1 + threadIdx.x; r < n; r += blockDim.x) {
-        const double w = y[r] + alpha * v[r];
-        W[r + (int64_t)jj * n] = w;
-        W2[r + (int64_t)jj * n] = w;
+    const int r = r0 + threadIdx.x;
+    if (r < n) {
+        const double w = ybuf[toff[b] + r] + alpha * vbuf[toff[b] + r];
+        VW[vwoff[b] + (int64_t)PNB * n + r + (int64_t)jj * n] = w;
+        WV[vwoff[b] + r + (int64_t)jj * n] = w;
     }
 }
 
@@ -289,9 +350,6 @@ __global__ void __launch_bounds__(256) k_trd_w(const int32_t *nn, int64_t count,
 void sytd2_batched(double *base, const MatBatch &Ab, double *d, double *e, double *tau, const int64_t *toff,
                    cudaStream_t s) {
     if (Ab.count == 0 || Ab.maxn == 0) return;
-    double fl = 0.0;
-    for (auto v : Ab.h_n) fl += 4.0 / 3.0 * v * v * v;
-    KTime kt(KC_SYTD2, s, fl);
     const int64_t cnt = Ab.count;
     std::vector<int64_t> vwoff(cnt + 1, 0), poff(cnt + 1, 0);
     for (int64_t b = 0; b < cnt; b++) {
@@ -301,16 +359,21 @@ void sytd2_batched(double *base, const MatBatch &Ab, double *d, double *e, doubl
         poff[b + 1] = poff[b] + T * T * ST;
     }
     const int64_t tn = read1(toff + cnt, s);
-    DBuf<double> VW, WV, P, vbuf, ybuf;
-    DBuf<int64_t> dvw, dpo, pre;
+    std::vector<int64_t> partoff(cnt + 1, 0);
+    for (int64_t b = 0; b < cnt; b++) partoff[b + 1] = partoff[b] + cdiv(Ab.h_n[b], RB) * PSL;
+    DBuf<double> VW, WV, P, vbuf, ybuf, part, scal;
+    DBuf<int64_t> dvw, dpo, dpa, pre;
     VW.alloc(std::max<int64_t>(vwoff[cnt], 1), s);
     WV.alloc(std::max<int64_t>(vwoff[cnt], 1), s);
     P.alloc(std::max<int64_t>(poff[cnt], 1), s);
     vbuf.alloc(std::max<int64_t>(tn, 1), s);
     ybuf.alloc(std::max<int64_t>(tn, 1), s);
+    part.alloc(std::max<int64_t>(partoff[cnt], 1), s);
+    scal.alloc(cnt, s);
     pre.alloc(cnt + 1, s);
     upload(dvw, std::vector<int64_t>(vwoff.begin(), vwoff.end() - 1), s);
     upload(dpo, std::vector<int64_t>(poff.begin(), poff.end() - 1), s);
+    upload(dpa, std::vector<int64_t>(partoff.begin(), partoff.end() - 1), s);
     DBuf<int> err;
     err.alloc(2, s);
     err.zero(s);
@@ -319,17 +382,33 @@ void sytd2_batched(double *base, const MatBatch &Ab, double *d, double *e, doubl
     for (int j0 = 0; j0 < Ab.maxn; j0 += PNB) {
         const int j1 = std::min(Ab.maxn, j0 + PNB);
         for (int j = j0; j < j1; j++) {
-            k_trd_col<<<(unsigned)cnt, 256, 0, s>>>(base, Ab.off.p, Ab.ld.p, Ab.n.p, cnt, j, j0, d, e, tau, toff,
-                                                     VW.p, WV.p, dvw.p, vbuf.p);
+            // the FP64 column steps (the panel's rank-2k update is a tensor-core product): the
+            // trailing lower triangle is read once per column by the symmetric product
+            double by = 0.0;
+            for (auto v : Ab.h_n) {
+                const double m = v - j - 1;
+                if (m > 0) by += 4.0 * m * (m + 1);
+            }
+            KTime kt(KC_SYTD2, s, 0.0, by);
+            const dim3 g1((unsigned)cdiv(Ab.maxn - j, RB), (unsigned)cnt);
+            k_trd_c1<<<g1, RB, 0, s>>>(base, Ab.off.p, Ab.ld.p, Ab.n.p, cnt, j, j0, VW.p, dvw.p, part.p, dpa.p);
+            CK_LAUNCH();
+            k_trd_sched<<<1, 1024, 0, s>>>(base, Ab.off.p, Ab.ld.p, Ab.n.p, cnt, j, d, e, tau, toff, part.p, dpa.p,
+                                           scal.p, pre.p);
             CK_LAUNCH();
             if (j >= Ab.maxn - 1) break;
-            k_trd_sched<<<1, 1024, 0, s>>>(Ab.n.p, cnt, j, tau, toff, pre.p);
+            const dim3 g3((unsigned)cdiv(Ab.maxn - j - 1, RB), (unsigned)cnt);
+            k_trd_c3<<<g3, RB, 0, s>>>(base, Ab.off.p, Ab.ld.p, Ab.n.p, cnt, j, j0, e, tau, toff, scal.p, VW.p, WV.p,
+                                       dvw.p, vbuf.p, part.p, dpa.p);
             CK_LAUNCH();
             k_trd_symv<<<symv_grid, 256, 0, s>>>(base, Ab.off.p, Ab.ld.p, Ab.n.p, cnt, j, toff, vbuf.p, P.p, dpo.p,
                                                  pre.p);
             CK_LAUNCH();
-            k_trd_w<<<(unsigned)cnt, 256, 0, s>>>(Ab.n.p, cnt, j, j0, tau, toff, vbuf.p, P.p, dpo.p, VW.p, WV.p,
-                                                  dvw.p, ybuf.p);
+            k_trd_w2<<<g3, RB, 0, s>>>(Ab.n.p, cnt, j, j0, tau, toff, vbuf.p, P.p, dpo.p, VW.p, WV.p, dvw.p, ybuf.p,
+                                       part.p, dpa.p);
+            CK_LAUNCH();
+            k_trd_w3<<<g3, RB, 0, s>>>(Ab.n.p, cnt, j, j0, tau, toff, vbuf.p, VW.p, WV.p, dvw.p, ybuf.p, part.p,
+                                       dpa.p);
             CK_LAUNCH();
         }
         // trailing update A22 -= V W^T + W V^T over rows / columns >= j1, K = 2 PNB

@@ -1,6 +1,8 @@
 """bench.py's reference arm (the FP64 oracle on the host cores) prints one JSON line with the
-fields of the benchmark contract, on the same workload, metric and config keys as the GPU
-arm, for both workloads.  CPU only (one step, no warm-up, on the bounded oracle samples)."""
+fields of the benchmark contract, with the metric and config keys of the GPU arm, for both
+workloads.  Its value is the time it measured on the bounded sample that it names in
+config.workload (the full workload it samples is named beside it); a DOF-ratio extrapolation
+appears only in its own labelled field.  CPU only (one step, no warm-up)."""
 import json
 import os
 import subprocess
@@ -27,8 +29,10 @@ def test_reference_arm_json_line(cfg, n_full, nrhs, tag):
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"] == {"value": d["value"], "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     c = d["config"]
-    assert c["n_dofs"] == n_full and c["nrhs"] == nrhs and tag in c["workload"]
-    assert c["l2"].startswith("inputs larger than L2")
+    sample = bench.workload(bench.WORKLOADS[cfg]["sample_N"], cfg)
+    assert c["n_dofs"] == sample["n"] and c["workload"] == bench.workload_name(sample)
+    assert c["sample_of_dofs"] == n_full and tag in c["sample_of"] and c["nrhs"] == nrhs
+    assert d["dof_scaled_lower_bound_s"] == pytest.approx(d["value"] * n_full / sample["n"])
     assert {"workload", "n_dofs", "nrhs", "solve_mode", "options", "l2", "parallelism"} <= set(c)
 
 

@@ -35,14 +35,17 @@ DEV = "cuda:0"
 # carries only ~3 significant digits (independent FP64 evaluations agree to ~1e-4).
 # The projector tolerance applies to the difference times delta_i tau (capped at 1), the
 # separation of the retained from the discarded eigenvalues (Davis-Kahan).
-# Rank-flip band: a mode count may differ only by eigenvalues with |mu tau - 1| < band.
+# Rank-flip band: a mode count may differ only by eigenvalues with |mu tau - 1| < 1e-9, where the
+# rank decision is flagged as unstable rather than a parity failure.  The smallest |mu tau - 1|
+# of these cases is 0.013 (cfg2_16, cfg5_16), far outside the band: their counts must agree.
+BAND = 1e-9
 CASES = {
-    "rt1_beta1": (lambda: _rt(8, 1, 1.0), dict(agg_passes=1, agg_passes_coarse=1, max_density=1.0), 1e-8, 1e-7, 1e-7),
-    "cfg1": (lambda: _cfg(1, 16), dict(), 1e-8, 1e-6, 1e-7),
-    "cfg2_16": (lambda: _cfg(2, 16), dict(), 1e-3, 1e-2, 1e-3),
-    "cfg3_16": (lambda: _cfg(3, 16), dict(tau_c=1.0), 1e-6, 1e-4, 1e-7),
-    "cfg5_16": (lambda: _cfg(5, 16), dict(), 1e-3, 1e-2, 1e-3),
-    "cfg4_6": (lambda: _cfg(4, 6), dict(agg_passes=1, agg_passes_coarse=1), 1e-8, 1e-6, 1e-7),
+    "rt1_beta1": (lambda: _rt(8, 1, 1.0), dict(agg_passes=1, agg_passes_coarse=1, max_density=1.0), 1e-8, 1e-7, BAND),
+    "cfg1": (lambda: _cfg(1, 16), dict(), 1e-8, 1e-6, BAND),
+    "cfg2_16": (lambda: _cfg(2, 16), dict(), 1e-3, 1e-2, BAND),
+    "cfg3_16": (lambda: _cfg(3, 16), dict(tau_c=1.0), 1e-6, 1e-4, BAND),
+    "cfg5_16": (lambda: _cfg(5, 16), dict(), 1e-3, 1e-2, BAND),
+    "cfg4_6": (lambda: _cfg(4, 6), dict(agg_passes=1, agg_passes_coarse=1), 1e-8, 1e-6, BAND),
 }
 
 
@@ -96,15 +99,20 @@ def test_hierarchy_structure_bit_exact(name):
         optr, oidx = amg.query(l, "OMEGA_PTR"), amg.query(l, "OMEGA_IDX")
         for i, Om in enumerate(_csr_lists(optr, oidx)):
             np.testing.assert_array_equal(Om, L.Omega[i], err_msg=f"Omega_{i} level {l}")
+        # colours depend on the overlaps only (not on the mode counts): always compared
+        np.testing.assert_array_equal(amg.query(l, "COLOUR"), L.colour, err_msg=f"colours level {l}")
         kg = amg.query(l, "K")
         band = CASES[name][4]
+        flagged = []
         for i in np.flatnonzero(kg != L.k):
             near = int((np.abs(L.mu[i] * L.tau - 1.0) < band).sum())
             assert abs(int(kg[i]) - int(L.k[i])) <= near, \
                 f"level {l} aggregate {i}: k {kg[i]} vs {L.k[i]} with {near} eigenvalues in the band"
-        if (kg != L.k).any():
-            return  # the coarse numbering differs past a legitimate rank flip
-        np.testing.assert_array_equal(amg.query(l, "COLOUR"), L.colour, err_msg=f"colours level {l}")
+            flagged.append(int(i))
+        if flagged:
+            # a flagged (unstable) rank decision renumbers the coarse DOFs after it: the coarse
+            # maps of this level and the coarser levels are not comparable
+            pytest.skip(f"level {l}: rank decision unstable (|mu tau - 1| < {band}) at aggregates {flagged}")
         # next level's element maps (merged coarse elements) and the element -> group map
         cptr, cidx = amg.query(l, "CELEM_PTR"), amg.query(l, "CELEM_IDX")
         C = H.levels[l + 1]
@@ -116,6 +124,28 @@ def test_hierarchy_structure_bit_exact(name):
         for g, members in enumerate(L.cgroups):
             ref[members] = g
         np.testing.assert_array_equal(cg, ref)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_two_handles_bit_identical(name):
+    """The set-up is deterministic: a second handle on the same input reproduces every integer
+    structure and every interpolation value bit for bit (no atomics in any summation that feeds
+    the local eigenproblems)."""
+    p, H, amg, _, _, _ = case(name)
+    o = dict(CASES[name][1])
+    if "tau_c" not in o and "c_tau" in p:
+        o["tau_c"] = p["c_tau"]
+    other = Lsamg(p["n"], torch.from_numpy(p["elem_dofs"]).to(DEV), torch.from_numpy(p["mats"]).to(DEV), **o)
+    st = amg.stats()
+    assert other.stats()["n"] == st["n"]
+    for l in range(st["n_levels"]):
+        for what in ("EPTR", "EIDX", "GROWS", "G"):
+            np.testing.assert_array_equal(other.query(l, what), amg.query(l, what), err_msg=f"{what} level {l}")
+        if l == st["n_levels"] - 1:
+            continue
+        for what in ("AGG", "K", "COLOUR", "CELEM_PTR", "CELEM_IDX", "Z"):
+            np.testing.assert_array_equal(other.query(l, what), amg.query(l, what), err_msg=f"{what} level {l}")
+    other.close()
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -314,29 +344,96 @@ def test_multi_rhs_matches_single_and_host_path():
     np.testing.assert_allclose(Xh, X.cpu().numpy(), rtol=1e-10, atol=1e-12)
 
 
-def test_adjoint_gradient_matches_oracle():
+def _adjoint_case(beta):
     c = fegen.config(5, N=8)
-    n, d, K0 = fegen.rt_quad(8, 1, 1.0, 3)
+    n, d, K0 = fegen.rt_quad(8, 1, beta, 3)
     K = np.ascontiguousarray(np.broadcast_to(K0, (d.shape[0],) + K0.shape))
-    theta = fegen.config(5, N=8)["coef"]
-    b = c["b"][0]
-    xs = c["x_star"]
+    return n, d, K, c["coef"], c["b"][0], c["x_star"]
+
+
+def _gpu_grad(n, d, K, theta, b, xs, rtol):
+    from paper_2607_07485_b300 import solve_with_grad
+    th = torch.from_numpy(theta).to(DEV).requires_grad_(True)
+    x = solve_with_grad(th, torch.from_numpy(b).to(DEV), n, torch.from_numpy(d).to(DEV),
+                        torch.from_numpy(K).to(DEV), mode=0, rtol=rtol)
+    loss = 0.5 * ((x - torch.from_numpy(xs).to(DEV)) ** 2).sum()
+    loss.backward()
+    return th.grad.cpu().numpy(), float(loss)
+
+
+def test_adjoint_gradient_matches_oracle():
+    # the adjoint workload's mesh and coefficients with beta = 1 (kappa(A) ~ 1e3): FP64 fixes the
+    # gradient far below 1e-8, the bar of the adjoint row
+    n, d, K, theta, b, xs = _adjoint_case(1.0)
     A = O.assemble(n, d, K * theta[:, None, None])
     Ho = O.setup(n, d, K * theta[:, None, None])
 
     def solve(rhs):
-        return O.pcg(lambda v: A @ v, rhs, lambda r: O.vcycle(Ho, r), rtol=1e-12)[0]
+        return O.pcg(lambda v: A @ v, rhs, lambda r: O.vcycle(Ho, r), rtol=1e-13)[0]
 
     _, _, g_ref = O.adjoint_grad(n, d, K, theta, b, xs, solve)
-    from paper_2607_07485_b300 import solve_with_grad
-    th = torch.from_numpy(theta).to(DEV).requires_grad_(True)
-    bt = torch.from_numpy(b).to(DEV)
-    x = solve_with_grad(th, bt, n, torch.from_numpy(d).to(DEV), torch.from_numpy(K).to(DEV),
-                        mode=0, rtol=1e-12)
-    loss = 0.5 * ((x - torch.from_numpy(xs).to(DEV)) ** 2).sum()
-    loss.backward()
-    g = th.grad.cpu().numpy()
-    np.testing.assert_allclose(g, g_ref, rtol=1e-7, atol=1e-7 * np.abs(g_ref).max())
+    g, _ = _gpu_grad(n, d, K, theta, b, xs, 1e-13)
+    np.testing.assert_allclose(g, g_ref, rtol=1e-8, atol=1e-8 * np.abs(g_ref).max())
+
+
+def test_adjoint_gradient_on_the_adjoint_workload_form():
+    # the adjoint workload itself (RT_[1], beta = 1e-6, theta_e = exp(N(0,1))) at 8 x 8:
+    # kappa(A) ~ 9e11, so FP64 fixes x, lambda and g only to ~kappa eps ~ 2e-4 in the worst case;
+    # the oracle's own PCG and a sparse direct solve agree on g to 2.6e-7 (max-normalised).
+    # Reference: the direct solve; bar: 1e-6, about 4x that observed FP64 spread.
+    import scipy.sparse.linalg as spla
+    n, d, K, theta, b, xs = _adjoint_case(1e-6)
+    A = O.assemble(n, d, K * theta[:, None, None])
+    lu = spla.splu(A.tocsc())
+    _, _, g_ref = O.adjoint_grad(n, d, K, theta, b, xs, lu.solve)
+    g, _ = _gpu_grad(n, d, K, theta, b, xs, 1e-13)
+    assert np.abs(g - g_ref).max() <= 1e-6 * np.abs(g_ref).max()
+
+
+def test_adjoint_gradient_central_differences_on_gpu():
+    # central differences of the GPU loss itself (h = 1e-6 relative) on 32 seeded elements of
+    # the beta = 1 adjoint case: truncation ~h^2, solve error / h ~1e-13 / 1e-6
+    n, d, K, theta, b, xs = _adjoint_case(1.0)
+    g, _ = _gpu_grad(n, d, K, theta, b, xs, 1e-14)
+    from paper_2607_07485_b300 import Lsamg as _L
+    dd, KK, bb = torch.from_numpy(d).to(DEV), torch.from_numpy(K).to(DEV), torch.from_numpy(b).to(DEV)
+
+    def loss(th):
+        amg = _L(n, dd, KK, coef=torch.from_numpy(th).to(DEV), rtol=1e-14, maxit=500)
+        x, its, rel, rc = amg.solve(bb, mode=0)
+        amg.close()
+        r = x.cpu().numpy() - xs
+        return 0.5 * float(r @ r)
+
+    rng = np.random.default_rng(32)
+    for e in rng.choice(len(theta), size=32, replace=False):
+        h = 1e-6 * theta[e]
+        tp, tm = theta.copy(), theta.copy()
+        tp[e] += h
+        tm[e] -= h
+        fd = (loss(tp) - loss(tm)) / (2 * h)
+        assert abs(fd - g[e]) <= 1e-5 * np.abs(g).max(), f"element {e}: FD {fd:.6e} vs adjoint {g[e]:.6e}"
+
+
+def test_beta_small_solution_against_direct_solve():
+    # cfg2's form (RT_[3], beta = 1e-6, lognormal theta) at 4 x 4: the GPU solution (FP64 PCG
+    # to 1e-12) against a sparse direct solve, element-wise, within kappa(A) eps ||x||
+    import scipy.sparse.linalg as spla
+    c = fegen.config(2, N=4)
+    mats = np.ascontiguousarray(c["elem_mats"] * c["coef"][:, None, None])
+    A = O.assemble(c["n"], c["elem_dofs"], mats)
+    ev = np.linalg.eigvalsh(A.toarray())
+    kappa = ev[-1] / ev[0]
+    b = c["b"][0]
+    xs = spla.spsolve(A.tocsc(), b)
+    amg = Lsamg(c["n"], torch.from_numpy(c["elem_dofs"]).to(DEV), torch.from_numpy(mats).to(DEV),
+                tau_c=c["c_tau"], rtol=1e-12, maxit=500)
+    x, its, rel, rc = amg.solve(torch.from_numpy(b).to(DEV), mode=0)
+    assert rc == 0
+    x = x.cpu().numpy()
+    bound = kappa * np.finfo(float).eps * np.linalg.norm(xs)
+    assert np.abs(x - xs).max() <= bound, (np.abs(x - xs).max(), bound, kappa)
+    amg.close()
 
 
 # ------------------------------------------------------------------------------- failures
