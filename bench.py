@@ -3,7 +3,8 @@
 
 Workload (default, --cfg 2): RT_[3] grad-div (div u, div v) + 1e-6 (u, v) on a 256 x 256 quad
 mesh of the unit square (2,099,200 DOFs, 65,536 elements of 40 DOFs), per-element coefficient theta_e =
-exp(N(0,1)), right-hand side uniform[-1, 1] (seed 20260702).  --cfg 4: Q2 hexahedral
+exp(N(0,1)), right-hand side uniform[-1, 1] (seed 20260702).  --cfg 3: bicubic Bogner-Fox-Schmit
+anisotropic hyperdiffusion on 512 x 512 rectangles (1,052,676 DOFs).  --cfg 4: Q2 hexahedral
 elasticity on 48^3 cubes (2,738,019 DOFs, E ratio 1e4 checkerboard, nu = 0.45, Nitsche clamp)
 with 16 right-hand sides solved in one batched call.  Synthetic inputs from fegen.
 
@@ -47,6 +48,7 @@ BENCH_OPTS = dict(agg_passes=2, agg_passes_coarse=1, max_levels=4, maxit=400)
 # since two passes make overlaps of ~19k DOFs whose factors would not fit in HBM).
 WORKLOADS = {
     2: dict(N=WORKLOAD_N, opts=BENCH_OPTS, sample_N=16),
+    3: dict(N=512, opts=BENCH_OPTS, sample_N=32),
     4: dict(N=48, opts=dict(agg_passes=1, agg_passes_coarse=1, max_levels=4, maxit=400), sample_N=4),
 }
 L2_BYTES = 126e6
@@ -77,10 +79,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lsamg", choices=["lsamg", "reference"])
     ap.add_argument("--cfg", type=int, default=WORKLOAD_CFG, choices=sorted(WORKLOADS),
-                    help="2: RT_[3] grad-div, 1 right-hand side (default); 4: Q2 elasticity, 16 right-hand sides")
+                    help="2: RT_[3] grad-div, 1 right-hand side (default); 3: bicubic BFS hyperdiffusion; "
+                         "4: Q2 elasticity, 16 right-hand sides")
     ap.add_argument("--N", type=int, default=None, help="mesh size (default: the workload's, 256 or 48)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--oracle-sample", type=int, default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
@@ -145,6 +149,9 @@ def workload(N, cfg=WORKLOAD_CFG):
 
 
 def workload_name(c):
+    if c.get("cfg", WORKLOAD_CFG) == 3:
+        return (f"bicubic BFS anisotropic hyperdiffusion about (0.5,0.5), eps=1e-6, {c['N']}x{c['N']} rectangles, "
+                f"{c['n']:,} DOFs, {c['elem_dofs'].shape[0]:,} elements x 16 DOFs")
     if c.get("cfg", WORKLOAD_CFG) == 4:
         return (f"Q2 hex elasticity, nu=0.45, E ratio 1e4 checkerboard, Nitsche clamp, {c['N']}^3 cubes, "
                 f"{c['n']:,} DOFs, {c['elem_dofs'].shape[0]:,} elements x 81 DOFs, "
@@ -175,27 +182,41 @@ def max_over_ranks(value, device=None):
 
 
 # ----------------------------------------------------------------------------- CPU oracle leg
-def oracle_sample(cfg=WORKLOAD_CFG, threads=None):
+def oracle_sample(cfg=WORKLOAD_CFG):
     """The FP64 oracle on a bounded sample of the same workload (a small mesh of the same
     elements, the same options and the same number of right-hand sides): set-up + FP64 PCG to
-    1e-8 per right-hand side, with `threads` BLAS threads (None: all).  Returns (seconds, info)."""
+    1e-8 per right-hand side, with the BLAS threads of this process.  Returns (seconds, info)."""
     import oracle as O
-    from threadpoolctl import threadpool_limits
     c = workload(WORKLOADS[cfg]["sample_N"], cfg)
     o = dict(WORKLOADS[cfg]["opts"])
     o.pop("maxit", None)
-    with threadpool_limits(limits=threads):
-        t = time.perf_counter()
-        H = O.setup(c["n"], c["elem_dofs"], scaled_mats(c), opts=o, c_tau=c["c_tau"])
-        ts = time.perf_counter() - t
-        A = H.levels[0].A
-        t = time.perf_counter()
-        it = 0
-        for b in c["b"]:
-            x, its_b, hist = O.pcg(lambda v: A @ v, b, lambda r: O.vcycle(H, r))
-            it = max(it, its_b)
-        tsol = time.perf_counter() - t
+    t = time.perf_counter()
+    H = O.setup(c["n"], c["elem_dofs"], scaled_mats(c), opts=o, c_tau=c["c_tau"])
+    ts = time.perf_counter() - t
+    A = H.levels[0].A
+    t = time.perf_counter()
+    it = 0
+    for b in c["b"]:
+        x, its_b, hist = O.pcg(lambda v: A @ v, b, lambda r: O.vcycle(H, r))
+        it = max(it, its_b)
+    tsol = time.perf_counter() - t
     return ts + tsol, dict(n=c["n"], N=c["N"], name=workload_name(c), setup_s=ts, solve_s=tsol, its=it)
+
+
+ONE_THREAD_ENV = {k: "1" for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS",
+                                     "BLIS_NUM_THREADS", "VECLIB_MAXIMUM_THREADS", "NUMEXPR_NUM_THREADS")}
+
+
+def oracle_sample_one_thread(cfg):
+    """The same sample in a child process whose BLAS is limited to one thread (environment set
+    before NumPy loads); returns seconds, or None if the child failed."""
+    env = dict(os.environ, **ONE_THREAD_ENV)
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", str(cfg)], env=env,
+                       capture_output=True, text=True, timeout=900)
+    for ln in r.stdout.splitlines():
+        if ln.startswith("oracle_sample_seconds "):
+            return float(ln.split()[1])
+    return None
 
 
 def cpu_cores():
@@ -213,12 +234,14 @@ def cpu_baseline_entry(cfg, n_full, runs=1):
     measured all-thread time of one sample step.  A DOF-ratio extrapolation to the full workload is
     given separately (a lower bound: the local work grows as the cube of the aggregate size)."""
     t_all = [oracle_sample(cfg)[0] for _ in range(runs)]
-    t_one, info = oracle_sample(cfg, threads=1)
+    info = oracle_sample(cfg)[1]
+    t_one = oracle_sample_one_thread(cfg)
     v = statistics.mean(t_all)
+    one = "n/a" if t_one is None else f"{t_one:.2f} s"
     return dict(value=v, unit="s", cores=cpu_cores(), kind="oracle",
                 sample=(f"FP64 oracle (NumPy/SciPy) set-up + PCG to 1e-8 per right-hand side on {info['name']} "
                         f"(the same elements, options and right-hand-side count at a bounded size); "
-                        f"{v:.2f} s with {cpu_cores()} BLAS threads, {t_one:.2f} s with 1"),
+                        f"{v:.2f} s with {cpu_cores()} BLAS threads, {one} with 1"),
                 sample_dofs=info["n"], one_thread_s=t_one, nproc=os.cpu_count(),
                 dof_scaled_lower_bound_s=v * n_full / info["n"])
 
@@ -258,6 +281,9 @@ def run_reference(args, rank):
 # ----------------------------------------------------------------------------- GPU leg
 def main():
     args = parse()
+    if args.oracle_sample is not None:      # child of oracle_sample_one_thread
+        print(f"oracle_sample_seconds {oracle_sample(args.oracle_sample)[0]:.6f}", flush=True)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -316,6 +342,9 @@ def main():
             modes[mode] = dict(setup_s=st["setup_seconds"], solve_s=tsol, its=its, relres=rel,
                                converged=(rc == 0), step_s=time.perf_counter() - t0)
         amg.close()
+        print(f"[bench] warm-up {w}: " + ", ".join(f"mode {m}: set-up {v['setup_s']:.2f} s, solve {v['solve_s']:.2f} s, "
+                                                     f"{v['its']} its" for m, v in modes.items()),
+              file=sys.stderr, flush=True)
         conv = [m for m in modes if modes[m]["converged"]]
         best_mode = min(conv, key=lambda m: modes[m]["setup_s"] + modes[m]["solve_s"]) if conv else 0
     # ---- timed region
@@ -331,6 +360,8 @@ def main():
     setups, solves, its_list, stats = [], [], [], None
     for _ in range(args.steps):
         st, tsol, its, rel, rc = step(best_mode, profile=1)
+        print(f"[bench] step {len(setups)}: set-up {st['setup_seconds']:.2f} s, solve {tsol:.2f} s, {its} its",
+              file=sys.stderr, flush=True)
         setups.append(st["setup_seconds"])
         solves.append(tsol)
         its_list.append(its)

@@ -739,7 +739,6 @@ int lsamg_dgemm_nt(int64_t M, int64_t N, int64_t K, double alpha, const double *
         DBuf<int> err;
         err.alloc(2, s);
         err.zero(s);
-        constexpr int64_t KMAX = (int64_t)oz::MAX_CHUNKS * oz::TK;
         oz::Workspace ws;
         if (K == 0) {   // C = beta C through a product with a zero operand
             DBuf<double> z;
@@ -753,18 +752,17 @@ int lsamg_dgemm_nt(int64_t M, int64_t N, int64_t K, double alpha, const double *
             oz::gemm(ws.sl.p, ws.ex.p, C, {oz::GemmJob{0, sj[1].dst_off, 0, sj[1].exp_off, 0, 1, ldc, (int32_t)M,
                                                      (int32_t)N, 1, 0, 0, 0}},
                      0.0, beta, err.p, s);
-        }
-        for (int64_t k0 = 0; k0 < K; k0 += KMAX) {
-            const int32_t kk = (int32_t)std::min(KMAX, K - k0);
-            const int64_t hb = oz::slice_halves(M, kk), eb = oz::exp_ints(M);
-            std::vector<oz::SplitJob> sa{{k0 * lda, 1, lda, 0, 0, (int32_t)M, kk}};
-            std::vector<oz::SplitJob> sb{{k0 * ldb, 1, ldb, hb, eb, (int32_t)N, kk}};
-            ws.reserve(hb + oz::slice_halves(N, kk), eb + oz::exp_ints(N), s);
+        } else {
+            // the products run in K passes of at most 4096 (oz::gemm), the operands are split once
+            const int64_t hb = oz::slice_halves(M, K), eb = oz::exp_ints(M);
+            std::vector<oz::SplitJob> sa{{0, 1, lda, 0, 0, (int32_t)M, (int32_t)K}};
+            std::vector<oz::SplitJob> sb{{0, 1, ldb, hb, eb, (int32_t)N, (int32_t)K}};
+            ws.reserve(hb + oz::slice_halves(N, K), eb + oz::exp_ints(N), s);
             oz::split(A, sa, ws.sl.p, ws.ex.p, s);
             oz::split(B, sb, ws.sl.p, ws.ex.p, s);
             oz::gemm(ws.sl.p, ws.ex.p, C,
-                     {oz::GemmJob{0, hb, 0, eb, 0, 1, ldc, (int32_t)M, (int32_t)N, kk, 0, 0, 0}}, alpha,
-                     k0 == 0 ? beta : 1.0, err.p, s);
+                     {oz::GemmJob{0, hb, 0, eb, 0, 1, ldc, (int32_t)M, (int32_t)N, (int32_t)K, 0, 0, 0}}, alpha, beta,
+                     err.p, s);
         }
         check_err(err.p, s, "tensor-core FP64 product");
     });

@@ -499,13 +499,15 @@ __global__ void __launch_bounds__(256) k_tri_wave(const int32_t *tasks, int64_t 
                         for (int c = p; c <= e; c += 4) {
                             const double d = Di[e * (e + 1) / 2 + c];
 #pragma unroll
-                            for (int r = 0; r < WF_RG; r++) acc[r] += d * tv[r][c];
+                            for (int r = 0; r < WF_RG; r++)
+                                if (r < nr) acc[r] += d * tv[r][c];
                         }
                     } else {
                         for (int i = e + p; i < nb; i += 4) {
                             const double d = Di[i * (i + 1) / 2 + e];
 #pragma unroll
-                            for (int r = 0; r < WF_RG; r++) acc[r] += d * tv[r][i];
+                            for (int r = 0; r < WF_RG; r++)
+                                if (r < nr) acc[r] += d * tv[r][i];
                         }
                     }
                 }

@@ -825,31 +825,25 @@ void trsm_batched(const double *base_L, const MatBatch &Lb, double *base_B, cons
 void syrk_tn_batched(double *base_C, const MatBatch &Cb, const double *base_W, const MatBatch &Wb,
                      double alpha, bool w_rowmajor, cudaStream_t s, int *err) {
     if (Cb.count == 0 || Cb.maxn == 0) return;
-    // C (n x n, full) += alpha W^T W, W: K x n; the split operand is W^T (n rows of length K),
-    // in pieces of at most 16,352 along K
-    constexpr int KMAX = oz::MAX_CHUNKS * oz::TK;
-    int kmax = 0;
-    for (auto v : Wb.h_n) kmax = std::max(kmax, v);
-    oz::Workspace ws;
-    for (int k0 = 0; k0 < kmax; k0 += KMAX) {
-        std::vector<oz::SplitJob> sj;
-        std::vector<oz::GemmJob> gj;
-        int64_t h = 0, e = 0;
-        for (int64_t b = 0; b < Cb.count; b++) {
-            const int n = Cb.h_n[b], K = std::min(Wb.h_n[b] - k0, KMAX);
-            if (n <= 0 || K <= 0) continue;
-            const int64_t ld = Wb.h_ld[b];
-            const int64_t rs = w_rowmajor ? 1 : ld, ks = w_rowmajor ? ld : 1;   // W(k, i) at k*ks + i*rs
-            sj.push_back(oz::SplitJob{Wb.h_off[b] + (int64_t)k0 * ks, rs, ks, h, e, n, K});
-            gj.push_back(oz::GemmJob{h, h, e, e, Cb.h_off[b], 1, Cb.h_ld[b], n, n, K, 0, 0, 0});
-            h += oz::slice_halves(n, K);
-            e += oz::exp_ints(n);
-        }
-        if (gj.empty()) continue;
-        ws.reserve(h, e, s);
-        oz::split(base_W, sj, ws.sl.p, ws.ex.p, s);
-        oz::gemm(ws.sl.p, ws.ex.p, base_C, gj, alpha, 1.0, err, s);
+    // C (n x n, full) += alpha W^T W, W: K x n; the split operand is W^T (n rows of length K)
+    std::vector<oz::SplitJob> sj;
+    std::vector<oz::GemmJob> gj;
+    int64_t h = 0, e = 0;
+    for (int64_t b = 0; b < Cb.count; b++) {
+        const int n = Cb.h_n[b], K = Wb.h_n[b];
+        if (n <= 0 || K <= 0) continue;
+        const int64_t ld = Wb.h_ld[b];
+        const int64_t rs = w_rowmajor ? 1 : ld, ks = w_rowmajor ? ld : 1;   // W(k, i) at k*ks + i*rs
+        sj.push_back(oz::SplitJob{Wb.h_off[b], rs, ks, h, e, n, K});
+        gj.push_back(oz::GemmJob{h, h, e, e, Cb.h_off[b], 1, Cb.h_ld[b], n, n, K, 0, 0, 0});
+        h += oz::slice_halves(n, K);
+        e += oz::exp_ints(n);
     }
+    if (gj.empty()) return;
+    oz::Workspace ws;
+    ws.reserve(h, e, s);
+    oz::split(base_W, sj, ws.sl.p, ws.ex.p, s);
+    oz::gemm(ws.sl.p, ws.ex.p, base_C, gj, alpha, 1.0, err, s);
 }
 
 void transpose_batched(const double *base_S, const MatBatch &Sb, double *base_D, const MatBatch &Db,

@@ -224,177 +224,217 @@ __device__ __forceinline__ double i128_add_double(__int128 v, int e, double c) {
     return c + i128_to_double(v, e, false);
 }
 
-__global__ void __launch_bounds__(256, 1) k_gemm(const __half *sl, const int32_t *ex, double *C,
-                                                 const GemmJob *jobs, const int64_t *pre, int njobs, double alpha,
-                                                 double beta, int *err, const int32_t *skip) {
+// epilogue of one output: C = beta C + alpha 2^e sum_d 2^-8(d-2) S_d (S_2..S_6 exact, tail = S_7 +
+// S_8 / 256), the sum formed exactly as a 128-bit integer in units of 2^-48; with beta = 1 the old C
+// joins the integer sum exactly and the result is rounded once.  FP64 instructions are scarce on
+// this GPU: none in the common cases (alpha a power of two, beta 0 or 1).  Kept out of line: the
+// product loop's registers are not needed here.
+__device__ __noinline__ void store_out(double *cp, int32_t s2, int32_t s3, int32_t s4, int32_t s5, int32_t s6,
+                                       float tail, int e, double alpha, double beta) {
+    __int128 v = ((__int128)s2 << 48) + ((__int128)s3 << 40) + ((__int128)s4 << 32) + ((__int128)s5 << 24) +
+                 ((__int128)s6 << 16) + (__int128)__float2ll_rn(tail * 256.0f);
+    int e2;
+    const double fr = frexp(fabs(alpha), &e2);
+    if (fr != 0.5) {
+        const double val = alpha * i128_to_double(v, e, false);
+        *cp = (beta == 0.0) ? val : (beta == 1.0) ? *cp + val : fma(beta, *cp, val);
+        return;
+    }
+    if (alpha < 0.0) v = -v;
+    e += e2 - 1;
+    if (beta == 0.0) *cp = i128_to_double(v, e, false);
+    else if (beta == 1.0) *cp = i128_add_double(v, e, *cp);
+    else *cp = fma(beta, *cp, i128_to_double(v, e, false));
+}
+
+// 16 warps per CTA, warp tile 16 x 16 (one m16 tile, two n8 tiles): every slice's fragments
+// of a 16-wide K step fit in registers (56), with per-diagonal exact int32 sums for the diagonals
+// 2..6 and one FP32 sum for the two lowest-weight diagonals (S_7 + S_8 / 256, weights 2^-40 and
+// 2^-48 of the leading one: with at most 256 K steps per product its rounding stays below
+// 2^-75 of the leading unit times K, under the FP64 dot-product bound).
+constexpr int GW = 16;               // warps per CTA
+constexpr int GT = GW * 32;          // threads per CTA
+
+// A product tile: its job, 64-row tiles of C and the operands' slice blocks
+struct TileRef {
+    int job, tm, tn, c0, nch;
+    const __half *gA, *gB;
+    int64_t pA, pB;
+};
+
+__device__ __forceinline__ TileRef decode_tile(const __half *sl, const GemmJob *jobs, const int64_t *pre, int njobs,
+                                               int64_t t) {
+    TileRef r;
+    r.job = find_job(pre, njobs, t);
+    const GemmJob &J = jobs[r.job];
+    const int64_t local = t - pre[r.job];
+    const int tilesM = dcdiv(J.M, TM), tilesN = dcdiv(J.N, TM);
+    if (J.lower) tri_index(local, r.tm, r.tn);
+    else { r.tm = (int)(local / tilesN); r.tn = (int)(local % tilesN); }
+    const int ntot = dcdiv(max(J.ktot, 1), TK);          // chunks of the split operands
+    r.c0 = J.k0 / TK;                                    // this pass's chunk range
+    r.nch = dcdiv(max(J.K, 1), TK);
+    r.gA = sl + J.a_off + (int64_t)r.tm * ntot * BLK;
+    r.gB = sl + J.b_off + (int64_t)r.tn * ntot * BLK;
+    r.pA = (int64_t)tilesM * ntot * BLK;
+    r.pB = (int64_t)tilesN * ntot * BLK;
+    return r;
+}
+
+// Persistent: CTA b takes tiles b, b + grid, ... (tiles of skipped jobs left out); thread 0 keeps
+// the bulk-copy ring NST chunks ahead across tile boundaries, so the next tile's operands arrive
+// while the current tile's epilogue runs.
+__global__ void __launch_bounds__(GT, 1) k_gemm(const __half *sl, const int32_t *ex, double *C,
+                                                const GemmJob *jobs, const int64_t *pre, int njobs, double alpha,
+                                                double beta, int *err, const int32_t *skip) {
     extern __shared__ __align__(1024) unsigned char smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + NST * STAGE_BYTES);
     __shared__ int s_bad;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int j = find_job(pre, njobs, blockIdx.x);
-    const GemmJob J = jobs[j];
-    if (skip && skip[J.skip_idx] >= 0) return;
-    const int64_t local = blockIdx.x - pre[j];
-    const int tilesM = dcdiv(J.M, TM), tilesN = dcdiv(J.N, TM);
-    int tm, tn;
-    if (J.lower) tri_index(local, tm, tn);
-    else { tm = (int)(local / tilesN); tn = (int)(local % tilesN); }
-    const int nch = dcdiv(max(J.K, 1), TK);
-    const __half *gA = sl + J.a_off + (int64_t)tm * nch * BLK;
-    const __half *gB = sl + J.b_off + (int64_t)tn * nch * BLK;
-    const int64_t pA = (int64_t)tilesM * nch * BLK, pB = (int64_t)tilesN * nch * BLK;
+    const int64_t total = pre[njobs];
+    auto active = [&](int64_t t) {
+        if (!skip) return true;
+        return skip[jobs[find_job(pre, njobs, t)].skip_idx] < 0;
+    };
     if (tid == 0) {
         for (int st = 0; st < NST; st++) mbar_init(&full[st], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_bad = 0;
     }
     __syncthreads();
-    auto issue = [&](int c) {
-        const int st = c % NST;
+    // producer state (thread 0, kept in shared memory to spare registers): the next (tile, chunk)
+    // to stage and the number of chunks staged so far
+    __shared__ int64_t s_ptile, s_issued;
+    __shared__ int s_pchunk;
+    __shared__ TileRef s_pref;
+    auto prod_advance_tile = [&]() {
+        int64_t t = s_ptile;
+        while (t < total && !active(t)) t += gridDim.x;
+        s_ptile = t;
+        if (t < total) s_pref = decode_tile(sl, jobs, pre, njobs, t);
+    };
+    auto issue_next = [&]() {
+        if (s_ptile >= total) return;
+        const int st = (int)(s_issued % NST);
         unsigned char *sb = smem + st * STAGE_BYTES;
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_expect_tx(&full[st], STAGE_BYTES);
+        const TileRef &P = s_pref;
+        const int64_t cc = P.c0 + s_pchunk;
         for (int p = 0; p < NS; p++) {
-            bulk_g2s(sb + p * BLK * 2, gA + p * pA + (int64_t)c * BLK, BLK * 2, &full[st]);
-            bulk_g2s(sb + (NS + p) * BLK * 2, gB + p * pB + (int64_t)c * BLK, BLK * 2, &full[st]);
+            bulk_g2s(sb + p * BLK * 2, P.gA + p * P.pA + cc * BLK, BLK * 2, &full[st]);
+            bulk_g2s(sb + (NS + p) * BLK * 2, P.gB + p * P.pB + cc * BLK, BLK * 2, &full[st]);
+        }
+        s_issued++;
+        if (++s_pchunk == P.nch) {
+            s_pchunk = 0;
+            s_ptile += gridDim.x;
+            prod_advance_tile();
         }
     };
-    if (tid == 0)
-        for (int c = 0; c < NST && c < nch; c++) issue(c);
+    if (tid == 0) {
+        s_ptile = blockIdx.x;
+        s_issued = 0;
+        s_pchunk = 0;
+        prod_advance_tile();
+        for (int k = 0; k < NST; k++) issue_next();
+    }
 
-    const int wm = warp >> 2, wn = warp & 3;     // warp tile: rows wm*32.., cols wn*16..
-    // exact integer sums of the diagonals: hi = S_2 2^16 + S_3 2^8 + S_4 and lo = S_5 2^16 +
-    // S_6 2^8 + S_7 (int64; each S_d stays below 2^31 for K <= 16352); the lowest-weight diagonal
-    // (2^-48 of the leading one) goes to an FP32 sum, whose rounding stays below 2^-70 of it
-    int64_t hi[2][2][4], lo[2][2][4];
-    float tail[2][2][4];
-#pragma unroll
-    for (int a = 0; a < 2; a++)
+    const int wm = warp >> 2, wn = warp & 3;     // warp tile: rows wm*16.., cols wn*16..
+    // ldmatrix row / 16-byte chunk of this lane: the A tile (16 rows x 16 k), the B pair of n8 tiles
+    const int arow = lane & 15, akc = lane >> 4;
+    const int brow = ((lane >> 4) << 3) + (lane & 7), bkc = (lane >> 3) & 1;
+    constexpr int NI = ND - 3;                   // exact int32 diagonals 2 .. 6
+    int64_t consumed = 0;
+    for (int64_t tile = blockIdx.x; tile < total; tile += gridDim.x) {
+        if (!active(tile)) continue;
+        const TileRef T = decode_tile(sl, jobs, pre, njobs, tile);
+        const GemmJob &J = jobs[T.job];
+        int32_t iacc[NI][2][4];
+        float tail[2][4];
 #pragma unroll
         for (int b = 0; b < 2; b++)
 #pragma unroll
             for (int q = 0; q < 4; q++) {
-                tail[a][b][q] = 0.f;
-                hi[a][b][q] = 0;
-                lo[a][b][q] = 0;
+                tail[b][q] = 0.f;
+#pragma unroll
+                for (int d = 0; d < NI; d++) iacc[d][b][q] = 0;
             }
-    // ldmatrix row / 16-byte chunk of this lane: A tiles (16 rows x 16 k), B pair of n8 tiles
-    const int arow = lane & 15, akc = lane >> 4;
-    const int brow = ((lane >> 4) << 3) + (lane & 7), bkc = (lane >> 3) & 1;
-
-    for (int c = 0; c < nch; c++) {
-        const int st = c % NST;
-        const uint32_t parity = (uint32_t)((c / NST) & 1);
-        if (tid == 0 && !mbar_wait_bounded(&full[st], parity, 2000000000ull)) s_bad = 1;
-        __syncthreads();
-        if (s_bad) {
-            if (tid == 0) {
-                flag_error(err, LSAMG_DEVICE_TIMEOUT, (int)blockIdx.x);
-                // let the copies already in flight land before the CTA's shared memory is released
-                for (int c2 = c; c2 < nch && c2 < c + NST; c2++)
-                    mbar_wait_bounded(&full[c2 % NST], (uint32_t)((c2 / NST) & 1), 1000000000ull);
-            }
-            return;
-        }
-        mbar_wait_bounded(&full[st], parity, 1000000000ull);   // completed: returns at once
-        const uint32_t sA = smem_u32(smem + st * STAGE_BYTES);
-        const uint32_t sB = sA + NS * BLK * 2;
-        // per 16-wide K step: every slice's fragments once into registers, then the 28 slice
-        // products diagonal by diagonal, each diagonal's FP32 sum moved out exactly after the step
-#pragma unroll
-        for (int ks = 0; ks < 2; ks++) {
-            uint32_t af[NS][2][4], bf[NS][4];
-#pragma unroll
-            for (int p = 0; p < NS; p++) {
-#pragma unroll
-                for (int mt = 0; mt < 2; mt++) {
-                    const int r = wm * 32 + mt * 16 + arow, kc = ks * 2 + akc;
-                    ldsm_x4(af[p][mt], sA + p * BLK * 2 + r * 64 + ((((kc ^ (r >> 1)) & 3)) << 4));
+        for (int c = 0; c < T.nch; c++, consumed++) {
+            const int st = (int)(consumed % NST);
+            const uint32_t parity = (uint32_t)((consumed / NST) & 1);
+            if (tid == 0 && !mbar_wait_bounded(&full[st], parity, 2000000000ull)) s_bad = 1;
+            __syncthreads();
+            if (s_bad) {
+                if (tid == 0) {
+                    flag_error(err, LSAMG_DEVICE_TIMEOUT, (int)blockIdx.x);
+                    // let the copies already in flight land before the CTA's shared memory is released
+                    for (int64_t g2 = consumed; g2 < s_issued; g2++)
+                        mbar_wait_bounded(&full[g2 % NST], (uint32_t)((g2 / NST) & 1), 1000000000ull);
                 }
-                const int r = wn * 16 + brow, kc = ks * 2 + bkc;
-                ldsm_x4(bf[p], sB + p * BLK * 2 + r * 64 + ((((kc ^ (r >> 1)) & 3)) << 4));
+                return;
             }
+            mbar_wait_bounded(&full[st], parity, 1000000000ull);   // completed: returns at once
+            const uint32_t sA = smem_u32(smem + st * STAGE_BYTES);
+            const uint32_t sB = sA + NS * BLK * 2;
+#pragma unroll 1
+            for (int ks = 0; ks < 2; ks++) {
+                // every A slice's fragment stays in registers for the step; a B fragment is read from
+                // shared memory for each slice pair that uses it
+                uint32_t af[NS][4];
 #pragma unroll
-            for (int d = 2; d <= ND; d++) {
-                float acc[2][2][4];
+                for (int p = 0; p < NS; p++) {
+                    const int r = wm * 16 + arow, kc = ks * 2 + akc;
+                    ldsm_x4(af[p], sA + p * BLK * 2 + r * 64 + ((((kc ^ (r >> 1)) & 3)) << 4));
+                }
+                const int br = wn * 16 + brow, bkk = ks * 2 + bkc;
+                const uint32_t boff = br * 64 + ((((bkk ^ (br >> 1)) & 3)) << 4);
 #pragma unroll
-                for (int a = 0; a < 2; a++)
+                for (int d = 2; d <= ND; d++) {
+                    float acc[2][4];
 #pragma unroll
                     for (int b = 0; b < 2; b++)
 #pragma unroll
-                        for (int q = 0; q < 4; q++) acc[a][b][q] = 0.f;
+                        for (int q = 0; q < 4; q++) acc[b][q] = 0.f;
 #pragma unroll
-                for (int p = 1; p <= NS; p++) {
-                    const int q = d - p;
-                    if (q < 1 || q > NS) continue;
+                    for (int p = 1; p <= NS; p++) {
+                        const int q = d - p;
+                        if (q < 1 || q > NS) continue;
+                        uint32_t bf[4];
+                        ldsm_x4(bf, sB + (q - 1) * BLK * 2 + boff);
 #pragma unroll
-                    for (int mt = 0; mt < 2; mt++)
-#pragma unroll
-                        for (int nt = 0; nt < 2; nt++)
-                            mma16816(acc[mt][nt], af[p - 1][mt], bf[q - 1][2 * nt], bf[q - 1][2 * nt + 1]);
-                }
-                // exact FP32 -> int32 (the sums are integers below 2^22 in magnitude), or the tail
-#pragma unroll
-                for (int a = 0; a < 2; a++)
+                        for (int nt = 0; nt < 2; nt++) mma16816(acc[nt], af[p - 1], bf[2 * nt], bf[2 * nt + 1]);
+                    }
+                    // exact FP32 -> int32 (the sums are integers below 2^21 in magnitude), or the tail
 #pragma unroll
                     for (int b = 0; b < 2; b++)
 #pragma unroll
                         for (int q = 0; q < 4; q++) {
-                            if (d == ND) {
-                                tail[a][b][q] += acc[a][b][q];
-                            } else {
-                                const int64_t v = (int64_t)(__float_as_int(acc[a][b][q] + 12582912.0f) - 0x4B400000);
-                                const int sh = 8 * ((4 - d + 3 * 8) % 3);   // d = 2,5 -> 16; 3,6 -> 8; 4,7 -> 0
-                                if (d <= 4) hi[a][b][q] += v << sh;
-                                else lo[a][b][q] += v << sh;
-                            }
+                            if (d - 2 < NI)
+                                iacc[d - 2][b][q] += __float_as_int(acc[b][q] + 12582912.0f) - 0x4B400000;
+                            else if (d == ND - 1)
+                                tail[b][q] += acc[b][q];
+                            else
+                                tail[b][q] = fmaf(acc[b][q], 1.0f / 256.0f, tail[b][q]);
                         }
+                }
             }
+            __syncthreads();   // every warp is done with this stage
+            if (tid == 0) issue_next();
         }
-        __syncthreads();   // every warp is done with this stage
-        if (tid == 0 && c + NST < nch) issue(c + NST);
-    }
-    // epilogue: C = beta C + alpha 2^(ea + eb - 14) sum_d 2^-8(d-2) S_d, the sum formed exactly as
-    // a 128-bit integer in units of 2^-48; with beta = 1 the old C joins the integer sum exactly
-    // and the result is rounded once.  FP64 instructions are scarce on this GPU: none in the common
-    // cases (alpha a power of two, beta 0 or 1)
-    const int g = lane >> 2, tg = lane & 3;
-    int ash = 0;
-    bool aneg = alpha < 0.0, apow2 = false;
-    {
-        int e2;
-        const double fr = frexp(fabs(alpha), &e2);
-        if (fr == 0.5) { apow2 = true; ash = e2 - 1; }
-    }
-    const int bmode = (beta == 0.0) ? 0 : (beta == 1.0) ? 1 : 2;
-#pragma unroll
-    for (int mt = 0; mt < 2; mt++)
+        const int g = lane >> 2, tg = lane & 3;
 #pragma unroll
         for (int nt = 0; nt < 2; nt++)
 #pragma unroll
             for (int q = 0; q < 4; q++) {
-                const int i = tm * TM + wm * 32 + mt * 16 + g + ((q >> 1) << 3);
-                const int jj = tn * TM + wn * 16 + nt * 8 + 2 * tg + (q & 1);
+                const int i = T.tm * TM + wm * 16 + g + ((q >> 1) << 3);
+                const int jj = T.tn * TM + wn * 16 + nt * 8 + 2 * tg + (q & 1);
                 if (i >= J.M || jj >= J.N || (J.lower && i < jj)) continue;
-                __int128 v = ((__int128)hi[mt][nt][q] << 32) + ((__int128)lo[mt][nt][q] << 8) +
-                             (__int128)__float2int_rn(tail[mt][nt][q]);
-                int e = ex[J.a_exp + i] + ex[J.b_exp + jj] - 62;
-                double *cp = C + J.c_off + (int64_t)i * J.crs + (int64_t)jj * J.ccs;
-                if (!apow2) {
-                    const double val = alpha * i128_to_double(v, e, false);
-                    *cp = (bmode == 0) ? val : (bmode == 1) ? *cp + val : fma(beta, *cp, val);
-                    continue;
-                }
-                if (aneg) v = -v;
-                e += ash;
-                if (bmode == 0) {
-                    *cp = i128_to_double(v, e, false);
-                } else if (bmode == 1) {
-                    *cp = i128_add_double(v, e, *cp);
-                } else {
-                    *cp = fma(beta, *cp, i128_to_double(v, e, false));
-                }
+                store_out(C + J.c_off + (int64_t)i * J.crs + (int64_t)jj * J.ccs, iacc[0][nt][q], iacc[1][nt][q],
+                          iacc[2][nt][q], iacc[3][nt][q], iacc[4][nt][q], tail[nt][q],
+                          ex[J.a_exp + i] + ex[J.b_exp + jj] - 62, alpha, beta);
             }
+    }
 }
 
 // one device upload of a job array and the exclusive prefix of its CTA counts
@@ -422,7 +462,6 @@ void split(const double *src, const std::vector<SplitJob> &jobs, __half *dst, in
     static_assert(sizeof(SplitJob) % 8 == 0, "job layout");
     std::vector<int64_t> cnt(jobs.size());
     for (size_t i = 0; i < jobs.size(); i++) {
-        if (cdiv(std::max(jobs[i].K, 1), TK) > MAX_CHUNKS) fail(LSAMG_LIMIT, "tensor-core product longer than 16352");
         cnt[i] = jobs[i].rows > 0 ? cdiv(jobs[i].rows, TM) : 0;
     }
     DBuf<int64_t> buf;
@@ -442,28 +481,48 @@ void gemm(const __half *slices, const int32_t *exps, double *C, const std::vecto
           double beta, int *err, cudaStream_t s, const int32_t *skip) {
     if (jobs.empty()) return;
     static_assert(sizeof(GemmJob) % 8 == 0, "job layout");
-    std::vector<int64_t> cnt(jobs.size());
-    for (size_t i = 0; i < jobs.size(); i++) {
-        const GemmJob &J = jobs[i];
-        if (J.M <= 0 || J.N <= 0) { cnt[i] = 0; continue; }
-        if (cdiv(std::max(J.K, 1), TK) > MAX_CHUNKS) fail(LSAMG_LIMIT, "tensor-core product longer than 16352");
-        const int64_t tm = cdiv(J.M, TM), tn = cdiv(J.N, TM);
-        if (J.lower && tm != tn) fail(LSAMG_INVALID_ARG, "lower-triangular product of a non-square block");
-        cnt[i] = J.lower ? tm * (tm + 1) / 2 : tm * tn;
-    }
-    DBuf<int64_t> buf;
-    const GemmJob *dj = nullptr;
-    const int64_t *dp = nullptr;
-    const int64_t total = upload_jobs(jobs, cnt, buf, dj, dp, s);
-    if (total == 0) return;
-    if (total > 0x7fffffff) fail(LSAMG_LIMIT, "product grid too large");
+    static_assert(KPIECE % TK == 0, "K pieces are whole chunks");
+    int npieces = 1;
+    for (const auto &J : jobs) npieces = std::max<int>(npieces, (int)cdiv(std::max(J.K, 1), KPIECE));
     CK(cudaFuncSetAttribute(k_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM));
-    double fl = 0.0;   // FP64-equivalent flops of the products (lower: the triangle only)
-    for (const auto &J : jobs) fl += (J.lower ? 1.0 : 2.0) * J.M * (double)J.N * J.K;
-    KTime kt(KC_TC_GEMM, s, fl);
-    k_gemm<<<(unsigned)total, 256, GEMM_SMEM, s>>>(slices, exps, C, dj, dp, (int)jobs.size(), alpha, beta, err,
-                                                   skip);
-    CK_LAUNCH();
+    for (int pc = 0; pc < npieces; pc++) {
+        // pass pc: the pc-th K piece of every job (C accumulates from the second pass on)
+        std::vector<GemmJob> js;
+        std::vector<int64_t> cnt;
+        for (const auto &J0 : jobs) {
+            if (J0.M <= 0 || J0.N <= 0) continue;
+            const int64_t k0 = (int64_t)pc * KPIECE;
+            if (pc > 0 && k0 >= J0.K) continue;
+            GemmJob J = J0;
+            J.ktot = J0.K;
+            J.k0 = (int32_t)k0;
+            J.K = (int32_t)std::min<int64_t>(KPIECE, std::max<int64_t>(J0.K - k0, 0));
+            const int64_t tm = cdiv(J.M, TM), tn = cdiv(J.N, TM);
+            if (J.lower && tm != tn) fail(LSAMG_INVALID_ARG, "lower-triangular product of a non-square block");
+            js.push_back(J);
+            cnt.push_back(J.lower ? tm * (tm + 1) / 2 : tm * tn);
+        }
+        if (js.empty()) continue;
+        DBuf<int64_t> buf;
+        const GemmJob *dj = nullptr;
+        const int64_t *dp = nullptr;
+        const int64_t total = upload_jobs(js, cnt, buf, dj, dp, s);
+        if (total == 0) continue;
+        if (total > 0x7fffffff) fail(LSAMG_LIMIT, "product grid too large");
+        double fl = 0.0;   // FP64-equivalent flops of the products (lower: the triangle only)
+        for (const auto &J : js) fl += (J.lower ? 1.0 : 2.0) * J.M * (double)J.N * J.K;
+        KTime kt(KC_TC_GEMM, s, fl);
+        static int sms = 0;
+        if (!sms) {
+            int dev = 0;
+            CK(cudaGetDevice(&dev));
+            CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        }
+        const unsigned grid = (unsigned)std::min<int64_t>(total, sms);
+        k_gemm<<<grid, GT, GEMM_SMEM, s>>>(slices, exps, C, dj, dp, (int)js.size(), alpha, pc == 0 ? beta : 1.0, err,
+                                          skip);
+        CK_LAUNCH();
+    }
 }
 
 }  // namespace oz

@@ -37,7 +37,7 @@ constexpr int TK = 32;             // K chunk
 constexpr int BLK = TM * TK;       // halves per block (4 KB)
 constexpr int NS = 7;              // slices per operand entry
 constexpr int ND = 8;              // highest kept diagonal p + q
-constexpr int MAX_CHUNKS = 511;    // K chunks per product (int32 headroom)
+constexpr int KPIECE = 4096;       // longest K of one kernel pass (longer products run in pieces)
 
 // One operand: `rows` rows of length K; element (i, k) at src[src_off + i * rs + k * ks].
 struct SplitJob {
@@ -56,6 +56,7 @@ struct GemmJob {
     int64_t c_off, crs, ccs;
     int32_t M, N, K, lower;
     int32_t skip_idx, pad_;      // the job is skipped when skip != nullptr and skip[skip_idx] >= 0
+    int32_t k0 = 0, ktot = 0;    // set by gemm(): this piece's first K index and the operands' K
 };
 
 // Slice storage needed for an operand of `rows` x K: (halves, exponent ints).

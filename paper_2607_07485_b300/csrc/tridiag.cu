@@ -64,6 +64,7 @@ __global__ void __launch_bounds__(RB) k_trd_c1(double *base, const int64_t *off,
     double sq = 0.0;
     if (r < n) {
         double a = A[r + (int64_t)j * L];
+#pragma unroll 8
         for (int q = 0; q < jj; q++) a -= V[r + (int64_t)q * n] * wj[q] + W[r + (int64_t)q * n] * vj[q];
         A[r + (int64_t)j * L] = a;
         if (r >= j + 2) sq = a * a;
@@ -174,6 +175,7 @@ __global__ void __launch_bounds__(RB) k_trd_c3(double *base, const int64_t *off,
     double *pp = part + partoff[b] + (int64_t)blockIdx.x * PSL;
     for (int q = warp; q < jj; q += nwarp) {
         double a1 = 0.0, a2 = 0.0;
+#pragma unroll 8
         for (int i = lane; i < RB; i += 32) {
             const int rr = r0 + i;
             if (rr < n) {
@@ -229,12 +231,22 @@ __global__ void __launch_bounds__(256) k_trd_symv(const double *base, const int6
         const double *A22 = base + off[b] + (j + 1) + (int64_t)(j + 1) * L;
         const double *v = vbuf + toff[b] + (j + 1);
         const int r0 = ti * ST, c0 = tj * ST;
-        for (int t = threadIdx.x; t < ST * ST; t += blockDim.x) {
-            const int rr = t % ST, cc = t / ST;
-            const int gr = r0 + rr, gc = c0 + cc;
-            double a = 0.0;
-            if (gr < m && gc < m && gr >= gc) a = A22[gr + (int64_t)gc * L];
-            tile[rr][cc] = a;
+        {
+            // all 16 loads of a thread in flight before any shared-memory store
+            constexpr int PER = ST * ST / 256;
+            double a[PER];
+#pragma unroll
+            for (int u = 0; u < PER; u++) {
+                const int t = threadIdx.x + 256 * u;
+                const int rr = t % ST, cc = t / ST;
+                const int gr = r0 + rr, gc = c0 + cc;
+                a[u] = (gr < m && gc < m && gr >= gc) ? A22[gr + (int64_t)gc * L] : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < PER; u++) {
+                const int t = threadIdx.x + 256 * u;
+                tile[t % ST][t / ST] = a[u];
+            }
         }
         for (int t = threadIdx.x; t < ST; t += blockDim.x) {
             vr[t] = (r0 + t < m) ? v[r0 + t] : 0.0;
@@ -309,7 +321,9 @@ __global__ void __launch_bounds__(RB) k_trd_w2(const int32_t *nn, int64_t count,
     if (r < n) {
         const int i = r - j - 1, ti = i / ST, rr = i % ST;
         double y = 0.0;
+#pragma unroll 8
         for (int t = 0; t < T; t++) y += Pb[((int64_t)ti * T + t) * ST + rr];
+#pragma unroll 8
         for (int q = 0; q < jj; q++) y -= V[r + (int64_t)q * n] * s1[q] + W[r + (int64_t)q * n] * s2[q];
         y *= tau;
         ybuf[toff[b] + r] = y;

@@ -688,3 +688,42 @@ def test_exact_splitting_needs_the_g_row_closure(cg1_closures):
             total[np.ix_(loc, loc)] += Hm.T @ Hm
         errs.append(abs(total - Ad).max() / abs(Ad).max())
     assert errs[0] <= 1e-12 and errs[1] >= 1e-3
+
+
+def test_fcg_equals_pcg_with_a_fixed_spd_preconditioner():
+    # with a fixed SPD preconditioner the Polak-Ribiere coefficient of flexible CG(1) equals the
+    # Fletcher-Reeves one of PCG in exact arithmetic (z_{k+1}^T r_k = 0), so the iterates coincide;
+    # a sign or index slip in either beta breaks the agreement
+    rng = np.random.default_rng(41)
+    n = 60
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    A = (Q * np.logspace(0, 2, n)) @ Q.T
+    R = rng.standard_normal((n, n)) / np.sqrt(n)
+    M = np.linalg.inv(A + 3.0 * R @ R.T)    # SPD preconditioner, kappa(M A) ~ 10: few iterations
+    b = rng.standard_normal(n)
+    xp, ip, hp = O.pcg(lambda v: A @ v, b, lambda r: M @ r, rtol=1e-10)
+    xf, itf, hf = O.fcg(lambda v: A @ v, b, lambda r: M @ r, rtol=1e-10)
+    assert ip < n // 2
+    assert ip == itf
+    np.testing.assert_allclose(hf, hp, rtol=1e-6, atol=1e-14)
+    assert np.linalg.norm(xf - xp) <= 1e-10 * np.linalg.norm(xp)
+    # and both reach the exact solution
+    assert np.linalg.norm(xp - np.linalg.solve(A, b)) <= 1e-9 * np.linalg.norm(xp)
+
+
+def test_fp32_emulated_cycle_within_rounding_of_fp64():
+    # the FP32-emulated V-cycle is the FP64 cycle's operator up to FP32 rounding: on a
+    # well-conditioned tiny case its output differs by more than FP64 rounding (it does round)
+    # and by less than 64 eps_32 kappa(A) (the forward error of the perturbed local solves)
+    n, d, K = fegen.rt_quad(4, 1, 1.0)
+    mats = np.ascontiguousarray(np.broadcast_to(K, (d.shape[0],) + K.shape))
+    H = O.setup(n, d, mats, opts=dict(agg_passes=1, agg_passes_coarse=1, max_density=1.0))
+    A = H.levels[0].A.toarray()
+    ev = np.linalg.eigvalsh(A)
+    kappa = ev[-1] / ev[0]
+    r = np.random.default_rng(42).standard_normal(n)
+    z64 = O.vcycle(H, r)
+    z32 = O.vcycle(H, r, np.float32).astype(np.float64)
+    rel = np.linalg.norm(z32 - z64) / np.linalg.norm(z64)
+    eps32 = np.finfo(np.float32).eps
+    assert 100 * np.finfo(float).eps < rel <= 64 * eps32 * kappa, (rel, kappa)
