@@ -85,7 +85,38 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--oracle-sample", type=int, default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--closure-sweep", type=str, default=None, metavar="N,N,...",
+                    help="instead of the benchmark: stationary V-cycle iterations with the G-row and "
+                         "the A-closure on CG1 triangles of these mesh sizes (the Table 2 comparison), "
+                         "one JSON line per size and closure")
     return ap.parse_args()
+
+
+def closure_sweep(sizes):
+    """Table 2 set-up: CG1 right triangles, kappa = 1 + x + y, Nitsche u = 0, tau_cut = max mult
+    (c = 1), b = 0, random x0, stationary V-cycle to a 1e-10 residual reduction."""
+    import torch
+    import fegen
+    from paper_2607_07485_b300 import Lsamg
+    dev = torch.device("cuda", 0)
+    for N in sizes:
+        n, d, K = fegen.cg1_tri(N)
+        dofs, mats = torch.from_numpy(d).to(dev), torch.from_numpy(np.ascontiguousarray(K)).to(dev)
+        x0 = torch.from_numpy(np.random.default_rng(N).uniform(-1, 1, n)).to(dev)
+        b = torch.zeros(n, dtype=torch.float64, device=dev)
+        for closure in ("G", "A"):
+            t0 = time.perf_counter()
+            amg = Lsamg(n, dofs, mats, tau_c=1.0, closure=closure, rtol=1e-10, maxit=1000)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            _, its, rel, rc = amg.solve(b, x0=x0.clone(), mode=2)
+            torch.cuda.synchronize()
+            st = amg.stats()
+            print(json.dumps(dict(mesh=N, dofs=n, closure=closure, iterations=int(its[0]),
+                                  converged=rc == 0, relres=float(rel[0]), levels=st["n"],
+                                  setup_s=round(t1 - t0, 3), solve_s=round(time.perf_counter() - t1, 3))),
+                  flush=True)
+            amg.close()
 
 
 # ----------------------------------------------------------------------------- helpers
@@ -289,6 +320,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.closure_sweep:
+        closure_sweep([int(v) for v in args.closure_sweep.split(",")])
         return
     import torch
     import torch.distributed as dist

@@ -89,6 +89,13 @@ typedef struct {
     int32_t smoother;            /* 0: multiplicative Schwarz, colour-ordered (the paper's tests);
                                     1: additive Schwarz over all subdomains at once, damped by
                                     1 / #colours (the parallel block smoother Section 2 allows) */
+    int32_t closure;             /* overlaps Omega_i: 0: G-row closure (Def. 5.3; eq. 2.4, the paper's
+                                    method); 1: algebraic A-closure (Def. 5.2): omega_i and every p
+                                    with an assembled entry A(q, p) != 0 for some q in omega_i,
+                                    entries summed over the elements in ascending element order and
+                                    compared with exact zero.  Element DOFs outside Omega_i^A are
+                                    left out of the local matrices, so the splitting of Thm 5.6 need
+                                    not hold (the Table 2 comparison) */
 } lsamg_options;
 
 lsamg_options lsamg_options_default(void);

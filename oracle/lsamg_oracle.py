@@ -250,9 +250,14 @@ def closure(elems, agg, nagg, A=None):
     mult(j) = mult(T) = #aggregates meeting N(T) (eq. 2.5).
 
     With the assembled matrix A given, Omega_i is instead the algebraic A-closure of
-    Section 5 (Def. of Omega^A): omega_i together with every p whose row block A(p, omega_i)
-    has a nonzero entry after assembly (exact zeros from cancellation excluded).  Only the
-    closure changes; rows touching omega_i and multiplicities stay those of eqs. 2.3-2.5.
+    Section 5 (Def. of Omega^A): omega_i together with every p such that A(q, p) is nonzero
+    for some q in omega_i.  Reading of "nonzero" (the paper removes cancelled entries and
+    notes that zero or near-zero entries are commonly dropped from the graph of A): an
+    entry counts when |A(q, p)| > ACUT sqrt(|A(q, q)| |A(p, p)|).  Entries that cancel in
+    exact arithmetic are exact zeros on the finest level (orthogonal gradients) but carry
+    rounding after the Galerkin products of coarser levels; the relative cut treats both as
+    zero.  Only the closure changes; rows touching omega_i and multiplicities stay those of
+    eqs. 2.3-2.5.
 
     Returns (eagg, mult, ael, omega, Omega)."""
     eagg = [np.unique(agg[np.asarray(d, np.int64)]) for d in elems]
@@ -268,10 +273,12 @@ def closure(elems, agg, nagg, A=None):
     omega = [order[starts[i]:starts[i + 1]] for i in range(nagg)]
     Omega = []
     if A is not None:
-        An = sp.csr_matrix(A, copy=True)
-        An.eliminate_zeros()
+        Ac = sp.coo_matrix(A)
+        dg = np.abs(sp.csr_matrix(A).diagonal())
+        keep = np.abs(Ac.data) > ACUT * np.sqrt(dg[Ac.row] * dg[Ac.col])
+        Ak = sp.csr_matrix((np.ones(int(keep.sum())), (Ac.row[keep], Ac.col[keep])), shape=A.shape)
         for i in range(nagg):
-            nb = An[omega[i]].indices
+            nb = Ak[omega[i]].indices
             Omega.append(np.union1d(np.asarray(omega[i], np.int64), nb.astype(np.int64)))
         return eagg, mult, ael, omega, Omega
     for i in range(nagg):
@@ -316,6 +323,7 @@ def pinv_sym(M):
     return (V[:, keep] / w[keep]) @ V[:, keep].T
 
 
+ACUT = 1e-12  # reading: relative size below which an assembled entry counts as zero (A-closure)
 TIE = 1e-9  # reading: keep mu*tau < 1 - TIE, so exact ties mu = 1/tau (from mesh symmetry) are
             # discarded deterministically; tau_max <= tau_cut is unaffected
 

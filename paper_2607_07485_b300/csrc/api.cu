@@ -180,6 +180,7 @@ void do_setup(Handle &H, const lsamg_problem *P, const lsamg_options &o) {
     if (o.max_levels < 1 || o.max_levels > 8) fail(LSAMG_INVALID_ARG, "max_levels must be in 1..8");
     if (o.sweep_block < 0 || o.sweep_block > 64) fail(LSAMG_INVALID_ARG, "sweep_block must be in 0..64");
     if (o.smoother != 0 && o.smoother != 1) fail(LSAMG_INVALID_ARG, "smoother must be 0 or 1");
+    if (o.closure != 0 && o.closure != 1) fail(LSAMG_INVALID_ARG, "closure must be 0 (G-row) or 1 (A)");
     H.err.alloc(2, s);
     H.err.zero(s);
     int *err = H.err.p;
@@ -250,7 +251,7 @@ void do_setup(Handle &H, const lsamg_problem *P, const lsamg_options &o) {
             st.stage_seconds[1] += now() - t;
             t = now();
             trace("level %d: closure (nagg %d)", l, L.nagg);
-            closure_level(L, o.tau_c, err, s);
+            closure_level(L, o.tau_c, o.closure, err, s);
             st.stage_seconds[2] += now() - t;
             t = now();
             trace("level %d: local spectral", l);
@@ -620,6 +621,7 @@ lsamg_options lsamg_options_default(void) {
     o.split_sweep = 0;
     o.sweep_block = 0;
     o.smoother = 0;
+    o.closure = 0;
     return o;
 }
 

@@ -352,6 +352,81 @@ __global__ void k_olpos(const int64_t *Optr, const int32_t *Oidx, const int64_t 
     }
 }
 
+// Algebraic A-closure (Def. 5.2).  Warp per DOF r: vals[j] = assembled A(r, q_j) over the
+// structural row pattern q_0 < q_1 < ... of r, summed over the elements T containing r in
+// ascending element order (element matrices column-major: A_T(i, c) at Ae[c * nT + i]).
+__global__ void k_row_values(const int64_t *sptr, const int32_t *sidx, int64_t n, const int64_t *dptr,
+                             const int32_t *didx, const int64_t *eptr, const int32_t *eidx,
+                             const double *AT, const int64_t *aoff, double *vals) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = w0; r < n; r += nwarp) {
+        const int32_t *pat = sidx + sptr[r];
+        const int64_t m = sptr[r + 1] - sptr[r];
+        double *v = vals + sptr[r];
+        for (int64_t t = lane; t < m; t += 32) v[t] = 0.0;
+        __syncwarp();
+        for (int64_t j = dptr[r]; j < dptr[r + 1]; j++) {
+            const int32_t e = didx[j];
+            const int64_t b = eptr[e];
+            const int nT = (int)(eptr[e + 1] - b);
+            int lr = -1;
+            for (int c0 = 0; c0 < nT && lr < 0; c0 += 32) {
+                const int c = c0 + lane;
+                const unsigned hit = __ballot_sync(0xffffffffu, c < nT && eidx[b + c] == (int32_t)r);
+                if (hit) lr = c0 + __ffs((int)hit) - 1;
+            }
+            if (lr < 0) continue;   // r is in N(T) by construction of the DOF -> element map
+            const double *Ae = AT + aoff[e];
+            for (int c = lane; c < nT; c += 32) {
+                const int64_t k = lower_bound_i32(pat, m, eidx[b + c]);
+                v[k] += Ae[(int64_t)c * nT + lr];     // DOFs of one element are distinct
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// |A(r, r)| of every row (0 when r is not in its own pattern)
+__global__ void k_row_diag(const int64_t *sptr, const int32_t *sidx, const double *vals, int64_t n,
+                           double *dg) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t m = sptr[r + 1] - sptr[r];
+        const int64_t k = lower_bound_i32(sidx + sptr[r], m, (int32_t)r);
+        dg[r] = (k < m && sidx[sptr[r] + k] == r) ? fabs(vals[sptr[r] + k]) : 0.0;
+    }
+}
+
+// entry (r, q) of the A pattern is kept when q == r (omega_i is in Omega_i^A whatever A(r, r)
+// is) or |A(r, q)| > cut sqrt(|A(r, r)| |A(q, q)|): entries that cancel in exact arithmetic
+// (exact zeros on the finest level, rounding after coarse Galerkin products) count as zero
+__device__ __forceinline__ bool a_kept(int64_t r, int32_t q, double v, const double *dg, double cut) {
+    return q == r || fabs(v) > cut * sqrt(dg[r] * dg[q]);
+}
+
+__global__ void k_nz_count(const int64_t *sptr, const int32_t *sidx, const double *vals,
+                           const double *dg, double cut, int64_t n, int64_t *cnt) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        int64_t c = 0;
+        for (int64_t j = sptr[r]; j < sptr[r + 1]; j++) c += a_kept(r, sidx[j], vals[j], dg, cut);
+        cnt[r] = c;
+    }
+}
+
+__global__ void k_nz_fill(const int64_t *sptr, const int32_t *sidx, const double *vals,
+                          const double *dg, double cut, int64_t n, const int64_t *nzptr,
+                          int32_t *nzidx) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        int64_t o = nzptr[r];
+        for (int64_t j = sptr[r]; j < sptr[r + 1]; j++)
+            if (a_kept(r, sidx[j], vals[j], dg, cut)) nzidx[o++] = sidx[j];
+    }
+}
+
 // per (aggregate, element meeting Omega) entry: offset of its local-position block
 __global__ void k_oeloc_count(const int64_t *oeptr, const int32_t *oeidx, int64_t nent,
                               const int64_t *eptr, int64_t *cnt) {
@@ -496,7 +571,42 @@ void aggregate_level(Level &L, int passes, int *err, cudaStream_t s) {
     check_err(err, s, "aggregation");
 }
 
-void closure_level(Level &L, double tau_c, int *err, cudaStream_t s) {
+// Relative size below which an assembled entry counts as zero in the A-closure.
+constexpr double kACut = 1e-12;
+
+// Omega_i^A = union over the rows r in omega_i of the kept entries of A(r, :) (Def. 5.2)
+static void a_closure(Level &L, DBuf<int64_t> &Optr, DBuf<int32_t> &Oidx, int *err, cudaStream_t s) {
+    const int64_t n = L.n;
+    DBuf<int64_t> sptr, nzptr, cnt;
+    DBuf<int32_t> sidx, nzidx;
+    csr_union(L.dptr.p, L.didx.p, n, L.eptr.p, L.eidx.p, sptr, sidx, err, s);   // structural rows
+    const int64_t nnz = read1(sptr.p + n, s);
+    DBuf<double> vals, dg;
+    vals.alloc(std::max<int64_t>(nnz, 1), s);
+    dg.alloc(std::max<int64_t>(n, 1), s);
+    cnt.alloc(std::max<int64_t>(n, 1), s);
+    if (n > 0) {
+        k_row_values<<<grid_for(n * 32), TPB, 0, s>>>(sptr.p, sidx.p, n, L.dptr.p, L.didx.p, L.eptr.p,
+                                                       L.eidx.p, L.AT.p, L.aoff.p, vals.p);
+        CK_LAUNCH();
+        k_row_diag<<<grid_for(n), TPB, 0, s>>>(sptr.p, sidx.p, vals.p, n, dg.p);
+        CK_LAUNCH();
+        k_nz_count<<<grid_for(n), TPB, 0, s>>>(sptr.p, sidx.p, vals.p, dg.p, kACut, n, cnt.p);
+        CK_LAUNCH();
+    }
+    nzptr.alloc(n + 1, s);
+    exclusive_scan_i64(cnt.p, nzptr.p, n, s);
+    const int64_t nzt = read1(nzptr.p + n, s);
+    nzidx.alloc(std::max<int64_t>(nzt, 1), s);
+    if (n > 0) {
+        k_nz_fill<<<grid_for(n), TPB, 0, s>>>(sptr.p, sidx.p, vals.p, dg.p, kACut, n, nzptr.p, nzidx.p);
+        CK_LAUNCH();
+    }
+    trace("  A pattern: %lld structural, %lld kept", (long long)nnz, (long long)nzt);
+    csr_union(L.wptr.p, L.widx.p, L.nagg, nzptr.p, nzidx.p, Optr, Oidx, err, s);
+}
+
+void closure_level(Level &L, double tau_c, int closure, int *err, cudaStream_t s) {
     const int64_t ne = L.ne, n = L.n, nagg = L.nagg;
     // eagg(T): sorted distinct aggregates met by N(T); mult(T) = |eagg(T)|   (eq. 2.5)
     {
@@ -535,14 +645,21 @@ void closure_level(Level &L, double tau_c, int *err, cudaStream_t s) {
             CK_LAUNCH();
         }
     }
-    // Omega_i = union of N(T) over elements touching omega_i (eq. 2.4 = element closure, Thm 5.6):
-    // per DOF q the aggregates whose overlap contains q, then transpose
+    // G-row closure: Omega_i = union of N(T) over elements touching omega_i (eq. 2.4 = element
+    // closure, Thm 5.6), built as per DOF q the aggregates whose overlap contains q, then
+    // transposed.  A-closure: Omega_i^A per aggregate, and its transpose.
     {
         DBuf<int64_t> qptr;
         DBuf<int32_t> qidx;
-        csr_union(L.dptr.p, L.didx.p, n, L.eaptr.p, L.eaidx.p, qptr, qidx, err, s);
-        int64_t tot = read1(qptr.p + n, s);
-        csr_transpose(qptr.p, qidx.p, n, tot, nagg, L.Optr, L.Oidx, err, s);
+        if (closure == 0) {
+            csr_union(L.dptr.p, L.didx.p, n, L.eaptr.p, L.eaidx.p, qptr, qidx, err, s);
+            int64_t tot = read1(qptr.p + n, s);
+            csr_transpose(qptr.p, qidx.p, n, tot, nagg, L.Optr, L.Oidx, err, s);
+        } else {
+            a_closure(L, L.Optr, L.Oidx, err, s);
+            int64_t tot = read1(L.Optr.p + nagg, s);
+            csr_transpose(L.Optr.p, L.Oidx.p, nagg, tot, n, qptr, qidx, err, s);
+        }
         int64_t nO = read1(L.Optr.p + nagg, s);
         trace("  Omega total %lld", (long long)nO);
         L.Olpos.alloc(std::max<int64_t>(nO, 1), s);

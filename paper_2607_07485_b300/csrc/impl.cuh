@@ -143,7 +143,7 @@ struct Handle {
 void check_input(const Level &L, int *err, cudaStream_t s);
 void build_dof_elem(Level &L, int *err, cudaStream_t s);
 void aggregate_level(Level &L, int passes, int *err, cudaStream_t s);
-void closure_level(Level &L, double tau_c, int *err, cudaStream_t s);
+void closure_level(Level &L, double tau_c, int closure, int *err, cudaStream_t s);
 void colour_level(Level &L, int *err, cudaStream_t s);
 int64_t structural_nnz_level0(Level &L, int *err, cudaStream_t s);
 int64_t structural_nnz_coarse(const Level &fine, int *err, cudaStream_t s);

@@ -175,9 +175,15 @@ __global__ void k_assemble_gep(const int32_t *alist, int64_t na, const int64_t *
         int64_t b = eptr[e];
         int n = (int)(eptr[e + 1] - b);
         int32_t *own = pos + n;
-        for (int t = threadIdx.x; t < n; t += blockDim.x) pos[t] = lp[lbound(Om, nO, eidx[b + t])];
+        for (int t = threadIdx.x; t < n; t += blockDim.x) {
+            // -1: an element DOF outside Omega_i (only under the A-closure, whose local
+            // matrices drop those rows and columns)
+            const int32_t q = eidx[b + t];
+            const int64_t k = lbound(Om, nO, q);
+            pos[t] = (k < nO && Om[k] == q) ? lp[k] : -1;
+        }
         __syncthreads();
-        warp_compact(n, own, &ncols, [&](int c) { return pos[c] % es == slice; });   // owned columns
+        warp_compact(n, own, &ncols, [&](int c) { return pos[c] >= 0 && pos[c] % es == slice; });
         __syncthreads();
         const double *Ae = AT + aoff[e];
         const double w = 1.0 / (double)mult[e];
@@ -186,6 +192,7 @@ __global__ void k_assemble_gep(const int32_t *alist, int64_t na, const int64_t *
             const int c = own[t / n], r = t % n;
             const double v = Ae[(int64_t)c * n + r];
             const int pr = pos[r], pc = pos[c];
+            if (pr < 0) continue;
             T1[pr + (int64_t)pc * nO] += w * v;
             if (pr < nw && pc < nw) T2[pr + (int64_t)pc * nw] += v;
         }

@@ -46,7 +46,7 @@ class Options(C.Structure):
                 ("vcycle_fp32", C.c_int32), ("maxit", C.c_int32), ("rtol", C.c_double),
                 ("chunk_bytes", C.c_int64), ("use_graph", C.c_int32), ("verbose", C.c_int32),
                 ("profile", C.c_int32), ("large_dense", C.c_int32), ("split_sweep", C.c_int32),
-                ("sweep_block", C.c_int32), ("smoother", C.c_int32)]
+                ("sweep_block", C.c_int32), ("smoother", C.c_int32), ("closure", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -179,6 +179,10 @@ def options(**kw) -> Options:
     for k, v in kw.items():
         if not hasattr(o, k):
             raise TypeError(f"unknown option {k}")
+        if k == "closure" and isinstance(v, str):
+            if v not in ("G", "A"):
+                raise ValueError(f"closure must be 'G' or 'A', not {v!r}")
+            v = 0 if v == "G" else 1
         setattr(o, k, v)
     return o
 

@@ -75,3 +75,12 @@ def test_new_option_defaults(lib):
     from paper_2607_07485_b300 import options
     o = options()
     assert o.smoother == 0 and o.sweep_block == 0 and o.split_sweep == 0 and o.use_graph == 0
+
+
+def test_closure_option(lib):
+    # 0 = G-row closure (the paper's method, the default), 1 = algebraic A-closure (Def. 5.2)
+    from paper_2607_07485_b300 import options
+    assert options().closure == 0
+    assert options(closure="A").closure == 1 and options(closure="G").closure == 0
+    with pytest.raises(ValueError):
+        options(closure="B")

@@ -46,7 +46,17 @@ CASES = {
     "cfg3_16": (lambda: _cfg(3, 16), dict(tau_c=1.0), 1e-6, 1e-4, BAND),
     "cfg5_16": (lambda: _cfg(5, 16), dict(), 1e-3, 1e-2, BAND),
     "cfg4_6": (lambda: _cfg(4, 6), dict(agg_passes=1, agg_passes_coarse=1), 1e-8, 1e-6, BAND),
+    # CG1 triangles, kappa = 1 + x + y, 1,089 DOFs, tau_cut = max mult (the Table 2 set-up) with
+    # the G-row closure and with the algebraic A-closure (Def. 5.2)
+    "cg1_G": (lambda: _cg1(32), dict(tau_c=1.0), 1e-8, 1e-6, BAND),
+    "cg1_A": (lambda: _cg1(32), dict(tau_c=1.0, closure="A"), 1e-8, 1e-6, BAND),
 }
+
+
+def _cg1(N):
+    n, d, K = fegen.cg1_tri(N)
+    rng = np.random.default_rng(7)
+    return dict(n=n, elem_dofs=d, mats=np.ascontiguousarray(K), b=rng.uniform(-1, 1, (1, n)))
 
 
 def _rt(N, k, beta):

@@ -671,6 +671,11 @@ def test_a_closure_definition_and_cut_by_cancellation(cg1_closures):
         w = np.asarray(omega[i])
         brute = sorted(set(w.tolist()) | {p for p in range(n) if p not in set(w.tolist()) and np.any(Ad[p, w] != 0)})
         assert list(OmA[i]) == brute
+    # on the finest level the relative cut and the exact-zero rule keep the same entries: the
+    # cancelled entries are exact zeros and no genuine coupling is within 1e-6 of the cut
+    dg = np.sqrt(np.abs(np.diag(Ad)))
+    rel = np.abs(Ad) / np.outer(dg, dg)
+    assert rel[Ad != 0].min() > 1e6 * OL.ACUT
     assert all(set(a.tolist()) <= set(g.tolist()) for a, g in zip(OmA, OmG))
     assert sum(len(g) - len(a) for a, g in zip(OmA, OmG)) > 0
 
