@@ -352,78 +352,110 @@ __global__ void k_olpos(const int64_t *Optr, const int32_t *Oidx, const int64_t 
     }
 }
 
-// Algebraic A-closure (Def. 5.2).  Warp per DOF r: vals[j] = assembled A(r, q_j) over the
-// structural row pattern q_0 < q_1 < ... of r, summed over the elements T containing r in
-// ascending element order (element matrices column-major: A_T(i, c) at Ae[c * nT + i]).
-__global__ void k_row_values(const int64_t *sptr, const int32_t *sidx, int64_t n, const int64_t *dptr,
-                             const int32_t *didx, const int64_t *eptr, const int32_t *eidx,
-                             const double *AT, const int64_t *aoff, double *vals) {
-    const int lane = threadIdx.x & 31;
-    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t r = w0; r < n; r += nwarp) {
-        const int32_t *pat = sidx + sptr[r];
-        const int64_t m = sptr[r + 1] - sptr[r];
-        double *v = vals + sptr[r];
-        for (int64_t t = lane; t < m; t += 32) v[t] = 0.0;
-        __syncwarp();
+// Algebraic A-closure (Def. 5.2), decided on the G-row closure Omega^G_i, which contains it
+// (an assembled entry A(q, p) needs an element holding both q and p).
+// |A(r, r)| of every DOF, summed over its elements in ascending element order
+__global__ void k_assembled_diag(const int64_t *dptr, const int32_t *didx, int64_t n, const int64_t *eptr,
+                                 const int32_t *eidx, const double *AT, const int64_t *aoff, double *dg) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        double v = 0.0;
         for (int64_t j = dptr[r]; j < dptr[r + 1]; j++) {
             const int32_t e = didx[j];
             const int64_t b = eptr[e];
             const int nT = (int)(eptr[e + 1] - b);
-            int lr = -1;
-            for (int c0 = 0; c0 < nT && lr < 0; c0 += 32) {
-                const int c = c0 + lane;
-                const unsigned hit = __ballot_sync(0xffffffffu, c < nT && eidx[b + c] == (int32_t)r);
-                if (hit) lr = c0 + __ffs((int)hit) - 1;
-            }
-            if (lr < 0) continue;   // r is in N(T) by construction of the DOF -> element map
-            const double *Ae = AT + aoff[e];
-            for (int c = lane; c < nT; c += 32) {
-                const int64_t k = lower_bound_i32(pat, m, eidx[b + c]);
-                v[k] += Ae[(int64_t)c * nT + lr];     // DOFs of one element are distinct
-            }
-            __syncwarp();
+            int c = 0;
+            while (c < nT && eidx[b + c] != (int32_t)r) c++;
+            if (c < nT) v += AT[aoff[e] + (int64_t)c * nT + c];
         }
+        dg[r] = fabs(v);
     }
 }
 
-// |A(r, r)| of every row (0 when r is not in its own pattern)
-__global__ void k_row_diag(const int64_t *sptr, const int32_t *sidx, const double *vals, int64_t n,
-                           double *dg) {
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
-         r += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t m = sptr[r + 1] - sptr[r];
-        const int64_t k = lower_bound_i32(sidx + sptr[r], m, (int32_t)r);
-        dg[r] = (k < m && sidx[sptr[r] + k] == r) ? fabs(vals[sptr[r] + k]) : 0.0;
+// B_i = A(omega_i, Omega^G_i) stored column q-rank major: B[p_pos + q_rank * nO] = assembled A(q, p)
+// over the elements touching omega_i, each entry summed in ascending element order by the one
+// CTA owning its column (element matrices column-major: A_T(c, r) at Ae[r * nT + c])
+__global__ void k_assemble_rect(const int32_t *ids, int64_t na, const int64_t *aeptr, const int32_t *aeidx,
+                                const int64_t *eptr, const int32_t *eidx, const double *AT, const int64_t *aoff,
+                                const int64_t *Optr, const int32_t *Oidx, const int32_t *agg,
+                                const int32_t *posw, double *B, const int64_t *boff, int maxE, int es) {
+    extern __shared__ int32_t sh[];   // [maxE] rows (position in Omega^G), [maxE] columns, [maxE] owned
+    __shared__ int ncols;
+    const int64_t li = blockIdx.x;
+    if (li >= na) return;
+    const int32_t a = ids[li];
+    const int32_t *Om = Oidx + Optr[a];
+    const int64_t nO = Optr[a + 1] - Optr[a];
+    double *M = B + boff[li];
+    int32_t *prow = sh, *pcol = sh + maxE, *own = sh + 2 * maxE;
+    const int slice = blockIdx.y;
+    for (int64_t j = aeptr[a]; j < aeptr[a + 1]; j++) {
+        const int32_t e = aeidx[j];
+        const int64_t b = eptr[e];
+        const int n = (int)(eptr[e + 1] - b);
+        for (int t = threadIdx.x; t < n; t += blockDim.x) {
+            const int32_t q = eidx[b + t];
+            prow[t] = (int32_t)lower_bound_i32(Om, nO, q);   // N(T) is inside Omega^G_i
+            pcol[t] = agg[q] == a ? posw[q] : -1;
+        }
+        __syncthreads();
+        warp_compact(n, own, &ncols, [&](int c) { return pcol[c] >= 0 && pcol[c] % es == slice; });
+        __syncthreads();
+        const double *Ae = AT + aoff[e];
+        const int nc = ncols;
+        for (int t = threadIdx.x; t < nc * n; t += blockDim.x) {
+            const int c = own[t / n], r = t % n;
+            M[prow[r] + (int64_t)pcol[c] * nO] += Ae[(int64_t)r * n + c];
+        }
+        __syncthreads();
     }
 }
 
-// entry (r, q) of the A pattern is kept when q == r (omega_i is in Omega_i^A whatever A(r, r)
-// is) or |A(r, q)| > cut sqrt(|A(r, r)| |A(q, q)|): entries that cancel in exact arithmetic
-// (exact zeros on the finest level, rounding after coarse Galerkin products) count as zero
-__device__ __forceinline__ bool a_kept(int64_t r, int32_t q, double v, const double *dg, double cut) {
-    return q == r || fabs(v) > cut * sqrt(dg[r] * dg[q]);
+// keep[j] for the entries of Omega^G_i: p in omega_i, or |A(q, p)| > cut sqrt(|A(q, q)| |A(p, p)|)
+// for some q in omega_i (entries that cancel in exact arithmetic -- exact zeros on the finest
+// level, rounding after coarse Galerkin products -- count as zero)
+__global__ void k_a_keep(const int32_t *ids, int64_t na, const int64_t *Optr, const int32_t *Oidx,
+                         const int32_t *agg, const int64_t *wptr, const int32_t *widx, const double *dg,
+                         const double *B, const int64_t *boff, double cut, int32_t *keep) {
+    const int64_t li = blockIdx.x;
+    if (li >= na) return;
+    const int32_t a = ids[li];
+    const int64_t ob = Optr[a], nO = Optr[a + 1] - ob;
+    const int64_t wb = wptr[a], nw = wptr[a + 1] - wb;
+    const double *M = B + boff[li];
+    for (int64_t rr = threadIdx.x; rr < nO; rr += blockDim.x) {
+        const int32_t p = Oidx[ob + rr];
+        bool k = agg[p] == a;
+        for (int64_t c = 0; c < nw && !k; c++)
+            k = fabs(M[rr + c * nO]) > cut * sqrt(dg[p] * dg[widx[wb + c]]);
+        keep[ob + rr] = k ? 1 : 0;
+    }
 }
 
-__global__ void k_nz_count(const int64_t *sptr, const int32_t *sidx, const double *vals,
-                           const double *dg, double cut, int64_t n, int64_t *cnt) {
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
-         r += (int64_t)gridDim.x * blockDim.x) {
+// per aggregate: number of kept entries; then the kept entries in order (one warp per aggregate)
+__global__ void k_keep_count(const int64_t *Optr, const int32_t *keep, int64_t nagg, int64_t *cnt) {
+    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < nagg;
+         a += (int64_t)gridDim.x * blockDim.x) {
         int64_t c = 0;
-        for (int64_t j = sptr[r]; j < sptr[r + 1]; j++) c += a_kept(r, sidx[j], vals[j], dg, cut);
-        cnt[r] = c;
+        for (int64_t j = Optr[a]; j < Optr[a + 1]; j++) c += keep[j];
+        cnt[a] = c;
     }
 }
 
-__global__ void k_nz_fill(const int64_t *sptr, const int32_t *sidx, const double *vals,
-                          const double *dg, double cut, int64_t n, const int64_t *nzptr,
-                          int32_t *nzidx) {
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
-         r += (int64_t)gridDim.x * blockDim.x) {
-        int64_t o = nzptr[r];
-        for (int64_t j = sptr[r]; j < sptr[r + 1]; j++)
-            if (a_kept(r, sidx[j], vals[j], dg, cut)) nzidx[o++] = sidx[j];
+__global__ void k_keep_fill(const int64_t *Optr, const int32_t *Oidx, const int32_t *keep, int64_t nagg,
+                            const int64_t *optr, int32_t *oidx) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t a = w0; a < nagg; a += nwarp) {
+        int64_t o = optr[a];
+        for (int64_t j0 = Optr[a]; j0 < Optr[a + 1]; j0 += 32) {
+            const int64_t j = j0 + lane;
+            const bool k = j < Optr[a + 1] && keep[j];
+            const unsigned m = __ballot_sync(0xffffffffu, k);
+            if (k) oidx[o + __popc(m & ((1u << lane) - 1u))] = Oidx[j];
+            o += __popc(m);
+        }
     }
 }
 
@@ -574,36 +606,85 @@ void aggregate_level(Level &L, int passes, int *err, cudaStream_t s) {
 // Relative size below which an assembled entry counts as zero in the A-closure.
 constexpr double kACut = 1e-12;
 
-// Omega_i^A = union over the rows r in omega_i of the kept entries of A(r, :) (Def. 5.2)
-static void a_closure(Level &L, DBuf<int64_t> &Optr, DBuf<int32_t> &Oidx, int *err, cudaStream_t s) {
-    const int64_t n = L.n;
-    DBuf<int64_t> sptr, nzptr, cnt;
-    DBuf<int32_t> sidx, nzidx;
-    csr_union(L.dptr.p, L.didx.p, n, L.eptr.p, L.eidx.p, sptr, sidx, err, s);   // structural rows
-    const int64_t nnz = read1(sptr.p + n, s);
-    DBuf<double> vals, dg;
-    vals.alloc(std::max<int64_t>(nnz, 1), s);
+__global__ void k_elem_len(const int64_t *eptr, int64_t ne, int32_t *len) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne;
+         e += (int64_t)gridDim.x * blockDim.x)
+        len[e] = (int32_t)(eptr[e + 1] - eptr[e]);
+}
+
+// Omega^A_i from Omega^G_i (OGptr / OGidx): the block A(omega_i, Omega^G_i) of every aggregate,
+// assembled in chunks of at most 4 GB, decides which entries stay
+static void a_closure(Level &L, const DBuf<int64_t> &OGptr, const DBuf<int32_t> &OGidx, DBuf<int64_t> &Optr,
+                      DBuf<int32_t> &Oidx, int *err, cudaStream_t s) {
+    const int64_t n = L.n, nagg = L.nagg, ne = L.ne;
+    const int64_t nOG = read1(OGptr.p + nagg, s);
+    DBuf<double> dg;
     dg.alloc(std::max<int64_t>(n, 1), s);
-    cnt.alloc(std::max<int64_t>(n, 1), s);
     if (n > 0) {
-        k_row_values<<<grid_for(n * 32), TPB, 0, s>>>(sptr.p, sidx.p, n, L.dptr.p, L.didx.p, L.eptr.p,
-                                                       L.eidx.p, L.AT.p, L.aoff.p, vals.p);
-        CK_LAUNCH();
-        k_row_diag<<<grid_for(n), TPB, 0, s>>>(sptr.p, sidx.p, vals.p, n, dg.p);
-        CK_LAUNCH();
-        k_nz_count<<<grid_for(n), TPB, 0, s>>>(sptr.p, sidx.p, vals.p, dg.p, kACut, n, cnt.p);
+        k_assembled_diag<<<grid_for(n), TPB, 0, s>>>(L.dptr.p, L.didx.p, n, L.eptr.p, L.eidx.p, L.AT.p, L.aoff.p,
+                                                     dg.p);
         CK_LAUNCH();
     }
-    nzptr.alloc(n + 1, s);
-    exclusive_scan_i64(cnt.p, nzptr.p, n, s);
-    const int64_t nzt = read1(nzptr.p + n, s);
-    nzidx.alloc(std::max<int64_t>(nzt, 1), s);
-    if (n > 0) {
-        k_nz_fill<<<grid_for(n), TPB, 0, s>>>(sptr.p, sidx.p, vals.p, dg.p, kACut, n, nzptr.p, nzidx.p);
+    int32_t maxE = 1;
+    if (ne > 0) {
+        DBuf<int32_t> len;
+        len.alloc(ne, s);
+        k_elem_len<<<grid_for(ne), TPB, 0, s>>>(L.eptr.p, ne, len.p);
+        CK_LAUNCH();
+        maxE = std::max<int32_t>(1, max_i32(len.p, ne, s));
+    }
+    const size_t smem = 3 * (size_t)maxE * sizeof(int32_t);
+    if (smem > 200 * 1024) fail(LSAMG_LIMIT, "element map longer than the A-closure staging (17,066)");
+    CK(cudaFuncSetAttribute(k_assemble_rect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    DBuf<int32_t> keep;
+    keep.alloc(std::max<int64_t>(nOG, 1), s);
+    auto og = to_host(OGptr.p, nagg + 1, s);
+    auto wp = to_host(L.wptr.p, nagg + 1, s);
+    const int64_t budget = (int64_t)4 << 30;
+    for (int64_t a0 = 0; a0 < nagg;) {
+        std::vector<int32_t> ids;
+        std::vector<int64_t> boff(1, 0);
+        int64_t a1 = a0;
+        while (a1 < nagg) {
+            const int64_t by = (og[a1 + 1] - og[a1]) * (wp[a1 + 1] - wp[a1]) * 8;
+            if (a1 > a0 && (boff.back() * 8 + by) > budget) break;
+            ids.push_back((int32_t)a1);
+            boff.push_back(boff.back() + by / 8);
+            a1++;
+        }
+        const int64_t na = (int64_t)ids.size();
+        DBuf<int32_t> dids;
+        DBuf<int64_t> dboff;
+        upload(dids, ids, s);
+        upload(dboff, boff, s);
+        DBuf<double> B;
+        B.alloc(std::max<int64_t>(boff.back(), 1), s);
+        B.zero(s);
+        const int es = (int)std::max<int64_t>(1, std::min<int64_t>((148 * 4 + na - 1) / na, 16));
+        k_assemble_rect<<<dim3((unsigned)na, (unsigned)es), 256, smem, s>>>(
+            dids.p, na, L.aeptr.p, L.aeidx.p, L.eptr.p, L.eidx.p, L.AT.p, L.aoff.p, OGptr.p, OGidx.p, L.agg.p,
+            L.posw.p, B.p, dboff.p, maxE, es);
+        CK_LAUNCH();
+        k_a_keep<<<(unsigned)na, 256, 0, s>>>(dids.p, na, OGptr.p, OGidx.p, L.agg.p, L.wptr.p, L.widx.p, dg.p, B.p,
+                                             dboff.p, kACut, keep.p);
+        CK_LAUNCH();
+        a0 = a1;
+    }
+    DBuf<int64_t> cnt;
+    cnt.alloc(std::max<int64_t>(nagg, 1), s);
+    if (nagg > 0) {
+        k_keep_count<<<grid_for(nagg), TPB, 0, s>>>(OGptr.p, keep.p, nagg, cnt.p);
         CK_LAUNCH();
     }
-    trace("  A pattern: %lld structural, %lld kept", (long long)nnz, (long long)nzt);
-    csr_union(L.wptr.p, L.widx.p, L.nagg, nzptr.p, nzidx.p, Optr, Oidx, err, s);
+    Optr.alloc(nagg + 1, s);
+    exclusive_scan_i64(cnt.p, Optr.p, nagg, s);
+    const int64_t tot = read1(Optr.p + nagg, s);
+    Oidx.alloc(std::max<int64_t>(tot, 1), s);
+    if (nagg > 0) {
+        k_keep_fill<<<grid_for(nagg * 32), TPB, 0, s>>>(OGptr.p, OGidx.p, keep.p, nagg, Optr.p, Oidx.p);
+        CK_LAUNCH();
+    }
+    trace("  A-closure: %lld of %lld G-row closure entries kept", (long long)tot, (long long)nOG);
 }
 
 void closure_level(Level &L, double tau_c, int closure, int *err, cudaStream_t s) {
@@ -651,13 +732,14 @@ void closure_level(Level &L, double tau_c, int closure, int *err, cudaStream_t s
     {
         DBuf<int64_t> qptr;
         DBuf<int32_t> qidx;
-        if (closure == 0) {
-            csr_union(L.dptr.p, L.didx.p, n, L.eaptr.p, L.eaidx.p, qptr, qidx, err, s);
-            int64_t tot = read1(qptr.p + n, s);
-            csr_transpose(qptr.p, qidx.p, n, tot, nagg, L.Optr, L.Oidx, err, s);
-        } else {
-            a_closure(L, L.Optr, L.Oidx, err, s);
-            int64_t tot = read1(L.Optr.p + nagg, s);
+        csr_union(L.dptr.p, L.didx.p, n, L.eaptr.p, L.eaidx.p, qptr, qidx, err, s);
+        int64_t tot = read1(qptr.p + n, s);
+        csr_transpose(qptr.p, qidx.p, n, tot, nagg, L.Optr, L.Oidx, err, s);
+        if (closure != 0) {
+            DBuf<int64_t> gptr = std::move(L.Optr);
+            DBuf<int32_t> gidx = std::move(L.Oidx);
+            a_closure(L, gptr, gidx, L.Optr, L.Oidx, err, s);
+            tot = read1(L.Optr.p + nagg, s);
             csr_transpose(L.Optr.p, L.Oidx.p, nagg, tot, n, qptr, qidx, err, s);
         }
         int64_t nO = read1(L.Optr.p + nagg, s);

@@ -6,6 +6,23 @@
 
 namespace lsamg {
 
+// Warp 0 lists, in ascending order, the element columns c < n with keep(c) into own[]; returns
+// the count through *cnt (visible after the caller's __syncthreads).
+template <class F>
+__device__ __forceinline__ void warp_compact(int n, int32_t *own, int *cnt, F keep) {
+    if (threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
+    int q = 0;
+    for (int c0 = 0; c0 < n; c0 += 32) {
+        const int c = c0 + lane;
+        const bool k = c < n && keep(c);
+        const unsigned m = __ballot_sync(0xffffffffu, k);
+        if (k) own[q + __popc(m & ((1u << lane) - 1u))] = c;
+        q += __popc(m);
+    }
+    if (lane == 0) *cnt = q;
+}
+
 struct Level {
     int64_t n = 0;   // DOFs
     int64_t ne = 0;  // elements (level 0) or merged coarse elements (levels >= 1)

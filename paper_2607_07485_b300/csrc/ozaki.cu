@@ -1,4 +1,5 @@
 // FP64 products on FP16 tensor cores by exact splitting (see ozaki.cuh for the scheme).
+#include <cstdlib>
 #include <cstring>
 
 #include "ozaki.cuh"
@@ -35,7 +36,7 @@ __global__ void __launch_bounds__(256) k_split(const double *src, const SplitJob
     const int j = find_job(pre, njobs, blockIdx.x);
     const SplitJob J = jobs[j];
     const int t = (int)(blockIdx.x - pre[j]);
-    const int tiles = dcdiv(J.rows, TM), nch = dcdiv(max(J.K, 1), TK);
+    const int tiles = (int)stor_tiles(J.rows), nch = dcdiv(max(J.K, 1), TK);
     const int i0 = t * TM;
     const bool kfast = (J.ks == 1);
     const double *S = src + J.src_off;
@@ -229,22 +230,29 @@ __device__ __forceinline__ double i128_add_double(__int128 v, int e, double c) {
 // joins the integer sum exactly and the result is rounded once.  FP64 instructions are scarce on
 // this GPU: none in the common cases (alpha a power of two, beta 0 or 1).  Kept out of line: the
 // product loop's registers are not needed here.
+__device__ __forceinline__ double combine_out(__int128 v, int e, double alpha, double beta, double c);
+
 __device__ __noinline__ void store_out(double *cp, int32_t s2, int32_t s3, int32_t s4, int32_t s5, int32_t s6,
                                        float tail, int e, double alpha, double beta) {
-    __int128 v = ((__int128)s2 << 48) + ((__int128)s3 << 40) + ((__int128)s4 << 32) + ((__int128)s5 << 24) +
-                 ((__int128)s6 << 16) + (__int128)__float2ll_rn(tail * 256.0f);
+    const __int128 v = ((__int128)s2 << 48) + ((__int128)s3 << 40) + ((__int128)s4 << 32) + ((__int128)s5 << 24) +
+                       ((__int128)s6 << 16) + (__int128)__float2ll_rn(tail * 256.0f);
+    *cp = combine_out(v, e, alpha, beta, beta == 0.0 ? 0.0 : *cp);
+}
+
+// beta c + alpha v 2^e, rounded once when alpha is a power of two and beta is 0 or 1 (integer
+// instructions only), else through FP64 arithmetic
+__device__ __forceinline__ double combine_out(__int128 v, int e, double alpha, double beta, double c) {
     int e2;
     const double fr = frexp(fabs(alpha), &e2);
     if (fr != 0.5) {
         const double val = alpha * i128_to_double(v, e, false);
-        *cp = (beta == 0.0) ? val : (beta == 1.0) ? *cp + val : fma(beta, *cp, val);
-        return;
+        return (beta == 0.0) ? val : (beta == 1.0) ? c + val : fma(beta, c, val);
     }
     if (alpha < 0.0) v = -v;
     e += e2 - 1;
-    if (beta == 0.0) *cp = i128_to_double(v, e, false);
-    else if (beta == 1.0) *cp = i128_add_double(v, e, *cp);
-    else *cp = fma(beta, *cp, i128_to_double(v, e, false));
+    if (beta == 0.0) return i128_to_double(v, e, false);
+    if (beta == 1.0) return i128_add_double(v, e, c);
+    return fma(beta, c, i128_to_double(v, e, false));
 }
 
 // 16 warps per CTA, warp tile 16 x 16 (one m16 tile, two n8 tiles): every slice's fragments
@@ -268,7 +276,7 @@ __device__ __forceinline__ TileRef decode_tile(const __half *sl, const GemmJob *
     r.job = find_job(pre, njobs, t);
     const GemmJob &J = jobs[r.job];
     const int64_t local = t - pre[r.job];
-    const int tilesM = dcdiv(J.M, TM), tilesN = dcdiv(J.N, TM);
+    const int tilesN = dcdiv(J.N, TM);
     if (J.lower) tri_index(local, r.tm, r.tn);
     else { r.tm = (int)(local / tilesN); r.tn = (int)(local % tilesN); }
     const int ntot = dcdiv(max(J.ktot, 1), TK);          // chunks of the split operands
@@ -276,8 +284,8 @@ __device__ __forceinline__ TileRef decode_tile(const __half *sl, const GemmJob *
     r.nch = dcdiv(max(J.K, 1), TK);
     r.gA = sl + J.a_off + (int64_t)r.tm * ntot * BLK;
     r.gB = sl + J.b_off + (int64_t)r.tn * ntot * BLK;
-    r.pA = (int64_t)tilesM * ntot * BLK;
-    r.pB = (int64_t)tilesN * ntot * BLK;
+    r.pA = stor_tiles(J.M) * ntot * BLK;
+    r.pB = stor_tiles(J.N) * ntot * BLK;
     return r;
 }
 
@@ -437,6 +445,299 @@ __global__ void __launch_bounds__(GT, 1) k_gemm(const __half *sl, const int32_t 
     }
 }
 
+// ------------------------------------------------------------------------------- tcgen05 gemm
+// The same products on the fifth-generation tensor cores (tcgen05.mma, accumulators in tensor
+// memory).  A CTA computes a 128 x 32 tile of C.  In each 16-wide K step, A slice p multiplies
+// the B slices 1 .. 8-p stacked along N in ONE instruction (N = 32 (8 - p)): the product of
+// pair (p, q) lands in tensor-memory columns 32 (p + q - 2) .., i.e. in the accumulator of its
+// diagonal d = p + q, so seven instructions per K step cover all 28 pairs.  Each diagonal sum
+// of a K piece of 128 is an integer below 7 * 128 * 2^14 < 2^24, exact in FP32; the epilogue
+// moves it into 64-bit integers (two per output, units 2^32 and 1 of the lowest weight) and
+// forms the FP64 result once per tile.  The 7 x 32 FP32 accumulator columns are double
+// buffered (2 x 256 of the 512 columns), so the epilogue of one piece overlaps the products of
+// the next.  Warp 0 stages operands with bulk copies (three 70 KB stages), warp 1 owns the
+// tensor memory and issues the products (one thread), warps 2..9 run the epilogue.
+namespace tcg {
+constexpr int BM = 128, BN = 32;
+constexpr int TST = 3;                         // staging ring depth
+constexpr int A_BYTES = NS * BM * TK * 2;      // 7 slices x 128 rows x 64 B
+constexpr int B_BYTES = NS * BN * TK * 2;      // 7 slices x 32 rows x 64 B
+constexpr int STAGE = A_BYTES + B_BYTES;       // 70 KB
+constexpr int PIECE = 4;                       // K chunks of 32 per accumulation piece
+constexpr int EPI_WARPS = 8;
+constexpr int THREADS = (2 + EPI_WARPS) * 32;
+constexpr int SMEM = TST * STAGE + 1024;       // + alignment slack
+constexpr uint32_t TMEM_COLS = 512;
+constexpr uint64_t WAIT_NS = 2000000000ull;
+}  // namespace tcg
+
+__device__ __forceinline__ void tm_alloc(uint32_t *dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tm_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// D[tmem] (+)= A[smem] B[smem]^T, FP16 inputs, FP32 accumulation; acc = 0 overwrites D
+__device__ __forceinline__ void umma_f16(uint32_t dt, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            dt),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+        : "memory");
+}
+// arrive on `bar` once every product issued so far by this thread has completed
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// 32 lanes (this warp's quarter) x 8 consecutive 32-bit columns
+__device__ __forceinline__ void tm_ld8(uint32_t taddr, float (&v)[8]) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 8; i++) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tm_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// shared-memory matrix descriptor: K-major rows of 64 bytes in the 64-byte swizzle (16-byte
+// chunk index XOR (row / 2) mod 4, the layout the operand blocks are stored in), 8-row groups
+// 512 bytes apart
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
+}
+// instruction descriptor of kind::f16: FP32 D, FP16 A and B, both K-major, M x N
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// tiles of a lower-triangular job before tile row tm: row t holds min(tilesN, 4 t + 4) tiles,
+// those reaching the diagonal
+__host__ __device__ inline int64_t tc_lower_prefix(int64_t tm, int64_t tilesN) {
+    const int64_t t0 = tm < tilesN / 4 ? tm : tilesN / 4;
+    return 2 * t0 * (t0 + 1) + (tm - t0) * tilesN;
+}
+
+struct TcTile {
+    int job, tm, tn, nch;
+};
+__device__ __forceinline__ TcTile tc_decode(const GemmJob *jobs, const int64_t *pre, int njobs, int64_t t) {
+    TcTile r;
+    r.job = find_job(pre, njobs, t);
+    const GemmJob &J = jobs[r.job];
+    const int64_t local = t - pre[r.job];
+    const int tilesN = dcdiv(J.N, tcg::BN);
+    if (J.lower) {
+        int lo = 0, hi = dcdiv(J.M, tcg::BM) - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (tc_lower_prefix(mid, tilesN) <= local) lo = mid; else hi = mid - 1;
+        }
+        r.tm = lo;
+        r.tn = (int)(local - tc_lower_prefix(lo, tilesN));
+    } else {
+        r.tm = (int)(local / tilesN);
+        r.tn = (int)(local % tilesN);
+    }
+    r.nch = dcdiv(max(J.K, 1), TK);
+    return r;
+}
+
+__global__ void __launch_bounds__(tcg::THREADS, 1)
+    k_gemm_tc(const __half *sl, const int32_t *ex, double *C, const GemmJob *jobs, const int64_t *pre, int njobs,
+              double alpha, double beta, int *err, const int32_t *skip) {
+    using namespace tcg;
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t full[TST], empty[TST], tfull[2], tempty[2], done;
+    __shared__ uint32_t s_tmem;
+    __shared__ volatile int s_abort;
+    unsigned char *smem = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t total = pre[njobs];
+    auto active = [&](int64_t t) { return !skip || skip[jobs[find_job(pre, njobs, t)].skip_idx] < 0; };
+    auto fail_wait = [&](int where) {
+        if (!s_abort) flag_error(err, LSAMG_DEVICE_TIMEOUT, (int)blockIdx.x * 16 + where);
+        s_abort = 1;
+    };
+    if (tid == 0) {
+        for (int i = 0; i < TST; i++) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        for (int b = 0; b < 2; b++) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], EPI_WARPS);
+        }
+        mbar_init(&done, 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) tm_alloc(&s_tmem, TMEM_COLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = s_tmem;
+
+    if (warp == 0) {
+        // ---------------- producer: bulk copies of the slice blocks of every K chunk
+        if (lane == 0) {
+            int64_t it = 0;
+            for (int64_t t = blockIdx.x; t < total && !s_abort; t += gridDim.x) {
+                if (!active(t)) continue;
+                const TcTile T = tc_decode(jobs, pre, njobs, t);
+                const GemmJob &J = jobs[T.job];
+                const int ntot = dcdiv(max(J.ktot, 1), TK), c0 = J.k0 / TK;
+                const int64_t pA = stor_tiles(J.M) * ntot * BLK, pB = stor_tiles(J.N) * ntot * BLK;
+                const __half *gA = sl + J.a_off + (int64_t)(2 * T.tm) * ntot * BLK;
+                const __half *gB = sl + J.b_off + (int64_t)(T.tn >> 1) * ntot * BLK + (T.tn & 1) * (BN * TK);
+                for (int c = 0; c < T.nch && !s_abort; c++, it++) {
+                    const int st = (int)(it % TST);
+                    if (it >= TST && !mbar_wait_bounded(&empty[st], (uint32_t)((it / TST - 1) & 1), WAIT_NS)) {
+                        fail_wait(1);
+                        break;
+                    }
+                    unsigned char *sb = smem + st * STAGE;
+                    mbar_expect_tx(&full[st], STAGE);
+                    const int64_t cc = c0 + c;
+                    for (int p = 0; p < NS; p++) {
+                        const __half *a = gA + p * pA + cc * BLK;
+                        bulk_g2s(sb + p * (BM * TK * 2), a, BLK * 2, &full[st]);
+                        bulk_g2s(sb + p * (BM * TK * 2) + BLK * 2, a + (int64_t)ntot * BLK, BLK * 2, &full[st]);
+                        bulk_g2s(sb + A_BYTES + p * (BN * TK * 2), gB + p * pB + cc * BLK, BN * TK * 2, &full[st]);
+                    }
+                }
+            }
+            // copies still in flight land before the CTA's shared memory is released
+            for (int64_t g = (it > TST ? it - TST : 0); g < it; g++)
+                mbar_wait_bounded(&full[g % TST], (uint32_t)((g / TST) & 1), WAIT_NS);
+        }
+    } else if (warp == 1) {
+        // ---------------- issuer: 7 products per 16-wide K step
+        if (lane == 0) {
+            int64_t it = 0, pc = 0;
+            bool issued = false;
+            for (int64_t t = blockIdx.x; t < total && !s_abort; t += gridDim.x) {
+                if (!active(t)) continue;
+                const TcTile T = tc_decode(jobs, pre, njobs, t);
+                for (int c0 = 0; c0 < T.nch && !s_abort; c0 += PIECE, pc++) {
+                    const int b = (int)(pc & 1);
+                    if (pc >= 2 && !mbar_wait_bounded(&tempty[b], (uint32_t)(((pc >> 1) - 1) & 1), WAIT_NS)) {
+                        fail_wait(2);
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t dt = tbase + (uint32_t)b * 256u;
+                    const int c1 = min(T.nch, c0 + PIECE);
+                    for (int c = c0; c < c1; c++, it++) {
+                        const int st = (int)(it % TST);
+                        if (!mbar_wait_bounded(&full[st], (uint32_t)((it / TST) & 1), WAIT_NS)) {
+                            fail_wait(3);
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t sa = smem_u32(smem + st * STAGE), sbb = sa + A_BYTES;
+#pragma unroll
+                        for (int ks = 0; ks < 2; ks++)
+#pragma unroll
+                            for (int p = 1; p <= NS; p++)
+                                umma_f16(dt + 32u * (p - 1), sdesc_sw64(sa + (p - 1) * (BM * TK * 2) + ks * 32),
+                                         sdesc_sw64(sbb + ks * 32), idesc_f16(BM, BN * (8 - p)),
+                                         (c > c0 || ks > 0 || p > 1) ? 1u : 0u);
+                        umma_commit(&empty[st]);
+                        issued = true;
+                    }
+                    if (s_abort) break;
+                    umma_commit(&tfull[b]);
+                }
+            }
+            if (issued) {
+                // every product completed before the tensor memory is released
+                umma_commit(&done);
+                mbar_wait_bounded(&done, 0, WAIT_NS);
+            }
+        }
+    } else {
+        // ---------------- epilogue: rows 32 (warp % 4) + lane, 16 columns per warp
+        const int qd = warp & 3, cg = (warp - 2) >> 2;
+        const int row = 32 * qd + lane;
+        const uint32_t tq = tbase + ((uint32_t)(32 * qd) << 16);
+        int64_t pc = 0;
+        for (int64_t t = blockIdx.x; t < total && !s_abort; t += gridDim.x) {
+            if (!active(t)) continue;
+            const TcTile T = tc_decode(jobs, pre, njobs, t);
+            const GemmJob &J = jobs[T.job];
+            int64_t hi[16], lo[16];
+#pragma unroll
+            for (int j = 0; j < 16; j++) hi[j] = lo[j] = 0;
+            bool ok = true;
+            for (int c0 = 0; c0 < T.nch; c0 += PIECE, pc++) {
+                const int b = (int)(pc & 1);
+                if (!mbar_wait_bounded(&tfull[b], (uint32_t)((pc >> 1) & 1), WAIT_NS)) {
+                    fail_wait(4);
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+#pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    float v[NS][8];
+#pragma unroll
+                    for (int d = 0; d < NS; d++)
+                        tm_ld8(tq + (uint32_t)b * 256u + 32u * d + 16u * cg + 8u * h, v[d]);
+                    tm_wait_ld();
+#pragma unroll
+                    for (int j = 0; j < 8; j++) {
+                        // S_2..S_8: integers below 2^24, exact in FP32
+                        hi[8 * h + j] += ((int64_t)__float2int_rn(v[0][j]) << 16) +
+                                         ((int64_t)__float2int_rn(v[1][j]) << 8) + (int64_t)__float2int_rn(v[2][j]);
+                        lo[8 * h + j] += ((int64_t)__float2int_rn(v[3][j]) << 24) +
+                                         ((int64_t)__float2int_rn(v[4][j]) << 16) +
+                                         ((int64_t)__float2int_rn(v[5][j]) << 8) + (int64_t)__float2int_rn(v[6][j]);
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty[b]);
+            }
+            if (!ok) break;
+            const int i = T.tm * BM + row;
+            if (i >= J.M) continue;
+            const int ea = ex[J.a_exp + i] - 62;
+            double *crow = C + J.c_off + (int64_t)i * J.crs;
+            const int j0 = T.tn * BN + 16 * cg;
+            double cv[16];
+#pragma unroll
+            for (int j = 0; j < 16; j++) {
+                const int jj = j0 + j;
+                cv[j] = (beta != 0.0 && jj < J.N && !(J.lower && i < jj)) ? crow[(int64_t)jj * J.ccs] : 0.0;
+            }
+#pragma unroll
+            for (int j = 0; j < 16; j++) {
+                const int jj = j0 + j;
+                if (jj >= J.N || (J.lower && i < jj)) continue;
+                const __int128 vv = ((__int128)hi[j] << 32) + (__int128)lo[j];
+                crow[(int64_t)jj * J.ccs] = combine_out(vv, ea + ex[J.b_exp + jj], alpha, beta, cv[j]);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tm_dealloc(tbase, TMEM_COLS);
+    }
+}
+
 // one device upload of a job array and the exclusive prefix of its CTA counts
 template <class Job>
 int64_t upload_jobs(const std::vector<Job> &jobs, const std::vector<int64_t> &cnt, DBuf<int64_t> &buf,
@@ -462,7 +763,7 @@ void split(const double *src, const std::vector<SplitJob> &jobs, __half *dst, in
     static_assert(sizeof(SplitJob) % 8 == 0, "job layout");
     std::vector<int64_t> cnt(jobs.size());
     for (size_t i = 0; i < jobs.size(); i++) {
-        cnt[i] = jobs[i].rows > 0 ? cdiv(jobs[i].rows, TM) : 0;
+        cnt[i] = jobs[i].rows > 0 ? stor_tiles(jobs[i].rows) : 0;   // padding blocks are zero-filled
     }
     DBuf<int64_t> buf;
     const SplitJob *dj = nullptr;
@@ -477,10 +778,57 @@ void split(const double *src, const std::vector<SplitJob> &jobs, __half *dst, in
     CK_LAUNCH();
 }
 
+static int device_sms() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    return sms;
+}
+
+// products on the tcgen05 tensor cores: one launch for every K (64-bit integer accumulation
+// across K pieces in the epilogue)
+static void gemm_tc(const __half *slices, const int32_t *exps, double *C, const std::vector<GemmJob> &jobs,
+                    double alpha, double beta, int *err, cudaStream_t s, const int32_t *skip) {
+    std::vector<GemmJob> js;
+    std::vector<int64_t> cnt;
+    double fl = 0.0;   // FP64-equivalent flops of the products (lower: the triangle only)
+    for (const auto &J0 : jobs) {
+        if (J0.M <= 0 || J0.N <= 0) continue;
+        GemmJob J = J0;
+        J.k0 = 0;
+        J.ktot = J0.K;
+        const int64_t tm = cdiv(J.M, tcg::BM), tn = cdiv(J.N, tcg::BN);
+        if (J.lower && J.M != J.N) fail(LSAMG_INVALID_ARG, "lower-triangular product of a non-square block");
+        js.push_back(J);
+        cnt.push_back(J.lower ? tc_lower_prefix(tm, tn) : tm * tn);
+        fl += (J.lower ? 1.0 : 2.0) * J.M * (double)J.N * J.K;
+    }
+    if (js.empty()) return;
+    DBuf<int64_t> buf;
+    const GemmJob *dj = nullptr;
+    const int64_t *dp = nullptr;
+    const int64_t total = upload_jobs(js, cnt, buf, dj, dp, s);
+    if (total == 0) return;
+    if (total > 0x7fffffff) fail(LSAMG_LIMIT, "product grid too large");
+    KTime kt(KC_TC_GEMM, s, fl);
+    CK(cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tcg::SMEM));
+    const unsigned grid = (unsigned)std::min<int64_t>(total, device_sms());
+    k_gemm_tc<<<grid, tcg::THREADS, tcg::SMEM, s>>>(slices, exps, C, dj, dp, (int)js.size(), alpha, beta, err, skip);
+    CK_LAUNCH();
+}
+
 void gemm(const __half *slices, const int32_t *exps, double *C, const std::vector<GemmJob> &jobs, double alpha,
           double beta, int *err, cudaStream_t s, const int32_t *skip) {
     if (jobs.empty()) return;
     static_assert(sizeof(GemmJob) % 8 == 0, "job layout");
+    static const bool mma_sync = getenv("LSAMG_OZ_MMA") != nullptr;
+    if (!mma_sync) {
+        gemm_tc(slices, exps, C, jobs, alpha, beta, err, s, skip);
+        return;
+    }
     static_assert(KPIECE % TK == 0, "K pieces are whole chunks");
     int npieces = 1;
     for (const auto &J : jobs) npieces = std::max<int>(npieces, (int)cdiv(std::max(J.K, 1), KPIECE));
@@ -512,13 +860,7 @@ void gemm(const __half *slices, const int32_t *exps, double *C, const std::vecto
         double fl = 0.0;   // FP64-equivalent flops of the products (lower: the triangle only)
         for (const auto &J : js) fl += (J.lower ? 1.0 : 2.0) * J.M * (double)J.N * J.K;
         KTime kt(KC_TC_GEMM, s, fl);
-        static int sms = 0;
-        if (!sms) {
-            int dev = 0;
-            CK(cudaGetDevice(&dev));
-            CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        }
-        const unsigned grid = (unsigned)std::min<int64_t>(total, sms);
+        const unsigned grid = (unsigned)std::min<int64_t>(total, device_sms());
         k_gemm<<<grid, GT, GEMM_SMEM, s>>>(slices, exps, C, dj, dp, (int)js.size(), alpha, pc == 0 ? beta : 1.0, err,
                                           skip);
         CK_LAUNCH();

@@ -59,11 +59,16 @@ struct GemmJob {
     int32_t k0 = 0, ktot = 0;    // set by gemm(): this piece's first K index and the operands' K
 };
 
+// 64-row blocks stored per slice and K chunk: rounded up to an even count, so that a 128-row
+// operand tile of the tensor-core product always reads stored (zero-padded) rows.
+__host__ __device__ inline int64_t stor_tiles(int64_t rows) {
+    return 2 * (((rows > 1 ? rows : 1) + 2 * TM - 1) / (2 * TM));
+}
 // Slice storage needed for an operand of `rows` x K: (halves, exponent ints).
 inline int64_t slice_halves(int64_t rows, int64_t K) {
-    return (int64_t)NS * cdiv(std::max<int64_t>(rows, 1), TM) * cdiv(std::max<int64_t>(K, 1), TK) * BLK;
+    return (int64_t)NS * stor_tiles(rows) * cdiv(std::max<int64_t>(K, 1), TK) * BLK;
 }
-inline int64_t exp_ints(int64_t rows) { return cdiv(std::max<int64_t>(rows, 1), TM) * TM; }
+inline int64_t exp_ints(int64_t rows) { return stor_tiles(rows) * TM; }
 
 // Split the operands of `jobs` (host vector) from `src` into `dst` / `exps`.
 void split(const double *src, const std::vector<SplitJob> &jobs, __half *dst, int32_t *exps, cudaStream_t s);
