@@ -1,4 +1,5 @@
 // FP64 products on FP16 tensor cores by exact splitting (see ozaki.cuh for the scheme).
+#include <cmath>
 #include <cstdlib>
 #include <cstring>
 
@@ -255,6 +256,70 @@ __device__ __forceinline__ double combine_out(__int128 v, int e, double alpha, d
     return fma(beta, c, i128_to_double(v, e, false));
 }
 
+// alpha and beta of a product, classified once on the host: the epilogue then runs on integer
+// instructions only when alpha is a power of two (pow2, 2^(e2 - 1) with sign neg) and beta is 0
+// or 1 (bmode 0 / 1; 2: general beta)
+struct Scale {
+    double alpha, beta;
+    int32_t pow2, e2, neg, bmode;
+};
+inline Scale make_scale(double alpha, double beta) {
+    Scale sc;
+    sc.alpha = alpha;
+    sc.beta = beta;
+    int e2 = 0;
+    const double fr = std::frexp(std::fabs(alpha), &e2);
+    sc.pow2 = fr == 0.5 ? 1 : 0;
+    sc.e2 = e2;
+    sc.neg = alpha < 0.0 ? 1 : 0;
+    sc.bmode = beta == 0.0 ? 0 : beta == 1.0 ? 1 : 2;
+    return sc;
+}
+__device__ __forceinline__ double combine_scaled(__int128 v, int e, const Scale &sc, double c) {
+    if (sc.pow2) {
+        if (sc.neg) v = -v;
+        e += sc.e2 - 1;
+        if (sc.bmode == 0) return i128_to_double(v, e, false);
+        if (sc.bmode == 1) return i128_add_double(v, e, c);
+        return fma(sc.beta, c, i128_to_double(v, e, false));
+    }
+    const double val = sc.alpha * i128_to_double(v, e, false);
+    return sc.bmode == 0 ? val : sc.bmode == 1 ? c + val : fma(sc.beta, c, val);
+}
+
+// v 2^e rounded to nearest (ties to even) for the 96-bit integer v = hi 2^32 + lo given as two
+// 64-bit limbs (|hi| < 2^62).  Branch-free integer instructions while the result is a normal
+// number, so that the compiler interleaves the conversions of a thread's outputs.
+__device__ __forceinline__ double limbs_to_double(int64_t hi, int64_t lo, int e) {
+    hi += lo >> 32;                                   // lo = (lo >> 32) 2^32 + low 32 bits
+    uint32_t l = (uint32_t)lo;
+    const bool neg = hi < 0;
+    const uint64_t h = neg ? ~(uint64_t)hi + (l == 0u ? 1ull : 0ull) : (uint64_t)hi;   // |v| = h 2^32 + l
+    l = neg ? 0u - l : l;
+    // as a 96-bit number with its top limb nonzero when v != 0
+    const bool hz = h == 0;
+    const uint64_t H = hz ? (uint64_t)l : h;
+    const uint32_t Lw = hz ? 0u : l;
+    const int lz = __clzll((long long)H);             // 64 when v == 0 (result selected below)
+    const int sh = lz & 63;
+    const uint64_t top = (H << sh) | (sh ? (((uint64_t)Lw << 32) >> (64 - sh)) : 0ull);
+    const uint32_t sticky = sh < 32 ? (Lw << sh) : 0u;   // bits of the low limb below the window
+    uint64_t mant = top >> 11;
+    const uint32_t rb = (uint32_t)(top & 0x7ffull);
+    int E = 95 - lz + e - (hz ? 32 : 0);
+    mant += (rb > 0x400u || (rb == 0x400u && (sticky != 0u || (mant & 1ull)))) ? 1ull : 0ull;
+    const int ovf = (int)(mant >> 53);
+    mant >>= ovf;
+    E += ovf;
+    if (H == 0) return 0.0;
+    if (E > 1023 || E < -1022) {                       // overflow / subnormal range: FP64 scaling
+        const double r = ldexp((double)mant, E - 52);
+        return neg ? -r : r;
+    }
+    return __longlong_as_double(
+        (long long)(((uint64_t)(E + 1023) << 52) | (mant & ((1ull << 52) - 1)) | (neg ? (1ull << 63) : 0ull)));
+}
+
 // 16 warps per CTA, warp tile 16 x 16 (one m16 tile, two n8 tiles): every slice's fragments
 // of a 16-wide K step fit in registers (56), with per-diagonal exact int32 sums for the diagonals
 // 2..6 and one FP32 sum for the two lowest-weight diagonals (S_7 + S_8 / 256, weights 2^-40 and
@@ -456,7 +521,8 @@ __global__ void __launch_bounds__(GT, 1) k_gemm(const __half *sl, const int32_t 
 // forms the FP64 result once per tile.  The 7 x 32 FP32 accumulator columns are double
 // buffered (2 x 256 of the 512 columns), so the epilogue of one piece overlaps the products of
 // the next.  Warp 0 stages operands with bulk copies (three 70 KB stages), warp 1 owns the
-// tensor memory and issues the products (one thread), warps 2..9 run the epilogue.
+// tensor memory and issues the products (one thread), warps 2..17 run the epilogue (four per
+// 32-lane quarter of the tensor memory, 8 columns each).
 namespace tcg {
 constexpr int BM = 128, BN = 32;
 constexpr int TST = 3;                         // staging ring depth
@@ -464,7 +530,11 @@ constexpr int A_BYTES = NS * BM * TK * 2;      // 7 slices x 128 rows x 64 B
 constexpr int B_BYTES = NS * BN * TK * 2;      // 7 slices x 32 rows x 64 B
 constexpr int STAGE = A_BYTES + B_BYTES;       // 70 KB
 constexpr int PIECE = 4;                       // K chunks of 32 per accumulation piece
-constexpr int EPI_WARPS = 8;
+#ifndef TC_EPI_WARPS
+#define TC_EPI_WARPS 16
+#endif
+constexpr int EPI_WARPS = TC_EPI_WARPS;        // epilogue warps: EPI_WARPS / 4 per lane quarter
+constexpr int EC = BN / (EPI_WARPS / 4);       // columns per epilogue thread
 constexpr int THREADS = (2 + EPI_WARPS) * 32;
 constexpr int SMEM = TST * STAGE + 1024;       // + alignment slack
 constexpr uint32_t TMEM_COLS = 512;
@@ -555,7 +625,7 @@ __device__ __forceinline__ TcTile tc_decode(const GemmJob *jobs, const int64_t *
 
 __global__ void __launch_bounds__(tcg::THREADS, 1)
     k_gemm_tc(const __half *sl, const int32_t *ex, double *C, const GemmJob *jobs, const int64_t *pre, int njobs,
-              double alpha, double beta, int *err, const int32_t *skip) {
+              const Scale sc, int *err, const int32_t *skip) {
     using namespace tcg;
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t full[TST], empty[TST], tfull[2], tempty[2], done;
@@ -667,7 +737,7 @@ __global__ void __launch_bounds__(tcg::THREADS, 1)
             }
         }
     } else {
-        // ---------------- epilogue: rows 32 (warp % 4) + lane, 16 columns per warp
+        // ---------------- epilogue: rows 32 (warp % 4) + lane, EC columns per warp
         const int qd = warp & 3, cg = (warp - 2) >> 2;
         const int row = 32 * qd + lane;
         const uint32_t tq = tbase + ((uint32_t)(32 * qd) << 16);
@@ -676,9 +746,9 @@ __global__ void __launch_bounds__(tcg::THREADS, 1)
             if (!active(t)) continue;
             const TcTile T = tc_decode(jobs, pre, njobs, t);
             const GemmJob &J = jobs[T.job];
-            int64_t hi[16], lo[16];
+            int64_t hi[EC], lo[EC];
 #pragma unroll
-            for (int j = 0; j < 16; j++) hi[j] = lo[j] = 0;
+            for (int j = 0; j < EC; j++) hi[j] = lo[j] = 0;
             bool ok = true;
             for (int c0 = 0; c0 < T.nch; c0 += PIECE, pc++) {
                 const int b = (int)(pc & 1);
@@ -689,11 +759,11 @@ __global__ void __launch_bounds__(tcg::THREADS, 1)
                 }
                 tc_fence_after();
 #pragma unroll
-                for (int h = 0; h < 2; h++) {
+                for (int h = 0; h < EC / 8; h++) {
                     float v[NS][8];
 #pragma unroll
                     for (int d = 0; d < NS; d++)
-                        tm_ld8(tq + (uint32_t)b * 256u + 32u * d + 16u * cg + 8u * h, v[d]);
+                        tm_ld8(tq + (uint32_t)b * 256u + 32u * d + (uint32_t)(EC * cg) + 8u * h, v[d]);
                     tm_wait_ld();
 #pragma unroll
                     for (int j = 0; j < 8; j++) {
@@ -714,19 +784,32 @@ __global__ void __launch_bounds__(tcg::THREADS, 1)
             if (i >= J.M) continue;
             const int ea = ex[J.a_exp + i] - 62;
             double *crow = C + J.c_off + (int64_t)i * J.crs;
-            const int j0 = T.tn * BN + 16 * cg;
-            double cv[16];
+            const int j0 = T.tn * BN + EC * cg;
+            double cv[EC];
+            int eb[EC];
 #pragma unroll
-            for (int j = 0; j < 16; j++) {
+            for (int j = 0; j < EC; j++) {
                 const int jj = j0 + j;
-                cv[j] = (beta != 0.0 && jj < J.N && !(J.lower && i < jj)) ? crow[(int64_t)jj * J.ccs] : 0.0;
+                const bool in = jj < J.N && !(J.lower && i < jj);
+                cv[j] = (sc.bmode != 0 && in) ? crow[(int64_t)jj * J.ccs] : 0.0;
+                eb[j] = jj < J.N ? ex[J.b_exp + jj] : 0;
             }
+            // C = beta C + alpha v 2^e: v rounded once, then the (FP64) update of C
 #pragma unroll
-            for (int j = 0; j < 16; j++) {
+            for (int j = 0; j < EC; j++) {
                 const int jj = j0 + j;
                 if (jj >= J.N || (J.lower && i < jj)) continue;
-                const __int128 vv = ((__int128)hi[j] << 32) + (__int128)lo[j];
-                crow[(int64_t)jj * J.ccs] = combine_out(vv, ea + ex[J.b_exp + jj], alpha, beta, cv[j]);
+                int e = ea + eb[j];
+                if (sc.pow2) {
+                    e += sc.e2 - 1;
+                    if (sc.neg) {
+                        hi[j] = -hi[j];
+                        lo[j] = -lo[j];
+                    }
+                }
+                double r = limbs_to_double(hi[j], lo[j], e);
+                if (!sc.pow2) r *= sc.alpha;
+                crow[(int64_t)jj * J.ccs] = sc.bmode == 0 ? r : sc.bmode == 1 ? cv[j] + r : fma(sc.beta, cv[j], r);
             }
         }
     }
@@ -816,7 +899,8 @@ static void gemm_tc(const __half *slices, const int32_t *exps, double *C, const 
     KTime kt(KC_TC_GEMM, s, fl);
     CK(cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tcg::SMEM));
     const unsigned grid = (unsigned)std::min<int64_t>(total, device_sms());
-    k_gemm_tc<<<grid, tcg::THREADS, tcg::SMEM, s>>>(slices, exps, C, dj, dp, (int)js.size(), alpha, beta, err, skip);
+    k_gemm_tc<<<grid, tcg::THREADS, tcg::SMEM, s>>>(slices, exps, C, dj, dp, (int)js.size(), make_scale(alpha, beta),
+                                                    err, skip);
     CK_LAUNCH();
 }
 
