@@ -4,7 +4,8 @@
 // Per panel of PNB columns (LAPACK's latrd/sytrd organisation):
 //   * column j is brought up to date with the panel's earlier reflectors
 //     (a -= V W(j,:)^T + W V(j,:)^T), its Householder reflector is formed (d_j, e_j, tau_j);
-//   * y = A22 v, A22 the trailing matrix as it stood before the panel, read once over its lower
+//   * y = A22 v, A22 the trailing matrix as it stood before the panel (split once per panel into
+//     FP32 pairs, products in double-float arithmetic on the FP32 pipe), read once over its lower
 //     triangle by 64 x 64 tiles spread over the whole GPU; every tile writes its two partial
 //     products (the tile and its transpose) to its own slot and one CTA per matrix sums the
 //     slots in a fixed order, so the result does not depend on scheduling;
@@ -22,6 +23,52 @@ namespace {
 
 constexpr int PNB = 32;   // reflectors per panel (the rank-2k update has K = 64)
 constexpr int ST = 64;    // tile of the symmetric product
+
+// The symmetric products y = A22 v carry two multiply-adds per stored entry, which would keep
+// this GPU's FP64 pipe (1/64 of the FP32 rate) saturated below a third of the memory bandwidth.
+// They run instead in double-float arithmetic on the FP32 pipe: every entry of A22 and v is
+// split into an FP32 pair hi + lo holding its leading 48 bits (truncated; relative error below
+// 2^-47), products keep their exact FP32 rounding error (fma) and the three leading cross terms,
+// sums are error-free (two-sum) into a pair.  The per-tile results are rounded to FP64 once.
+// For |x| < 2^-78 the low part underflows (absolute error below 2^-126) and below 2^-126 the
+// entry is flushed to zero: the reduced matrices C = L^-1 S L^-T have norm of order one, so this
+// is far below their FP64 rounding.
+__device__ __forceinline__ float2 df_split(double x) {
+    const uint64_t b = (uint64_t)__double_as_longlong(x);
+    const uint32_t sgn = (uint32_t)(b >> 32) & 0x80000000u;
+    const int e = (int)((b >> 52) & 0x7ff);                 // biased FP64 exponent
+    const uint64_t m = b & 0xfffffffffffffull;              // 52 fraction bits
+    const int fe = e - 896;                                  // FP32 biased exponent of hi
+    if (fe <= 0) return make_float2(0.f, 0.f);
+    if (fe >= 255) return make_float2(__uint_as_float(sgn | 0x7f800000u), 0.f);
+    const uint32_t hib = sgn | ((uint32_t)fe << 23) | (uint32_t)(m >> 29);
+    const uint32_t r = (uint32_t)(m & 0x1fffffffull);        // the 29 bits below hi: r 2^(e - 1075)
+    const int lz = __clz((int)r) - 3;                        // r's top bit at 28 - lz
+    const int le = 28 - lz + e - 1075 + 127;                 // FP32 biased exponent of lo
+    const uint32_t lm = lz >= 5 ? (r << (lz - 5)) : (r >> (5 - lz));
+    const uint32_t lob = (r == 0u || le <= 0) ? 0u : (sgn | ((uint32_t)le << 23) | (lm & 0x7fffffu));
+    return make_float2(__uint_as_float(hib), __uint_as_float(lob));
+}
+// (sh, sl) += a v
+__device__ __forceinline__ void df_mac(float &sh, float &sl, float2 a, float2 v) {
+    const float p = __fmul_rn(a.x, v.x);
+    float e = fmaf(a.x, v.x, -p);
+    e = fmaf(a.x, v.y, e);
+    e = fmaf(a.y, v.x, e);
+    const float t = __fadd_rn(sh, p);
+    const float bv = __fsub_rn(t, sh);
+    const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bv)), __fsub_rn(p, bv));
+    sl = __fadd_rn(sl, __fadd_rn(err, e));
+    sh = t;
+}
+// (sh, sl) += (oh, ol)
+__device__ __forceinline__ void df_add(float &sh, float &sl, float oh, float ol) {
+    const float t = __fadd_rn(sh, oh);
+    const float bv = __fsub_rn(t, sh);
+    const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bv)), __fsub_rn(oh, bv));
+    sl = __fadd_rn(sl, __fadd_rn(err, ol));
+    sh = t;
+}
 
 __device__ double trd_block_sum(double v, double *red) {
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -204,73 +251,131 @@ __device__ __forceinline__ int trd_find(const int64_t *pre, int64_t count, int64
 }
 
 __device__ __forceinline__ void trd_tri(int64_t t, int &ti, int &tj) {
-    int i = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    int i = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);   // corrected below
     while ((int64_t)(i + 1) * (i + 2) / 2 <= t) i++;
     while ((int64_t)i * (i + 1) / 2 > t) i--;
     ti = i;
     tj = (int)(t - (int64_t)i * (i + 1) / 2);
 }
 
+// (hi, lo) FP32 pairs of the trailing lower triangle (rows and columns >= j0) of every matrix,
+// column-major with leading dimension n: the operand of the panel's symmetric products (the
+// trailing matrix is the same for all column steps of a panel, so it is split once per panel)
+__global__ void __launch_bounds__(256) k_trd_pairs(const double *base, const int64_t *off, const int32_t *ld,
+                                                   const int32_t *nn, int64_t count, int j0, float2 *F,
+                                                   const int64_t *foff) {
+    const int64_t b = blockIdx.y;
+    if (b >= count) return;
+    const int n = nn[b], L = ld[b];
+    const int c = j0 + (int)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (c >= n) return;
+    const double *A = base + off[b] + (int64_t)c * L;
+    float2 *Fc = F + foff[b] + (int64_t)c * n;
+    for (int r = c + (threadIdx.x & 31); r < n; r += 32) Fc[r] = df_split(A[r]);
+}
+
 // partial products of the 64 x 64 tiles of the trailing lower triangle with v: slot (ti, tj)
 // holds A22(ti, tj) v(tj) (the diagonal tile as the full symmetric block), slot (tj, ti) holds
-// A22(ti, tj)^T v(ti)
-__global__ void __launch_bounds__(256) k_trd_symv(const double *base, const int64_t *off, const int32_t *ld,
-                                                  const int32_t *nn, int64_t count, int j, const int64_t *toff,
-                                                  const double *vbuf, double *P, const int64_t *poff,
-                                                  const int64_t *pre) {
-    __shared__ double tile[ST][ST + 1];
-    __shared__ double vr[ST], vc[ST];
+// A22(ti, tj)^T v(ti).  CTA c takes the contiguous tile range [c total / grid, (c + 1) total /
+// grid) of the batch (tiles of a matrix in row order, matrices in batch order): the matrix of
+// its first tile is found once (32-way search by one warp), then tiles and matrices advance
+// incrementally, and the loads of the next tile are in flight while the current one is used.
+__global__ void __launch_bounds__(256, 4) k_trd_symv(const float2 *F, const int64_t *foff, const int32_t *nn,
+                                                     int64_t count, int j, const int64_t *toff, const double *vbuf,
+                                                     double *P, const int64_t *poff, const int64_t *pre) {
+    // rows padded to 68 pairs: the 16 threads of a half-warp read 16 distinct 8-byte banks both
+    // along rows and along columns
+    __shared__ float2 tile[ST][ST + 4];
+    __shared__ float2 vr[ST], vc[ST];
+    __shared__ int s_b;
+    constexpr int PER = ST * ST / 256;
     const int64_t total = pre[count];
+    const int64_t w0 = total * blockIdx.x / gridDim.x, w1 = total * (blockIdx.x + 1) / gridDim.x;
+    if (w0 >= w1) return;
+    if (threadIdx.x < 32) {
+        // largest b with pre[b] <= w0 (then pre[b + 1] > w0: the matrix holding tile w0)
+        const int lane = threadIdx.x;
+        int64_t lo = 0, hi = count - 1;
+        while (hi > lo) {
+            const int64_t step = (hi - lo + 32) / 32;
+            const int64_t cand = lo + lane * step;
+            const unsigned ok = __ballot_sync(0xffffffffu, cand <= hi && pre[cand] <= w0);
+            lo += (int64_t)(31 - __clz((int)ok)) * step;
+            hi = min(hi, lo + step - 1);
+        }
+        if (lane == 0) s_b = (int)lo;
+    }
+    __syncthreads();
     const int lane4 = threadIdx.x & 3, idx = threadIdx.x >> 2;   // 64 groups of 4 threads
-    for (int64_t w = blockIdx.x; w < total; w += gridDim.x) {
-        const int b = trd_find(pre, count, w);
-        int ti, tj;
-        trd_tri(w - pre[b], ti, tj);
-        const int n = nn[b], L = ld[b], m = n - j - 1;
-        const int T = (m + ST - 1) / ST;
-        const double *A22 = base + off[b] + (j + 1) + (int64_t)(j + 1) * L;
-        const double *v = vbuf + toff[b] + (j + 1);
+    // state of the tile being loaded
+    int b = s_b, ti, tj;
+    trd_tri(w0 - pre[b], ti, tj);
+    int L = nn[b], m = L - j - 1, T = (m + ST - 1) / ST;
+    const float2 *A22 = F + foff[b] + (j + 1) + (int64_t)(j + 1) * L;
+    const double *v = vbuf + toff[b] + (j + 1);
+    float2 a[PER];
+    double vx = 0.0;
+    auto issue = [&]() {
         const int r0 = ti * ST, c0 = tj * ST;
-        {
-            // all 16 loads of a thread in flight before any shared-memory store
-            constexpr int PER = ST * ST / 256;
-            double a[PER];
 #pragma unroll
-            for (int u = 0; u < PER; u++) {
-                const int t = threadIdx.x + 256 * u;
-                const int rr = t % ST, cc = t / ST;
-                const int gr = r0 + rr, gc = c0 + cc;
-                a[u] = (gr < m && gc < m && gr >= gc) ? A22[gr + (int64_t)gc * L] : 0.0;
-            }
+        for (int u = 0; u < PER; u++) {
+            const int t = threadIdx.x + 256 * u;
+            const int rr = t % ST, cc = t / ST;
+            const int gr = r0 + rr, gc = c0 + cc;
+            a[u] = (gr < m && gc < m && gr >= gc) ? A22[gr + (int64_t)gc * L] : make_float2(0.f, 0.f);
+        }
+        if (threadIdx.x < 2 * ST) {
+            const int k = (threadIdx.x < ST ? r0 : c0 - ST) + threadIdx.x;
+            vx = k < m ? v[k] : 0.0;
+        }
+    };
+    issue();
+    for (int64_t w = w0; w < w1; w++) {
 #pragma unroll
-            for (int u = 0; u < PER; u++) {
-                const int t = threadIdx.x + 256 * u;
-                tile[t % ST][t / ST] = a[u];
-            }
+        for (int u = 0; u < PER; u++) {
+            const int t = threadIdx.x + 256 * u;
+            tile[t % ST][t / ST] = a[u];
         }
-        for (int t = threadIdx.x; t < ST; t += blockDim.x) {
-            vr[t] = (r0 + t < m) ? v[r0 + t] : 0.0;
-            vc[t] = (c0 + t < m) ? v[c0 + t] : 0.0;
-        }
+        if (threadIdx.x < ST) vr[threadIdx.x] = df_split(vx);
+        else if (threadIdx.x < 2 * ST) vc[threadIdx.x - ST] = df_split(vx);
         __syncthreads();
-        const bool diag = (ti == tj);
+        const int cti = ti, ctj = tj, cT = T;
+        const int64_t cpo = poff[b];
+        // next tile: advance within the matrix, else to the next non-empty matrix
+        if (w + 1 < w1) {
+            if (++tj > ti) {
+                tj = 0;
+                if (++ti >= T) {
+                    do b++; while (pre[b + 1] <= w + 1);
+                    ti = 0;
+                    L = nn[b];
+                    m = L - j - 1;
+                    T = (m + ST - 1) / ST;
+                    A22 = F + foff[b] + (j + 1) + (int64_t)(j + 1) * L;
+                    v = vbuf + toff[b] + (j + 1);
+                }
+            }
+            issue();
+        }
+        const bool diag = (cti == ctj);
         // row part: row idx, 16 columns per thread of the group
-        double rs = 0.0, cs = 0.0;
+        float rh = 0.f, rl = 0.f, ch = 0.f, cl = 0.f;
         for (int c = lane4; c < ST; c += 4) {
-            double a = tile[idx][c];
-            if (diag && c > idx) a = tile[c][idx];       // upper half of the diagonal tile by symmetry
-            rs += a * vc[c];
+            float2 x = tile[idx][c];
+            if (diag && c > idx) x = tile[c][idx];       // upper half of the diagonal tile by symmetry
+            df_mac(rh, rl, x, vc[c]);
         }
         if (!diag)
-            for (int r = lane4; r < ST; r += 4) cs += tile[r][idx] * vr[r];
-        rs += __shfl_xor_sync(0xffffffffu, rs, 1);
-        rs += __shfl_xor_sync(0xffffffffu, rs, 2);
-        cs += __shfl_xor_sync(0xffffffffu, cs, 1);
-        cs += __shfl_xor_sync(0xffffffffu, cs, 2);
+            for (int r = lane4; r < ST; r += 4) df_mac(ch, cl, tile[r][idx], vr[r]);
+#pragma unroll
+        for (int o = 1; o <= 2; o <<= 1) {
+            df_add(rh, rl, __shfl_xor_sync(0xffffffffu, rh, o), __shfl_xor_sync(0xffffffffu, rl, o));
+            df_add(ch, cl, __shfl_xor_sync(0xffffffffu, ch, o), __shfl_xor_sync(0xffffffffu, cl, o));
+        }
         if (lane4 == 0) {
-            double *Pb = P + poff[b];
-            Pb[((int64_t)ti * T + tj) * ST + idx] = rs;
-            if (!diag) Pb[((int64_t)tj * T + ti) * ST + idx] = cs;
+            double *Pb = P + cpo;
+            Pb[((int64_t)cti * cT + ctj) * ST + idx] = (double)rh + (double)rl;
+            if (!diag) Pb[((int64_t)ctj * cT + cti) * ST + idx] = (double)ch + (double)cl;
         }
         __syncthreads();
     }
@@ -365,10 +470,11 @@ void sytd2_batched(double *base, const MatBatch &Ab, double *d, double *e, doubl
                    cudaStream_t s) {
     if (Ab.count == 0 || Ab.maxn == 0) return;
     const int64_t cnt = Ab.count;
-    std::vector<int64_t> vwoff(cnt + 1, 0), poff(cnt + 1, 0);
+    std::vector<int64_t> vwoff(cnt + 1, 0), poff(cnt + 1, 0), fo(cnt + 1, 0);
     for (int64_t b = 0; b < cnt; b++) {
         const int64_t n = Ab.h_n[b];
         vwoff[b + 1] = vwoff[b] + 2 * PNB * n;
+        fo[b + 1] = fo[b] + n * n;
         const int64_t T = cdiv(std::max<int64_t>(n - 1, 1), ST);
         poff[b + 1] = poff[b] + T * T * ST;
     }
@@ -376,7 +482,10 @@ void sytd2_batched(double *base, const MatBatch &Ab, double *d, double *e, doubl
     std::vector<int64_t> partoff(cnt + 1, 0);
     for (int64_t b = 0; b < cnt; b++) partoff[b + 1] = partoff[b] + cdiv(Ab.h_n[b], RB) * PSL;
     DBuf<double> VW, WV, P, vbuf, ybuf, part, scal;
-    DBuf<int64_t> dvw, dpo, dpa, pre;
+    DBuf<int64_t> dvw, dpo, dpa, pre, dfo;
+    DBuf<float2> F;
+    F.alloc(std::max<int64_t>(fo[cnt], 1), s);
+    upload(dfo, std::vector<int64_t>(fo.begin(), fo.end() - 1), s);
     VW.alloc(std::max<int64_t>(vwoff[cnt], 1), s);
     WV.alloc(std::max<int64_t>(vwoff[cnt], 1), s);
     P.alloc(std::max<int64_t>(poff[cnt], 1), s);
@@ -392,9 +501,15 @@ void sytd2_batched(double *base, const MatBatch &Ab, double *d, double *e, doubl
     err.alloc(2, s);
     err.zero(s);
     oz::Workspace ws;
-    const unsigned symv_grid = 148 * 8;
+    const unsigned symv_grid = 148 * 4;   // one resident wave (4 CTAs of 256 threads per SM)
     for (int j0 = 0; j0 < Ab.maxn; j0 += PNB) {
         const int j1 = std::min(Ab.maxn, j0 + PNB);
+        {
+            KTime kt(KC_SYTD2, s);
+            const dim3 gp((unsigned)cdiv(Ab.maxn - j0, 8), (unsigned)cnt);
+            k_trd_pairs<<<gp, 256, 0, s>>>(base, Ab.off.p, Ab.ld.p, Ab.n.p, cnt, j0, F.p, dfo.p);
+            CK_LAUNCH();
+        }
         for (int j = j0; j < j1; j++) {
             // the FP64 column steps (the panel's rank-2k update is a tensor-core product): the
             // trailing lower triangle is read once per column by the symmetric product
@@ -415,8 +530,7 @@ void sytd2_batched(double *base, const MatBatch &Ab, double *d, double *e, doubl
             k_trd_c3<<<g3, RB, 0, s>>>(base, Ab.off.p, Ab.ld.p, Ab.n.p, cnt, j, j0, e, tau, toff, scal.p, VW.p, WV.p,
                                        dvw.p, vbuf.p, part.p, dpa.p);
             CK_LAUNCH();
-            k_trd_symv<<<symv_grid, 256, 0, s>>>(base, Ab.off.p, Ab.ld.p, Ab.n.p, cnt, j, toff, vbuf.p, P.p, dpo.p,
-                                                 pre.p);
+            k_trd_symv<<<symv_grid, 256, 0, s>>>(F.p, dfo.p, Ab.n.p, cnt, j, toff, vbuf.p, P.p, dpo.p, pre.p);
             CK_LAUNCH();
             k_trd_w2<<<g3, RB, 0, s>>>(Ab.n.p, cnt, j, j0, tau, toff, vbuf.p, P.p, dpo.p, VW.p, WV.p, dvw.p, ybuf.p,
                                        part.p, dpa.p);
