@@ -374,14 +374,16 @@ __device__ __forceinline__ bool wf_wait(const uint32_t *flag, uint32_t epoch, in
 }
 
 template <class T, bool FWD>
-__global__ void __launch_bounds__(256) k_tri_wave(const int32_t *tasks, int64_t ntask, const int32_t *sys,
+__global__ void __launch_bounds__(256, FWD ? 2 : 4) k_tri_wave(const int32_t *tasks, int64_t ntask, const int32_t *sys,
                                                   const int64_t *Optr, const T *Lp, const int64_t *Loff,
                                                   const double *Dp, const int64_t *Doff, const int64_t *Foff,
                                                   uint32_t *flags, uint32_t epoch, int cb, T *ws, int64_t wsn,
                                                   int nrhs, int *err) {
     __shared__ T yj[WF_RG][TRI_CB];
     __shared__ double tv[WF_RG][TRI_CB];
+    __shared__ double vo[WF_RG][TRI_CB];                    // this block of the right-hand sides
     __shared__ double red[8][WF_RG][TRI_CB];
+    __shared__ double sDi[TRI_CB * (TRI_CB + 1) / 2];       // inverted diagonal block
     __shared__ int s_ok;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int64_t q = blockIdx.x; q < ntask; q += gridDim.x) {
@@ -394,9 +396,20 @@ __global__ void __launch_bounds__(256) k_tri_wave(const int32_t *tasks, int64_t 
         const T *L = Lp + Loff[a];
         T *v = ws + ob;
         uint32_t *fl = flags + Foff[a];
-        const double *Di = Dp + Doff[a] + (int64_t)k * tri_block_words(cb);
+        {
+            // the inverted diagonal block is staged while the dependencies are consumed (it is
+            // needed only at the end of the task, on the critical path of the wavefront)
+            const double *Di = Dp + Doff[a] + (int64_t)k * tri_block_words(cb);
+            const int nw = nb * (nb + 1) / 2;
+            for (int t = threadIdx.x; t < nw; t += blockDim.x) sDi[t] = __ldg(Di + t);
+        }
         for (int g0 = 0; g0 < nrhs; g0 += WF_RG) {
             const int nr = min(WF_RG, nrhs - g0);
+            // own block of the right-hand sides: written only by this task
+            for (int t = threadIdx.x; t < nr * TRI_CB; t += blockDim.x) {
+                const int r = t / TRI_CB, c = t - r * TRI_CB;
+                vo[r][c] = (c < nb) ? (double)__ldcg(v + (int64_t)(g0 + r) * wsn + r0 + c) : 0.0;
+            }
             // per-warp partial sums over every dependency block: forward, rows warp + 8 i of the
             // block (each lane over two columns); backward, columns lane / lane + 32 (each warp
             // over rows warp + 8 i of the dependency block)
@@ -408,43 +421,38 @@ __global__ void __launch_bounds__(256) k_tri_wave(const int32_t *tasks, int64_t 
             const int jn = FWD ? k : K - 1 - k;          // dependency blocks
             for (int jj = 0; jj < jn; jj++) {
                 const int j = FWD ? jj : K - 1 - jj;
-                if (!wf_wait(fl + j, epoch, err, &s_ok)) return;
                 const int c0 = j * cb, nc = min(cb, n - c0);
+                // the factor block does not depend on the wavefront: its loads are in flight
+                // before the wait for block j
+                T lv[8][2];
+#pragma unroll
+                for (int i = 0; i < 8; i++) {
+                    const int ii = warp + 8 * i;
+#pragma unroll
+                    for (int u = 0; u < 2; u++) {
+                        const int c = lane + 32 * u;
+                        if (FWD) {   // L[r0 + i, c0 + c]: rows of this block, columns of block j
+                            const int64_t gi = (int64_t)r0 + ii;
+                            lv[i][u] = (ii < nb && c < nc) ? L[gi * (gi + 1) / 2 + c0 + c] : (T)0;
+                        } else {     // L[c0 + i, r0 + c]: rows of block j, columns of this block
+                            const int64_t gi = (int64_t)c0 + ii;
+                            lv[i][u] = (ii < nc && c < nb) ? L[gi * (gi + 1) / 2 + r0 + c] : (T)0;
+                        }
+                    }
+                }
+                if (!wf_wait(fl + j, epoch, err, &s_ok)) return;
                 for (int t = threadIdx.x; t < nr * TRI_CB; t += blockDim.x) {
                     const int r = t / TRI_CB, c = t - r * TRI_CB;
                     yj[r][c] = (c < nc) ? __ldcg(v + (int64_t)(g0 + r) * wsn + c0 + c) : (T)0;
                 }
                 __syncthreads();
-                T lv[8][2];
                 if (FWD) {
-                    // L[r0 + i, c0 + c]: rows of this block, columns of block j
-#pragma unroll
-                    for (int i = 0; i < 8; i++) {
-                        const int ii = warp + 8 * i;
-                        const int64_t gi = (int64_t)r0 + ii;
-#pragma unroll
-                        for (int u = 0; u < 2; u++) {
-                            const int c = lane + 32 * u;
-                            lv[i][u] = (ii < nb && c < nc) ? L[gi * (gi + 1) / 2 + c0 + c] : (T)0;
-                        }
-                    }
 #pragma unroll
                     for (int r = 0; r < WF_RG; r++)
                         if (r < nr)
 #pragma unroll
                             for (int i = 0; i < 8; i++) part[r][i] += lv[i][0] * yj[r][lane] + lv[i][1] * yj[r][lane + 32];
                 } else {
-                    // L[c0 + i, r0 + c]: rows of block j, columns of this block
-#pragma unroll
-                    for (int i = 0; i < 8; i++) {
-                        const int ii = warp + 8 * i;
-                        const int64_t gi = (int64_t)c0 + ii;
-#pragma unroll
-                        for (int u = 0; u < 2; u++) {
-                            const int c = lane + 32 * u;
-                            lv[i][u] = (ii < nc && c < nb) ? L[gi * (gi + 1) / 2 + r0 + c] : (T)0;
-                        }
-                    }
 #pragma unroll
                     for (int r = 0; r < WF_RG; r++)
                         if (r < nr)
@@ -459,18 +467,28 @@ __global__ void __launch_bounds__(256) k_tri_wave(const int32_t *tasks, int64_t 
             }
             // combine the partial sums: t = v_block - (L_block,deps . y_deps)
             if (FWD) {
+                // butterfly over the warp: the 32 sums (r, i) end one per lane, lane = 8 r + i
+                double x[WF_RG * 8];
 #pragma unroll
                 for (int r = 0; r < WF_RG; r++)
 #pragma unroll
-                    for (int i = 0; i < 8; i++) {
-                        double sacc = (double)part[r][i];
-                        for (int o = 16; o; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
-                        if (lane == 0) red[0][r][warp + 8 * i] = sacc;
+                    for (int i = 0; i < 8; i++) x[8 * r + i] = (double)part[r][i];
+#pragma unroll
+                for (int o = 16, c = WF_RG * 8; o >= 1; o >>= 1, c >>= 1) {
+                    const bool up = (lane & o) != 0;
+#pragma unroll
+                    for (int t = 0; t < c / 2; t++) {
+                        const double send = up ? x[t] : x[t + c / 2];
+                        const double keep = up ? x[t + c / 2] : x[t];
+                        x[t] = keep + __shfl_xor_sync(0xffffffffu, send, o);
                     }
+                }
+                static_assert(WF_RG * 8 == 32, "one partial sum per lane");
+                red[0][lane >> 3][warp + 8 * (lane & 7)] = x[0];
                 __syncthreads();
                 for (int t = threadIdx.x; t < nr * TRI_CB; t += blockDim.x) {
                     const int r = t / TRI_CB, i = t - r * TRI_CB;
-                    tv[r][i] = (i < nb) ? (double)__ldcg(v + (int64_t)(g0 + r) * wsn + r0 + i) - red[0][r][i] : 0.0;
+                    tv[r][i] = (i < nb) ? vo[r][i] - red[0][r][i] : 0.0;
                 }
             } else {
 #pragma unroll
@@ -484,7 +502,7 @@ __global__ void __launch_bounds__(256) k_tri_wave(const int32_t *tasks, int64_t 
                     double sacc = 0.0;
 #pragma unroll
                     for (int w = 0; w < 8; w++) sacc += red[w][r][c];
-                    tv[r][c] = (c < nb) ? (double)__ldcg(v + (int64_t)(g0 + r) * wsn + r0 + c) - sacc : 0.0;
+                    tv[r][c] = (c < nb) ? vo[r][c] - sacc : 0.0;
                 }
             }
             __syncthreads();
@@ -497,14 +515,14 @@ __global__ void __launch_bounds__(256) k_tri_wave(const int32_t *tasks, int64_t 
                 if (e < nb) {
                     if (FWD) {
                         for (int c = p; c <= e; c += 4) {
-                            const double d = Di[e * (e + 1) / 2 + c];
+                            const double d = sDi[e * (e + 1) / 2 + c];
 #pragma unroll
                             for (int r = 0; r < WF_RG; r++)
                                 if (r < nr) acc[r] += d * tv[r][c];
                         }
                     } else {
                         for (int i = e + p; i < nb; i += 4) {
-                            const double d = Di[i * (i + 1) / 2 + e];
+                            const double d = sDi[i * (i + 1) / 2 + e];
 #pragma unroll
                             for (int r = 0; r < WF_RG; r++)
                                 if (r < nr) acc[r] += d * tv[r][i];
