@@ -239,9 +239,10 @@ __global__ void __launch_bounds__(256) k_schwarz(const int32_t *aggs, int64_t na
 }
 
 // ---------------------------------------------------------------- transfers
-// rc[off_a + j] = sum_p Z_a[p, j] res[omega_a[p]] (P^T r, P = blockdiag R_omega^T Z_a).  One CTA
-// per aggregate: the 8 warps take interleaved rows of Z_a (coalesced, 4 rows in flight), lanes
-// take columns in chunks of 128, and the warps' partial sums are added in shared memory.
+// rc[off_a + j] = sum_p Z_a[p, j] res[omega_a[p]] (P^T r, P = blockdiag R_omega^T Z_a).  CTA
+// (x, a) takes the 128 columns 128 x .. of Z_a over all its rows: the 8 warps take interleaved
+// rows (coalesced, 4 rows in flight), lanes 4 x 32 columns, and the warps' partial sums are added
+// in shared memory in a fixed order.  Large coarse blocks are spread over several CTAs.
 template <class T>
 __global__ void __launch_bounds__(256) k_restrict(const int64_t *wptr, const int32_t *widx, const int32_t *k,
                                                   const int64_t *off, const T *Z, const int64_t *zoff,
@@ -249,42 +250,44 @@ __global__ void __launch_bounds__(256) k_restrict(const int64_t *wptr, const int
                                                   int nrhs) {
     __shared__ T red[8][128];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int64_t a = blockIdx.x; a < nagg; a += gridDim.x) {
+    const int j0 = (int)blockIdx.x * 128;
+    for (int64_t a = blockIdx.y; a < nagg; a += gridDim.y) {
         const int ka = k[a];
+        if (j0 >= ka) continue;
         const int64_t wb = wptr[a];
         const int nw = (int)(wptr[a + 1] - wb);
         const T *z = Z + zoff[a];
         for (int r = 0; r < nrhs; r++) {
             const T *rr = res + (int64_t)r * n;
-            for (int j0 = 0; j0 < ka; j0 += 128) {
-                T acc[4] = {0, 0, 0, 0};
+            T acc[4] = {0, 0, 0, 0};
 #pragma unroll 4
-                for (int p = warp; p < nw; p += 8) {
-                    const T rp = rr[widx[wb + p]];
-                    const T *zr = z + (int64_t)p * ka + j0;
+            for (int p = warp; p < nw; p += 8) {
+                const T rp = rr[widx[wb + p]];
+                const T *zr = z + (int64_t)p * ka + j0;
 #pragma unroll
-                    for (int u = 0; u < 4; u++) {
-                        const int j = lane + 32 * u;
-                        if (j0 + j < ka) acc[u] += zr[j] * rp;
-                    }
+                for (int u = 0; u < 4; u++) {
+                    const int j = lane + 32 * u;
+                    if (j0 + j < ka) acc[u] += zr[j] * rp;
                 }
-#pragma unroll
-                for (int u = 0; u < 4; u++) red[warp][lane + 32 * u] = acc[u];
-                __syncthreads();
-                if (threadIdx.x < 128 && j0 + (int)threadIdx.x < ka) {
-                    T sum = 0;
-#pragma unroll
-                    for (int w = 0; w < 8; w++) sum += red[w][threadIdx.x];
-                    rc[(int64_t)r * nc + off[a] + j0 + threadIdx.x] = sum;
-                }
-                __syncthreads();
             }
+#pragma unroll
+            for (int u = 0; u < 4; u++) red[warp][lane + 32 * u] = acc[u];
+            __syncthreads();
+            if (threadIdx.x < 128 && j0 + (int)threadIdx.x < ka) {
+                T sum = 0;
+#pragma unroll
+                for (int w = 0; w < 8; w++) sum += red[w][threadIdx.x];
+                rc[(int64_t)r * nc + off[a] + j0 + threadIdx.x] = sum;
+            }
+            __syncthreads();
         }
     }
 }
 
-// x[omega_a[p]] += sum_j Z_a[p, j] ec[off_a + j] (x += P e_c).  One CTA per aggregate, the coarse
-// values staged in shared memory, a warp per row of Z_a (4 rows in flight).
+// x[omega_a[p]] += sum_j Z_a[p, j] ec[off_a + j] (x += P e_c).  CTA (x, a) takes rows
+// TR_ROWS x .. of aggregate a: the coarse values staged in shared memory, a warp per row of Z_a
+// (4 rows in flight).
+constexpr int TR_ROWS = 64;
 template <class T>
 __global__ void __launch_bounds__(256) k_interp(const int64_t *wptr, const int32_t *widx, const int32_t *k,
                                                 const int64_t *off, const T *Z, const int64_t *zoff,
@@ -293,10 +296,13 @@ __global__ void __launch_bounds__(256) k_interp(const int64_t *wptr, const int32
     extern __shared__ unsigned char smraw[];
     T *e = reinterpret_cast<T *>(smraw);   // [max k]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int64_t a = blockIdx.x; a < nagg; a += gridDim.x) {
+    const int p0 = (int)blockIdx.x * TR_ROWS;
+    for (int64_t a = blockIdx.y; a < nagg; a += gridDim.y) {
         const int ka = k[a];
         const int64_t wb = wptr[a];
         const int nw = (int)(wptr[a + 1] - wb);
+        if (p0 >= nw || ka == 0) continue;
+        const int p1 = min(nw, p0 + TR_ROWS);
         const T *z = Z + zoff[a];
         for (int r = 0; r < nrhs; r++) {
             __syncthreads();
@@ -304,7 +310,7 @@ __global__ void __launch_bounds__(256) k_interp(const int64_t *wptr, const int32
             __syncthreads();
             T *xr = x + (int64_t)r * n;
 #pragma unroll 4
-            for (int p = warp; p < nw; p += 8) {
+            for (int p = p0 + warp; p < p1; p += 8) {
                 const T *zr = z + (int64_t)p * ka;
                 T sum = 0;
                 for (int j = lane; j < ka; j += 32) sum += zr[j] * e[j];
@@ -1035,23 +1041,25 @@ void vcycle(Handle &H, int l, int nrhs, cudaStream_t s) {
     const T *Z;
     if constexpr (std::is_same<T, float>::value) Z = L.Z32.p; else Z = L.Z64.p;
     {
-    KTime kt(KC_TRANSFER, s);
-    k_restrict<T><<<gridv(L.nagg, 1, 148 * 16), 256, 0, s>>>(L.wptr.p, L.widx.p, L.k.p, L.off.p, Z,
-                                                            L.zoff.p, L.nagg, r, L.n, bvec<T>(C),
-                                                            C.n, nrhs);
+    KTime kt(KC_TRANSFER, s, 0.0, L.transfer_bytes[std::is_same<T, double>::value ? 1 : 0] * nrhs);
+    const dim3 gr((unsigned)std::max<int64_t>(1, cdiv(L.max_k, 128)),
+                  (unsigned)std::max<int64_t>(1, std::min<int64_t>(L.nagg, 65535)));
+    k_restrict<T><<<gr, 256, 0, s>>>(L.wptr.p, L.widx.p, L.k.p, L.off.p, Z, L.zoff.p, L.nagg, r, L.n, bvec<T>(C),
+                                     C.n, nrhs);
     CK_LAUNCH();
     }
     vcycle<T>(H, l + 1, nrhs, s);
     {
-    KTime kt(KC_TRANSFER, s);
+    KTime kt(KC_TRANSFER, s, 0.0, L.transfer_bytes[std::is_same<T, double>::value ? 1 : 0] * nrhs);
     const size_t ism = (size_t)std::max(1, L.max_k) * sizeof(T);
     if (ism > 48 * 1024) {
         if (ism > 227 * 1024) fail(LSAMG_LIMIT, "coarse block too large for the interpolation kernel");
         CK(cudaFuncSetAttribute(k_interp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism));
     }
-    k_interp<T><<<gridv(L.nagg, 1, 148 * 16), 256, ism, s>>>(L.wptr.p, L.widx.p, L.k.p, L.off.p, Z,
-                                                          L.zoff.p, L.nagg, xvec<T>(C), C.n, x,
-                                                          L.n, nrhs);
+    const dim3 gi((unsigned)std::max<int64_t>(1, cdiv(L.max_nw, TR_ROWS)),
+                  (unsigned)std::max<int64_t>(1, std::min<int64_t>(L.nagg, 65535)));
+    k_interp<T><<<gi, 256, ism, s>>>(L.wptr.p, L.widx.p, L.k.p, L.off.p, Z, L.zoff.p, L.nagg, xvec<T>(C), C.n, x,
+                                     L.n, nrhs);
     CK_LAUNCH();
     }
     // residual after the coarse correction: r = b - A x

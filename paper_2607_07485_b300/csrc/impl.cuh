@@ -72,6 +72,8 @@ struct Level {
     DBuf<float> Z32;
     std::vector<int32_t> h_k;
     int32_t max_k = 0;                 // largest k_i (shared-memory staging of the interpolation)
+    int32_t max_nw = 0;                // largest |omega_i|
+    double transfer_bytes[2] = {0.0, 0.0};   // bytes of one restriction (or interpolation), FP32 / FP64
     std::vector<double> h_gap;
     DBuf<int32_t> cgroup;   // [ne] coarse element of each element (-1 if none)
     // multiplicative Schwarz smoother

@@ -1,6 +1,5 @@
 // FP64 products on FP16 tensor cores by exact splitting (see ozaki.cuh for the scheme).
 #include <cmath>
-#include <cstdlib>
 #include <cstring>
 
 #include "ozaki.cuh"
@@ -8,10 +7,6 @@
 namespace lsamg {
 namespace oz {
 namespace {
-
-constexpr int NST = 3;                         // staging ring depth
-constexpr int STAGE_BYTES = 2 * NS * BLK * 2;  // A and B slices of one K chunk
-constexpr int GEMM_SMEM = NST * STAGE_BYTES + 64;
 
 __device__ __forceinline__ int dcdiv(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
@@ -153,109 +148,6 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
                  "l"(src), "r"(bytes), "r"(smem_u32(bar))
                  : "memory");
 }
-__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], uint32_t addr) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(addr));
-}
-__device__ __forceinline__ void mma16816(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-__device__ __forceinline__ void tri_index(int64_t t, int &ti, int &tj) {
-    int i = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-    while ((int64_t)(i + 1) * (i + 2) / 2 <= t) i++;
-    while ((int64_t)i * (i + 1) / 2 > t) i--;
-    ti = i;
-    tj = (int)(t - (int64_t)i * (i + 1) / 2);
-}
-
-// v 2^e rounded to nearest (ties to even), negated if neg: integer instructions only while the
-// result is a normal FP64 number (the FP64 pipe of this GPU is 1/64 of its FP32 rate)
-__device__ __forceinline__ double i128_to_double(__int128 v, int e, bool neg) {
-    if (v == 0) return 0.0;
-    if (v < 0) { v = -v; neg = !neg; }
-    const unsigned __int128 m = (unsigned __int128)v;
-    const uint64_t h = (uint64_t)(m >> 64), l = (uint64_t)m;
-    int p = h ? 127 - __clzll((long long)h) : 63 - __clzll((long long)l);   // top bit
-    uint64_t mant;
-    if (p <= 52) {
-        mant = l << (52 - p);
-    } else {
-        const int sh = p - 52;
-        const unsigned __int128 qq = m >> sh;
-        const unsigned __int128 rem = m - (qq << sh);
-        const unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
-        mant = (uint64_t)qq;
-        if (rem > half || (rem == half && (mant & 1ull))) {
-            mant++;
-            if (mant == (1ull << 53)) { mant >>= 1; p++; }
-        }
-    }
-    const int E = p + e;
-    if (E > 1023 || E < -1022) {
-        const double r = ldexp((double)mant, p - 52 + e);
-        return neg ? -r : r;
-    }
-    const uint64_t bits = ((uint64_t)(E + 1023) << 52) | (mant & ((1ull << 52) - 1)) | (neg ? (1ull << 63) : 0ull);
-    return __longlong_as_double((long long)bits);
-}
-
-// c + v 2^e for a 128-bit integer v (|v| < 2^100) rounded once: c's significand joins the integer
-// sum at the common unit when both fit in 127 bits (otherwise one operand is below the other's
-// rounding and an FP64 add of the rounded v is exact to the last bit's rounding)
-__device__ __forceinline__ double i128_add_double(__int128 v, int e, double c) {
-    const uint64_t cb = (uint64_t)__double_as_longlong(c);
-    int ec = (int)((cb >> 52) & 0x7ff);
-    if (ec == 0x7ff) return c + i128_to_double(v, e, false);          // inf / nan propagate
-    int64_t mc = (int64_t)(cb & ((1ull << 52) - 1));
-    if (ec) mc |= 1ll << 52; else ec = 1;
-    if (mc == 0) return i128_to_double(v, e, false);
-    if (v == 0) return c;
-    if (cb >> 63) mc = -mc;
-    const int E = ec - 1075;                                           // c = mc 2^E
-    const unsigned __int128 av = (unsigned __int128)(v < 0 ? -v : v);
-    const uint64_t vh = (uint64_t)(av >> 64), vl = (uint64_t)av;
-    const int vb = vh ? 128 - __clzll((long long)vh) : 64 - __clzll((long long)vl);   // bits of |v|
-    const int d = E - e;
-    if (d >= 0 && d <= 126 - 53) return i128_to_double(v + ((__int128)mc << d), e, false);
-    if (d < 0 && vb - d <= 126) return i128_to_double((v << (-d)) + (__int128)mc, E, false);
-    return c + i128_to_double(v, e, false);
-}
-
-// epilogue of one output: C = beta C + alpha 2^e sum_d 2^-8(d-2) S_d (S_2..S_6 exact, tail = S_7 +
-// S_8 / 256), the sum formed exactly as a 128-bit integer in units of 2^-48; with beta = 1 the old C
-// joins the integer sum exactly and the result is rounded once.  FP64 instructions are scarce on
-// this GPU: none in the common cases (alpha a power of two, beta 0 or 1).  Kept out of line: the
-// product loop's registers are not needed here.
-__device__ __forceinline__ double combine_out(__int128 v, int e, double alpha, double beta, double c);
-
-__device__ __noinline__ void store_out(double *cp, int32_t s2, int32_t s3, int32_t s4, int32_t s5, int32_t s6,
-                                       float tail, int e, double alpha, double beta) {
-    const __int128 v = ((__int128)s2 << 48) + ((__int128)s3 << 40) + ((__int128)s4 << 32) + ((__int128)s5 << 24) +
-                       ((__int128)s6 << 16) + (__int128)__float2ll_rn(tail * 256.0f);
-    *cp = combine_out(v, e, alpha, beta, beta == 0.0 ? 0.0 : *cp);
-}
-
-// beta c + alpha v 2^e, rounded once when alpha is a power of two and beta is 0 or 1 (integer
-// instructions only), else through FP64 arithmetic
-__device__ __forceinline__ double combine_out(__int128 v, int e, double alpha, double beta, double c) {
-    int e2;
-    const double fr = frexp(fabs(alpha), &e2);
-    if (fr != 0.5) {
-        const double val = alpha * i128_to_double(v, e, false);
-        return (beta == 0.0) ? val : (beta == 1.0) ? c + val : fma(beta, c, val);
-    }
-    if (alpha < 0.0) v = -v;
-    e += e2 - 1;
-    if (beta == 0.0) return i128_to_double(v, e, false);
-    if (beta == 1.0) return i128_add_double(v, e, c);
-    return fma(beta, c, i128_to_double(v, e, false));
-}
-
 // alpha and beta of a product, classified once on the host: the epilogue then runs on integer
 // instructions only when alpha is a power of two (pow2, 2^(e2 - 1) with sign neg) and beta is 0
 // or 1 (bmode 0 / 1; 2: general beta)
@@ -275,18 +167,6 @@ inline Scale make_scale(double alpha, double beta) {
     sc.bmode = beta == 0.0 ? 0 : beta == 1.0 ? 1 : 2;
     return sc;
 }
-__device__ __forceinline__ double combine_scaled(__int128 v, int e, const Scale &sc, double c) {
-    if (sc.pow2) {
-        if (sc.neg) v = -v;
-        e += sc.e2 - 1;
-        if (sc.bmode == 0) return i128_to_double(v, e, false);
-        if (sc.bmode == 1) return i128_add_double(v, e, c);
-        return fma(sc.beta, c, i128_to_double(v, e, false));
-    }
-    const double val = sc.alpha * i128_to_double(v, e, false);
-    return sc.bmode == 0 ? val : sc.bmode == 1 ? c + val : fma(sc.beta, c, val);
-}
-
 // v 2^e rounded to nearest (ties to even) for the 96-bit integer v = hi 2^32 + lo given as two
 // 64-bit limbs (|hi| < 2^62).  Branch-free integer instructions while the result is a normal
 // number, so that the compiler interleaves the conversions of a thread's outputs.
@@ -318,196 +198,6 @@ __device__ __forceinline__ double limbs_to_double(int64_t hi, int64_t lo, int e)
     }
     return __longlong_as_double(
         (long long)(((uint64_t)(E + 1023) << 52) | (mant & ((1ull << 52) - 1)) | (neg ? (1ull << 63) : 0ull)));
-}
-
-// 16 warps per CTA, warp tile 16 x 16 (one m16 tile, two n8 tiles): every slice's fragments
-// of a 16-wide K step fit in registers (56), with per-diagonal exact int32 sums for the diagonals
-// 2..6 and one FP32 sum for the two lowest-weight diagonals (S_7 + S_8 / 256, weights 2^-40 and
-// 2^-48 of the leading one: with at most 256 K steps per product its rounding stays below
-// 2^-75 of the leading unit times K, under the FP64 dot-product bound).
-constexpr int GW = 16;               // warps per CTA
-constexpr int GT = GW * 32;          // threads per CTA
-
-// A product tile: its job, 64-row tiles of C and the operands' slice blocks
-struct TileRef {
-    int job, tm, tn, c0, nch;
-    const __half *gA, *gB;
-    int64_t pA, pB;
-};
-
-__device__ __forceinline__ TileRef decode_tile(const __half *sl, const GemmJob *jobs, const int64_t *pre, int njobs,
-                                               int64_t t) {
-    TileRef r;
-    r.job = find_job(pre, njobs, t);
-    const GemmJob &J = jobs[r.job];
-    const int64_t local = t - pre[r.job];
-    const int tilesN = dcdiv(J.N, TM);
-    if (J.lower) tri_index(local, r.tm, r.tn);
-    else { r.tm = (int)(local / tilesN); r.tn = (int)(local % tilesN); }
-    const int ntot = dcdiv(max(J.ktot, 1), TK);          // chunks of the split operands
-    r.c0 = J.k0 / TK;                                    // this pass's chunk range
-    r.nch = dcdiv(max(J.K, 1), TK);
-    r.gA = sl + J.a_off + (int64_t)r.tm * ntot * BLK;
-    r.gB = sl + J.b_off + (int64_t)r.tn * ntot * BLK;
-    r.pA = stor_tiles(J.M) * ntot * BLK;
-    r.pB = stor_tiles(J.N) * ntot * BLK;
-    return r;
-}
-
-// Persistent: CTA b takes tiles b, b + grid, ... (tiles of skipped jobs left out); thread 0 keeps
-// the bulk-copy ring NST chunks ahead across tile boundaries, so the next tile's operands arrive
-// while the current tile's epilogue runs.
-__global__ void __launch_bounds__(GT, 1) k_gemm(const __half *sl, const int32_t *ex, double *C,
-                                                const GemmJob *jobs, const int64_t *pre, int njobs, double alpha,
-                                                double beta, int *err, const int32_t *skip) {
-    extern __shared__ __align__(1024) unsigned char smem[];
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + NST * STAGE_BYTES);
-    __shared__ int s_bad;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t total = pre[njobs];
-    auto active = [&](int64_t t) {
-        if (!skip) return true;
-        return skip[jobs[find_job(pre, njobs, t)].skip_idx] < 0;
-    };
-    if (tid == 0) {
-        for (int st = 0; st < NST; st++) mbar_init(&full[st], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        s_bad = 0;
-    }
-    __syncthreads();
-    // producer state (thread 0, kept in shared memory to spare registers): the next (tile, chunk)
-    // to stage and the number of chunks staged so far
-    __shared__ int64_t s_ptile, s_issued;
-    __shared__ int s_pchunk;
-    __shared__ TileRef s_pref;
-    auto prod_advance_tile = [&]() {
-        int64_t t = s_ptile;
-        while (t < total && !active(t)) t += gridDim.x;
-        s_ptile = t;
-        if (t < total) s_pref = decode_tile(sl, jobs, pre, njobs, t);
-    };
-    auto issue_next = [&]() {
-        if (s_ptile >= total) return;
-        const int st = (int)(s_issued % NST);
-        unsigned char *sb = smem + st * STAGE_BYTES;
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_expect_tx(&full[st], STAGE_BYTES);
-        const TileRef &P = s_pref;
-        const int64_t cc = P.c0 + s_pchunk;
-        for (int p = 0; p < NS; p++) {
-            bulk_g2s(sb + p * BLK * 2, P.gA + p * P.pA + cc * BLK, BLK * 2, &full[st]);
-            bulk_g2s(sb + (NS + p) * BLK * 2, P.gB + p * P.pB + cc * BLK, BLK * 2, &full[st]);
-        }
-        s_issued++;
-        if (++s_pchunk == P.nch) {
-            s_pchunk = 0;
-            s_ptile += gridDim.x;
-            prod_advance_tile();
-        }
-    };
-    if (tid == 0) {
-        s_ptile = blockIdx.x;
-        s_issued = 0;
-        s_pchunk = 0;
-        prod_advance_tile();
-        for (int k = 0; k < NST; k++) issue_next();
-    }
-
-    const int wm = warp >> 2, wn = warp & 3;     // warp tile: rows wm*16.., cols wn*16..
-    // ldmatrix row / 16-byte chunk of this lane: the A tile (16 rows x 16 k), the B pair of n8 tiles
-    const int arow = lane & 15, akc = lane >> 4;
-    const int brow = ((lane >> 4) << 3) + (lane & 7), bkc = (lane >> 3) & 1;
-    constexpr int NI = ND - 3;                   // exact int32 diagonals 2 .. 6
-    int64_t consumed = 0;
-    for (int64_t tile = blockIdx.x; tile < total; tile += gridDim.x) {
-        if (!active(tile)) continue;
-        const TileRef T = decode_tile(sl, jobs, pre, njobs, tile);
-        const GemmJob &J = jobs[T.job];
-        int32_t iacc[NI][2][4];
-        float tail[2][4];
-#pragma unroll
-        for (int b = 0; b < 2; b++)
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-                tail[b][q] = 0.f;
-#pragma unroll
-                for (int d = 0; d < NI; d++) iacc[d][b][q] = 0;
-            }
-        for (int c = 0; c < T.nch; c++, consumed++) {
-            const int st = (int)(consumed % NST);
-            const uint32_t parity = (uint32_t)((consumed / NST) & 1);
-            if (tid == 0 && !mbar_wait_bounded(&full[st], parity, 2000000000ull)) s_bad = 1;
-            __syncthreads();
-            if (s_bad) {
-                if (tid == 0) {
-                    flag_error(err, LSAMG_DEVICE_TIMEOUT, (int)blockIdx.x);
-                    // let the copies already in flight land before the CTA's shared memory is released
-                    for (int64_t g2 = consumed; g2 < s_issued; g2++)
-                        mbar_wait_bounded(&full[g2 % NST], (uint32_t)((g2 / NST) & 1), 1000000000ull);
-                }
-                return;
-            }
-            mbar_wait_bounded(&full[st], parity, 1000000000ull);   // completed: returns at once
-            const uint32_t sA = smem_u32(smem + st * STAGE_BYTES);
-            const uint32_t sB = sA + NS * BLK * 2;
-#pragma unroll 1
-            for (int ks = 0; ks < 2; ks++) {
-                // every A slice's fragment stays in registers for the step; a B fragment is read from
-                // shared memory for each slice pair that uses it
-                uint32_t af[NS][4];
-#pragma unroll
-                for (int p = 0; p < NS; p++) {
-                    const int r = wm * 16 + arow, kc = ks * 2 + akc;
-                    ldsm_x4(af[p], sA + p * BLK * 2 + r * 64 + ((((kc ^ (r >> 1)) & 3)) << 4));
-                }
-                const int br = wn * 16 + brow, bkk = ks * 2 + bkc;
-                const uint32_t boff = br * 64 + ((((bkk ^ (br >> 1)) & 3)) << 4);
-#pragma unroll
-                for (int d = 2; d <= ND; d++) {
-                    float acc[2][4];
-#pragma unroll
-                    for (int b = 0; b < 2; b++)
-#pragma unroll
-                        for (int q = 0; q < 4; q++) acc[b][q] = 0.f;
-#pragma unroll
-                    for (int p = 1; p <= NS; p++) {
-                        const int q = d - p;
-                        if (q < 1 || q > NS) continue;
-                        uint32_t bf[4];
-                        ldsm_x4(bf, sB + (q - 1) * BLK * 2 + boff);
-#pragma unroll
-                        for (int nt = 0; nt < 2; nt++) mma16816(acc[nt], af[p - 1], bf[2 * nt], bf[2 * nt + 1]);
-                    }
-                    // exact FP32 -> int32 (the sums are integers below 2^21 in magnitude), or the tail
-#pragma unroll
-                    for (int b = 0; b < 2; b++)
-#pragma unroll
-                        for (int q = 0; q < 4; q++) {
-                            if (d - 2 < NI)
-                                iacc[d - 2][b][q] += __float_as_int(acc[b][q] + 12582912.0f) - 0x4B400000;
-                            else if (d == ND - 1)
-                                tail[b][q] += acc[b][q];
-                            else
-                                tail[b][q] = fmaf(acc[b][q], 1.0f / 256.0f, tail[b][q]);
-                        }
-                }
-            }
-            __syncthreads();   // every warp is done with this stage
-            if (tid == 0) issue_next();
-        }
-        const int g = lane >> 2, tg = lane & 3;
-#pragma unroll
-        for (int nt = 0; nt < 2; nt++)
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-                const int i = T.tm * TM + wm * 16 + g + ((q >> 1) << 3);
-                const int jj = T.tn * TM + wn * 16 + nt * 8 + 2 * tg + (q & 1);
-                if (i >= J.M || jj >= J.N || (J.lower && i < jj)) continue;
-                store_out(C + J.c_off + (int64_t)i * J.crs + (int64_t)jj * J.ccs, iacc[0][nt][q], iacc[1][nt][q],
-                          iacc[2][nt][q], iacc[3][nt][q], iacc[4][nt][q], tail[nt][q],
-                          ex[J.a_exp + i] + ex[J.b_exp + jj] - 62, alpha, beta);
-            }
-    }
 }
 
 // ------------------------------------------------------------------------------- tcgen05 gemm
@@ -794,22 +484,29 @@ __global__ void __launch_bounds__(tcg::THREADS, 1)
                 cv[j] = (sc.bmode != 0 && in) ? crow[(int64_t)jj * J.ccs] : 0.0;
                 eb[j] = jj < J.N ? ex[J.b_exp + jj] : 0;
             }
-            // C = beta C + alpha v 2^e: v rounded once, then the (FP64) update of C
+            // C = beta C + alpha v 2^e: v rounded once, then the (FP64) update of C; the uniform
+            // cases are separate loops so that no unused FP64 operation is issued
+            double r[EC];
+            const int es = sc.pow2 ? sc.e2 - 1 : 0;
+            const bool flip = sc.pow2 && sc.neg;
+#pragma unroll
+            for (int j = 0; j < EC; j++)
+                r[j] = limbs_to_double(flip ? -hi[j] : hi[j], flip ? -lo[j] : lo[j], ea + eb[j] + es);
+            if (!sc.pow2) {
+#pragma unroll
+                for (int j = 0; j < EC; j++) r[j] *= sc.alpha;
+            }
+            if (sc.bmode == 1) {
+#pragma unroll
+                for (int j = 0; j < EC; j++) r[j] += cv[j];
+            } else if (sc.bmode == 2) {
+#pragma unroll
+                for (int j = 0; j < EC; j++) r[j] = fma(sc.beta, cv[j], r[j]);
+            }
 #pragma unroll
             for (int j = 0; j < EC; j++) {
                 const int jj = j0 + j;
-                if (jj >= J.N || (J.lower && i < jj)) continue;
-                int e = ea + eb[j];
-                if (sc.pow2) {
-                    e += sc.e2 - 1;
-                    if (sc.neg) {
-                        hi[j] = -hi[j];
-                        lo[j] = -lo[j];
-                    }
-                }
-                double r = limbs_to_double(hi[j], lo[j], e);
-                if (!sc.pow2) r *= sc.alpha;
-                crow[(int64_t)jj * J.ccs] = sc.bmode == 0 ? r : sc.bmode == 1 ? cv[j] + r : fma(sc.beta, cv[j], r);
+                if (jj < J.N && !(J.lower && i < jj)) crow[(int64_t)jj * J.ccs] = r[j];
             }
         }
     }
@@ -908,47 +605,7 @@ void gemm(const __half *slices, const int32_t *exps, double *C, const std::vecto
           double beta, int *err, cudaStream_t s, const int32_t *skip) {
     if (jobs.empty()) return;
     static_assert(sizeof(GemmJob) % 8 == 0, "job layout");
-    static const bool mma_sync = getenv("LSAMG_OZ_MMA") != nullptr;
-    if (!mma_sync) {
-        gemm_tc(slices, exps, C, jobs, alpha, beta, err, s, skip);
-        return;
-    }
-    static_assert(KPIECE % TK == 0, "K pieces are whole chunks");
-    int npieces = 1;
-    for (const auto &J : jobs) npieces = std::max<int>(npieces, (int)cdiv(std::max(J.K, 1), KPIECE));
-    CK(cudaFuncSetAttribute(k_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM));
-    for (int pc = 0; pc < npieces; pc++) {
-        // pass pc: the pc-th K piece of every job (C accumulates from the second pass on)
-        std::vector<GemmJob> js;
-        std::vector<int64_t> cnt;
-        for (const auto &J0 : jobs) {
-            if (J0.M <= 0 || J0.N <= 0) continue;
-            const int64_t k0 = (int64_t)pc * KPIECE;
-            if (pc > 0 && k0 >= J0.K) continue;
-            GemmJob J = J0;
-            J.ktot = J0.K;
-            J.k0 = (int32_t)k0;
-            J.K = (int32_t)std::min<int64_t>(KPIECE, std::max<int64_t>(J0.K - k0, 0));
-            const int64_t tm = cdiv(J.M, TM), tn = cdiv(J.N, TM);
-            if (J.lower && tm != tn) fail(LSAMG_INVALID_ARG, "lower-triangular product of a non-square block");
-            js.push_back(J);
-            cnt.push_back(J.lower ? tm * (tm + 1) / 2 : tm * tn);
-        }
-        if (js.empty()) continue;
-        DBuf<int64_t> buf;
-        const GemmJob *dj = nullptr;
-        const int64_t *dp = nullptr;
-        const int64_t total = upload_jobs(js, cnt, buf, dj, dp, s);
-        if (total == 0) continue;
-        if (total > 0x7fffffff) fail(LSAMG_LIMIT, "product grid too large");
-        double fl = 0.0;   // FP64-equivalent flops of the products (lower: the triangle only)
-        for (const auto &J : js) fl += (J.lower ? 1.0 : 2.0) * J.M * (double)J.N * J.K;
-        KTime kt(KC_TC_GEMM, s, fl);
-        const unsigned grid = (unsigned)std::min<int64_t>(total, device_sms());
-        k_gemm<<<grid, GT, GEMM_SMEM, s>>>(slices, exps, C, dj, dp, (int)js.size(), alpha, pc == 0 ? beta : 1.0, err,
-                                          skip);
-        CK_LAUNCH();
-    }
+    gemm_tc(slices, exps, C, jobs, alpha, beta, err, s, skip);
 }
 
 }  // namespace oz

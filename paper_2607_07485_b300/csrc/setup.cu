@@ -798,6 +798,16 @@ void local_spectral(Level &L, const lsamg_options &o, int *err, cudaStream_t s, 
     upload(L.off, off, s);
     upload(L.k, L.h_k, s);
     L.max_k = L.h_k.empty() ? 0 : *std::max_element(L.h_k.begin(), L.h_k.end());
+    L.max_nw = L.h_nw.empty() ? 0 : *std::max_element(L.h_nw.begin(), L.h_nw.end());
+    {
+        // Z_i read once, omega-indexed fine vector and the coarse vector once each
+        double zw = 0.0;
+        for (int64_t a = 0; a < nagg; a++) zw += (double)L.h_nw[a] * L.h_k[a];
+        for (int t = 0; t < 2; t++) {
+            const double sz = t ? 8.0 : 4.0;
+            L.transfer_bytes[t] = zw * sz + (double)L.n * (sz + 4.0) + (double)L.nc * sz;
+        }
+    }
     L.Z64.alloc(std::max<int64_t>(zoff[nagg], 1), s);
     L.Z32.alloc(std::max<int64_t>(zoff[nagg], 1), s);
     for (auto &ch : chunks) {

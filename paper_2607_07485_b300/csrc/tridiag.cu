@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(256) k_trd_pairs(const double *base, const int
 // incrementally, and the loads of the next tile are in flight while the current one is used.
 __global__ void __launch_bounds__(256, 4) k_trd_symv(const float2 *F, const int64_t *foff, const int32_t *nn,
                                                      int64_t count, int j, const int64_t *toff, const double *vbuf,
-                                                     double *P, const int64_t *poff, const int64_t *pre) {
+                                                     float2 *P, const int64_t *poff, const int64_t *pre) {
     // rows padded to 68 pairs: the 16 threads of a half-warp read 16 distinct 8-byte banks both
     // along rows and along columns
     __shared__ float2 tile[ST][ST + 4];
@@ -373,9 +373,9 @@ __global__ void __launch_bounds__(256, 4) k_trd_symv(const float2 *F, const int6
             df_add(ch, cl, __shfl_xor_sync(0xffffffffu, ch, o), __shfl_xor_sync(0xffffffffu, cl, o));
         }
         if (lane4 == 0) {
-            double *Pb = P + cpo;
-            Pb[((int64_t)cti * cT + ctj) * ST + idx] = (double)rh + (double)rl;
-            if (!diag) Pb[((int64_t)ctj * cT + cti) * ST + idx] = (double)ch + (double)cl;
+            float2 *Pb = P + cpo;
+            Pb[((int64_t)cti * cT + ctj) * ST + idx] = make_float2(rh, rl);
+            if (!diag) Pb[((int64_t)ctj * cT + cti) * ST + idx] = make_float2(ch, cl);
         }
         __syncthreads();
     }
@@ -384,7 +384,7 @@ __global__ void __launch_bounds__(256, 4) k_trd_symv(const float2 *F, const int6
 // w of column j, rows j+1 .. n-1 by blocks: y = the product slots summed in fixed order, then
 // w' = tau (y - V s1 - W s2) into ybuf, partial w'^T v
 __global__ void __launch_bounds__(RB) k_trd_w2(const int32_t *nn, int64_t count, int j, int j0, const double *tt,
-                                               const int64_t *toff, const double *vbuf, const double *P,
+                                               const int64_t *toff, const double *vbuf, const float2 *P,
                                                const int64_t *poff, double *VW, double *WV, const int64_t *vwoff,
                                                double *ybuf, double *part, const int64_t *partoff) {
     __shared__ double red[32];
@@ -421,13 +421,17 @@ __global__ void __launch_bounds__(RB) k_trd_w2(const int32_t *nn, int64_t count,
     __syncthreads();
     const double *v = vbuf + toff[b];
     const int T = (m + ST - 1) / ST;
-    const double *Pb = P + poff[b];
+    const float2 *Pb = P + poff[b];
     double wv = 0.0;
     if (r < n) {
         const int i = r - j - 1, ti = i / ST, rr = i % ST;
-        double y = 0.0;
+        float yh = 0.f, yl = 0.f;   // the double-float slots, summed error-free
 #pragma unroll 8
-        for (int t = 0; t < T; t++) y += Pb[((int64_t)ti * T + t) * ST + rr];
+        for (int t = 0; t < T; t++) {
+            const float2 q = Pb[((int64_t)ti * T + t) * ST + rr];
+            df_add(yh, yl, q.x, q.y);
+        }
+        double y = (double)yh + (double)yl;
 #pragma unroll 8
         for (int q = 0; q < jj; q++) y -= V[r + (int64_t)q * n] * s1[q] + W[r + (int64_t)q * n] * s2[q];
         y *= tau;
@@ -481,7 +485,8 @@ void sytd2_batched(double *base, const MatBatch &Ab, double *d, double *e, doubl
     const int64_t tn = read1(toff + cnt, s);
     std::vector<int64_t> partoff(cnt + 1, 0);
     for (int64_t b = 0; b < cnt; b++) partoff[b + 1] = partoff[b] + cdiv(Ab.h_n[b], RB) * PSL;
-    DBuf<double> VW, WV, P, vbuf, ybuf, part, scal;
+    DBuf<double> VW, WV, vbuf, ybuf, part, scal;
+    DBuf<float2> P;
     DBuf<int64_t> dvw, dpo, dpa, pre, dfo;
     DBuf<float2> F;
     F.alloc(std::max<int64_t>(fo[cnt], 1), s);

@@ -1,8 +1,8 @@
 """The FP64 matrix product on the FP16 tensor cores (lsamg_dgemm_nt), which carries every dense
 update of the set-up, against an extended-precision product on the host: exact on integer
 operands, within the FP64 normwise dot-product bound on random and graded operands, for ragged
-shapes (M, N not multiples of 64, K not a multiple of 32) and for K beyond one int32 range
-(split products)."""
+shapes (M, N not multiples of the 128 x 32 product tile, K not a multiple of 32) and for long K
+(many 128-wide accumulation pieces carried in 64-bit integers)."""
 import numpy as np
 import pytest
 
@@ -72,7 +72,7 @@ def test_graded_rows_and_alpha_beta():
 
 def test_beta_zero_ignores_c_and_long_k_is_split():
     rng = np.random.default_rng(9)
-    M, N, K = 70, 65, 20000          # K above 16,352: two products accumulated
+    M, N, K = 70, 65, 20000          # 157 accumulation pieces of K = 128
     A = rng.standard_normal((M, K))
     B = rng.standard_normal((N, K))
     C0 = np.full((M, N), np.nan)
