@@ -421,16 +421,17 @@ __global__ void __launch_bounds__(256) k_gc(const int32_t *items, int64_t nitems
         blk_start[nb] = c;
         nblk = nb;
     }
-    __shared__ double Gs[32][33];
-    __shared__ double Rs[32][65];
+    // operands as double-float pairs (the product is FP64 multiply-add bound otherwise)
+    __shared__ float2 Gs[32][33];
+    __shared__ float2 Rs[32][65];
     const int r0 = tr * 32, c0 = tc * 64;
     int ty = threadIdx.x / 32, tx = threadIdx.x % 32;  // 8 x 32 threads: rows ty*4.., cols tx*2..
-    double acc[4][2] = {};
+    float ah[4][2] = {}, al[4][2] = {};
     __syncthreads();
     for (int q0 = 0; q0 < n; q0 += 32) {
         for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
             int r = t / 32, q = t % 32;
-            Gs[r][q] = (r0 + r < m && q0 + q < n) ? G[goff[e] + (int64_t)(r0 + r) * n + q0 + q] : 0.0;
+            Gs[r][q] = df_split((r0 + r < m && q0 + q < n) ? G[goff[e] + (int64_t)(r0 + r) * n + q0 + q] : 0.0);
         }
         for (int t = threadIdx.x; t < 32 * 64; t += blockDim.x) {
             int q = t / 64, c = t % 64;
@@ -446,12 +447,12 @@ __global__ void __launch_bounds__(256) k_gc(const int32_t *items, int64_t nitems
                     v = Z[zoff[a] + (int64_t)posw[dof] * k[a] + mode];
                 }
             }
-            Rs[q][c] = v;
+            Rs[q][c] = df_split(v);
         }
         __syncthreads();
 #pragma unroll 8
         for (int q = 0; q < 32; q++) {
-            double r0v[4], c0v[2];
+            float2 r0v[4], c0v[2];
 #pragma unroll
             for (int u = 0; u < 4; u++) r0v[u] = Gs[ty * 4 + u][q];
 #pragma unroll
@@ -459,7 +460,7 @@ __global__ void __launch_bounds__(256) k_gc(const int32_t *items, int64_t nitems
 #pragma unroll
             for (int u = 0; u < 4; u++)
 #pragma unroll
-                for (int v = 0; v < 2; v++) acc[u][v] = fma(r0v[u], c0v[v], acc[u][v]);
+                for (int v = 0; v < 2; v++) df_mac(ah[u][v], al[u][v], r0v[u], c0v[v]);
         }
         __syncthreads();
     }
@@ -469,7 +470,7 @@ __global__ void __launch_bounds__(256) k_gc(const int32_t *items, int64_t nitems
 #pragma unroll
         for (int v = 0; v < 2; v++) {
             int r = r0 + ty * 4 + u, c = c0 + tx * 2 + v;
-            if (r < m && c < ncol) out[(int64_t)r * ncol + c] = acc[u][v];
+            if (r < m && c < ncol) out[(int64_t)r * ncol + c] = (double)ah[u][v] + (double)al[u][v];
         }
 }
 

@@ -26,49 +26,9 @@ constexpr int ST = 64;    // tile of the symmetric product
 
 // The symmetric products y = A22 v carry two multiply-adds per stored entry, which would keep
 // this GPU's FP64 pipe (1/64 of the FP32 rate) saturated below a third of the memory bandwidth.
-// They run instead in double-float arithmetic on the FP32 pipe: every entry of A22 and v is
-// split into an FP32 pair hi + lo holding its leading 48 bits (truncated; relative error below
-// 2^-47), products keep their exact FP32 rounding error (fma) and the three leading cross terms,
-// sums are error-free (two-sum) into a pair.  The per-tile results are rounded to FP64 once.
-// For |x| < 2^-78 the low part underflows (absolute error below 2^-126) and below 2^-126 the
-// entry is flushed to zero: the reduced matrices C = L^-1 S L^-T have norm of order one, so this
-// is far below their FP64 rounding.
-__device__ __forceinline__ float2 df_split(double x) {
-    const uint64_t b = (uint64_t)__double_as_longlong(x);
-    const uint32_t sgn = (uint32_t)(b >> 32) & 0x80000000u;
-    const int e = (int)((b >> 52) & 0x7ff);                 // biased FP64 exponent
-    const uint64_t m = b & 0xfffffffffffffull;              // 52 fraction bits
-    const int fe = e - 896;                                  // FP32 biased exponent of hi
-    if (fe <= 0) return make_float2(0.f, 0.f);
-    if (fe >= 255) return make_float2(__uint_as_float(sgn | 0x7f800000u), 0.f);
-    const uint32_t hib = sgn | ((uint32_t)fe << 23) | (uint32_t)(m >> 29);
-    const uint32_t r = (uint32_t)(m & 0x1fffffffull);        // the 29 bits below hi: r 2^(e - 1075)
-    const int lz = __clz((int)r) - 3;                        // r's top bit at 28 - lz
-    const int le = 28 - lz + e - 1075 + 127;                 // FP32 biased exponent of lo
-    const uint32_t lm = lz >= 5 ? (r << (lz - 5)) : (r >> (5 - lz));
-    const uint32_t lob = (r == 0u || le <= 0) ? 0u : (sgn | ((uint32_t)le << 23) | (lm & 0x7fffffu));
-    return make_float2(__uint_as_float(hib), __uint_as_float(lob));
-}
-// (sh, sl) += a v
-__device__ __forceinline__ void df_mac(float &sh, float &sl, float2 a, float2 v) {
-    const float p = __fmul_rn(a.x, v.x);
-    float e = fmaf(a.x, v.x, -p);
-    e = fmaf(a.x, v.y, e);
-    e = fmaf(a.y, v.x, e);
-    const float t = __fadd_rn(sh, p);
-    const float bv = __fsub_rn(t, sh);
-    const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bv)), __fsub_rn(p, bv));
-    sl = __fadd_rn(sl, __fadd_rn(err, e));
-    sh = t;
-}
-// (sh, sl) += (oh, ol)
-__device__ __forceinline__ void df_add(float &sh, float &sl, float oh, float ol) {
-    const float t = __fadd_rn(sh, oh);
-    const float bv = __fsub_rn(t, sh);
-    const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bv)), __fsub_rn(oh, bv));
-    sl = __fadd_rn(sl, __fadd_rn(err, ol));
-    sh = t;
-}
+// They run instead in double-float arithmetic on the FP32 pipe (common.cuh: df_split, df_mac,
+// df_add): every entry of A22 and v is an FP32 pair holding its leading 48 bits, products keep
+// their exact FP32 rounding error and the leading cross terms, sums are error-free.
 
 __device__ double trd_block_sum(double v, double *red) {
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
