@@ -80,3 +80,15 @@ def test_beta_zero_ignores_c_and_long_k_is_split():
     err = np.abs(got - _ref(A, B)).astype(np.float64)
     assert np.isfinite(got).all()
     assert np.all(err <= _bound(A, B)), err.max()
+
+
+def test_accumulating_product_rounds_once():
+    # C = C0 - A B^T with integer data: every exact sum is below 2^53, so the result must be exact
+    # (the old C joins the integer sum before the single rounding)
+    rng = np.random.default_rng(13)
+    A = rng.integers(-2 ** 18, 2 ** 18, size=(200, 96)).astype(np.float64)
+    B = rng.integers(-2 ** 18, 2 ** 18, size=(75, 96)).astype(np.float64)
+    C0 = rng.integers(-2 ** 44, 2 ** 44, size=(200, 75)).astype(np.float64)
+    got = _run(A, B, C0.copy(), alpha=-1.0, beta=1.0)
+    ref = C0.astype(np.int64) - A.astype(np.int64) @ B.astype(np.int64).T
+    np.testing.assert_array_equal(got, ref.astype(np.float64))
