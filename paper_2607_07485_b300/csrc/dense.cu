@@ -319,17 +319,6 @@ __global__ void k_transpose(const double *baseS, const int64_t *soff, const int3
     }
 }
 
-__device__ double block_sum(double v, double *red) {
-    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __syncthreads();
-    if (lane == 0) red[w] = v;
-    __syncthreads();
-    double r = 0.0;
-    int nw = (blockDim.x + 31) >> 5;
-    for (int i = 0; i < nw; i++) r += red[i];
-    return r;
-}
 
 // ------------------------------------------------------------------------- stebz
 __device__ int sturm_count(const double *d, const double *e, int n, double x, double pivmin) {
@@ -688,7 +677,47 @@ void lower_update(double *base, const MatBatch &A, const std::vector<int32_t> &n
     oz::split(base, sj, ws.sl.p, ws.ex.p, s);
     oz::gemm(ws.sl.p, ws.ex.p, base, gj, -1.0, 1.0, err, s, skip);
 }
+// Inside a super panel [s0, s1): after panel [j0, j0 + w), the columns [j0 + w, s1) of the rows
+// below are brought up to date: A[j0+w : n, j0+w : s1) -= L[j0+w : n, j0 : j0+w) L[j0+w : s1,
+// j0 : j0+w)^T, as a lower-triangular product on the square [j0 + w, s1) and a full one on the
+// rows [s1, n) below it.
+void panel_update(double *base, const MatBatch &A, int j0, int w, int s1, oz::Workspace &ws, int *err,
+                  cudaStream_t s) {
+    std::vector<oz::SplitJob> sj;
+    std::vector<oz::GemmJob> gj;
+    int64_t h = 0, e = 0;
+    for (int64_t b = 0; b < A.count; b++) {
+        const int n = A.h_n[b];
+        const int c0 = j0 + w, c1 = std::min(n, s1);
+        if (c0 >= c1) continue;
+        const int64_t L = A.h_ld[b], o = A.h_off[b];
+        // rows [c0, c1) of the panel: both operands of the square part, B of the rectangle
+        const int ms = c1 - c0;
+        sj.push_back(oz::SplitJob{o + c0 + (int64_t)j0 * L, 1, L, h, e, ms, w});
+        const int64_t hs = h, es = e;
+        h += oz::slice_halves(ms, w);
+        e += oz::exp_ints(ms);
+        gj.push_back(oz::GemmJob{hs, hs, es, es, o + c0 + (int64_t)c0 * L, 1, L, ms, ms, w, 1, 0, 0});
+        const int mr = n - c1;
+        if (mr > 0) {
+            sj.push_back(oz::SplitJob{o + c1 + (int64_t)j0 * L, 1, L, h, e, mr, w});
+            gj.push_back(oz::GemmJob{h, hs, e, es, o + c1 + (int64_t)c0 * L, 1, L, mr, ms, w, 0, 0, 0});
+            h += oz::slice_halves(mr, w);
+            e += oz::exp_ints(mr);
+        }
+    }
+    if (gj.empty()) return;
+    ws.reserve(h, e, s);
+    oz::split(base, sj, ws.sl.p, ws.ex.p, s);
+    oz::gemm(ws.sl.p, ws.ex.p, base, gj, -1.0, 1.0, err, s);
+}
 }  // namespace
+
+// Two-level blocking: 64-column panels (FP64) inside super panels of SUPER columns.  Within a
+// super panel the updates after each panel touch only the super panel's columns (K = 64); the
+// trailing matrix beyond it is updated once per super panel with K = SUPER, where the
+// tensor-core products run several times faster than at K = 64.
+constexpr int SUPER = 256;
 
 void potrf_batched(double *base, const MatBatch &A, PotrfMode mode, int *err, cudaStream_t s) {
     if (A.count == 0 || A.maxn == 0) return;
@@ -719,7 +748,12 @@ void potrf_batched(double *base, const MatBatch &A, PotrfMode mode, int *err, cu
             }
         }
         if (rem <= 0) break;
-        lower_update(base, A, A.h_n, nullptr, j0, PB, ws, nullptr, err, s);
+        const int s0 = j0 - j0 % SUPER, s1 = s0 + SUPER;
+        if (j0 + PB < s1) {
+            panel_update(base, A, j0, PB, s1, ws, err, s);        // inside the super panel
+        } else {
+            lower_update(base, A, A.h_n, nullptr, s0, SUPER, ws, nullptr, err, s);   // beyond it
+        }
     }
 }
 
@@ -792,6 +826,37 @@ void trsm_batched(const double *base_L, const MatBatch &Lb, double *base_B, cons
     const int nblk = (int)cdiv(Bb.maxn, TB);
     dim3 g((unsigned)cdiv(Bb.maxm, SW), (unsigned)Bb.count);
     oz::Workspace ws;
+    // B rows [r0, r1) -= op(L) X over the solved rows [k0, k1) (two-level blocking as in potrf:
+    // the rows of the current super block after every 64-row block, the rest once per super
+    // block).  Forward: C rows below, A-op = L[r0:r1, k0:k1]; backward (trans): C rows above,
+    // A-op = L[k0:k1, r0:r1]^T.  B-op = X[k0:k1, :]^T.
+    auto update = [&](int r0, int r1, int k0, int k1) {
+        std::vector<oz::SplitJob> sa, sb;
+        std::vector<oz::GemmJob> gj;
+        int64_t h = 0, e = 0;
+        for (int64_t b = 0; b < Bb.count; b++) {
+            const int n = Bb.h_n[b], m = Bb.h_m[b];
+            const int kk1 = std::min(n, k1), rr1 = std::min(n, r1);
+            const int M = rr1 - r0, K = kk1 - k0;
+            if (M <= 0 || K <= 0 || m <= 0) continue;
+            const int64_t LL = Lb.h_ld[b], LB = Bb.h_ld[b];
+            sa.push_back(trans ? oz::SplitJob{Lb.h_off[b] + k0 + (int64_t)r0 * LL, LL, 1, h, e, M, K}
+                               : oz::SplitJob{Lb.h_off[b] + r0 + (int64_t)k0 * LL, 1, LL, h, e, M, K});
+            const int64_t ha = h, ea = e;
+            h += oz::slice_halves(M, K);
+            e += oz::exp_ints(M);
+            sb.push_back(oz::SplitJob{Bb.h_off[b] + k0, LB, 1, h, e, m, K});
+            const int64_t hb = h, eb = e;
+            h += oz::slice_halves(m, K);
+            e += oz::exp_ints(m);
+            gj.push_back(oz::GemmJob{ha, hb, ea, eb, Bb.h_off[b] + r0, 1, LB, M, m, K, 0, 0, 0});
+        }
+        if (gj.empty()) return;
+        ws.reserve(h, e, s);
+        oz::split(base_L, sa, ws.sl.p, ws.ex.p, s);
+        oz::split(base_B, sb, ws.sl.p, ws.ex.p, s);
+        oz::gemm(ws.sl.p, ws.ex.p, base_B, gj, -1.0, 1.0, err, s);
+    };
     for (int step = 0; step < nblk; step++) {
         const int kb = trans ? nblk - 1 - step : step;
         const int r0 = kb * TB;
@@ -807,42 +872,14 @@ void trsm_batched(const double *base_L, const MatBatch &Lb, double *base_B, cons
                                           Bb.count, r0, trans ? 1 : 0);
             CK_LAUNCH();
         }
-        // the rest of B: below the block (L21 X_r) or above it (L_r,0:r0^T X_r)
-        std::vector<oz::SplitJob> sj;
-        std::vector<oz::GemmJob> gj;
-        int64_t h = 0, e = 0;
-        for (int64_t b = 0; b < Bb.count; b++) {
-            const int n = Bb.h_n[b], m = Bb.h_m[b];
-            if (r0 >= n || m <= 0) continue;
-            const int bs = std::min(TB, n - r0);
-            const int M = trans ? r0 : n - r0 - bs;
-            if (M <= 0) continue;
-            const int64_t LL = Lb.h_ld[b], LB = Bb.h_ld[b];
-            oz::SplitJob JA = trans ? oz::SplitJob{Lb.h_off[b] + r0, LL, 1, h, e, M, bs}
-                                    : oz::SplitJob{Lb.h_off[b] + (r0 + bs) + (int64_t)r0 * LL, 1, LL, h, e, M, bs};
-            const int64_t ha = h, ea = e;
-            h += oz::slice_halves(M, bs);
-            e += oz::exp_ints(M);
-            oz::SplitJob JB{Bb.h_off[b] + r0, LB, 1, h, e, m, bs};
-            const int64_t hb = h, eb = e;
-            h += oz::slice_halves(m, bs);
-            e += oz::exp_ints(m);
-            sj.push_back(JA);
-            sj.push_back(JB);
-            const int64_t c_off = Bb.h_off[b] + (trans ? 0 : r0 + bs);
-            gj.push_back(oz::GemmJob{ha, hb, ea, eb, c_off, 1, LB, M, m, bs, 0, 0, 0});
+        const int s0 = r0 - r0 % SUPER, s1 = s0 + SUPER;
+        if (!trans) {
+            update(r0 + TB, s1, r0, r0 + TB);                   // rows of this super block
+            if (r0 + TB >= s1) update(s1, Bb.maxn, s0, s1);     // below it, K = SUPER
+        } else {
+            update(s0, r0, r0, r0 + TB);                        // rows of this super block
+            if (r0 == s0) update(0, s0, s0, s1);                // above it, K = SUPER
         }
-        if (gj.empty()) continue;
-        ws.reserve(h, e, s);
-        // A and B operands come from different arrays: split them in two calls
-        std::vector<oz::SplitJob> sa, sb;
-        for (size_t q = 0; q < sj.size(); q += 2) {
-            sa.push_back(sj[q]);
-            sb.push_back(sj[q + 1]);
-        }
-        oz::split(base_L, sa, ws.sl.p, ws.ex.p, s);
-        oz::split(base_B, sb, ws.sl.p, ws.ex.p, s);
-        oz::gemm(ws.sl.p, ws.ex.p, base_B, gj, -1.0, 1.0, err, s);
     }
 }
 
