@@ -18,7 +18,7 @@ int64_t launch_count() { return g_launches; }
 static const char *kKNames[KC_N] = {"elem_factor", "potrf", "pstrf", "trsm", "syrk", "sytd2",
                                     "stebz", "stein", "ormtr", "assemble", "coarse_gram",
                                     "schwarz_sweep", "gram_spmv", "transfer", "coarse_solve",
-                                    "graph", "tc_dgemm", "tc_split"};
+                                    "graph", "tc_dgemm", "tc_split", "sytd2_symv"};
 const char *kclass_name(int c) { return (c >= 0 && c < KC_N) ? kKNames[c] : ""; }
 static bool g_kt_on = false;
 void ktimer_enable(bool on) { g_kt_on = on; }

@@ -60,7 +60,7 @@ struct ProfScope {
 enum KClass {
     KC_ELEM_FACTOR = 0, KC_POTRF, KC_PSTRF, KC_TRSM, KC_SYRK, KC_SYTD2, KC_STEBZ, KC_STEIN,
     KC_ORMTR, KC_ASSEMBLE, KC_COARSE_GRAM, KC_SCHWARZ, KC_SPMV, KC_TRANSFER, KC_COARSE_SOLVE,
-    KC_GRAPH, KC_TC_GEMM, KC_TC_SPLIT, KC_N
+    KC_GRAPH, KC_TC_GEMM, KC_TC_SPLIT, KC_SYMV, KC_N
 };
 const char *kclass_name(int c);
 void ktimer_enable(bool on);

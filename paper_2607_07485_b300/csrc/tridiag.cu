@@ -201,15 +201,6 @@ __global__ void __launch_bounds__(RB) k_trd_c3(double *base, const int64_t *off,
     }
 }
 
-__device__ __forceinline__ int trd_find(const int64_t *pre, int64_t count, int64_t w) {
-    int64_t lo = 0, hi = count - 1;
-    while (lo < hi) {
-        const int64_t mid = (lo + hi + 1) >> 1;
-        if (pre[mid] <= w) lo = mid; else hi = mid - 1;
-    }
-    return (int)lo;
-}
-
 __device__ __forceinline__ void trd_tri(int64_t t, int &ti, int &tj) {
     int i = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);   // corrected below
     while ((int64_t)(i + 1) * (i + 2) / 2 <= t) i++;
@@ -483,26 +474,34 @@ void sytd2_batched(double *base, const MatBatch &Ab, double *d, double *e, doubl
                 const double m = v - j - 1;
                 if (m > 0) by += 4.0 * m * (m + 1);
             }
-            KTime kt(KC_SYTD2, s, 0.0, by);
-            const dim3 g1((unsigned)cdiv(Ab.maxn - j, RB), (unsigned)cnt);
-            k_trd_c1<<<g1, RB, 0, s>>>(base, Ab.off.p, Ab.ld.p, Ab.n.p, cnt, j, j0, VW.p, dvw.p, part.p, dpa.p);
-            CK_LAUNCH();
-            k_trd_sched<<<1, 1024, 0, s>>>(base, Ab.off.p, Ab.ld.p, Ab.n.p, cnt, j, d, e, tau, toff, part.p, dpa.p,
-                                           scal.p, pre.p);
-            CK_LAUNCH();
-            if (j >= Ab.maxn - 1) break;
-            const dim3 g3((unsigned)cdiv(Ab.maxn - j - 1, RB), (unsigned)cnt);
-            k_trd_c3<<<g3, RB, 0, s>>>(base, Ab.off.p, Ab.ld.p, Ab.n.p, cnt, j, j0, e, tau, toff, scal.p, VW.p, WV.p,
-                                       dvw.p, vbuf.p, part.p, dpa.p);
-            CK_LAUNCH();
-            k_trd_symv<<<symv_grid, 256, 0, s>>>(F.p, dfo.p, Ab.n.p, cnt, j, toff, vbuf.p, P.p, dpo.p, pre.p);
-            CK_LAUNCH();
-            k_trd_w2<<<g3, RB, 0, s>>>(Ab.n.p, cnt, j, j0, tau, toff, vbuf.p, P.p, dpo.p, VW.p, WV.p, dvw.p, ybuf.p,
-                                       part.p, dpa.p);
-            CK_LAUNCH();
-            k_trd_w3<<<g3, RB, 0, s>>>(Ab.n.p, cnt, j, j0, tau, toff, vbuf.p, VW.p, WV.p, dvw.p, ybuf.p, part.p,
-                                       dpa.p);
-            CK_LAUNCH();
+            const dim3 g3((unsigned)cdiv(std::max(Ab.maxn - j - 1, 1), RB), (unsigned)cnt);
+            {
+                KTime kt(KC_SYTD2, s);
+                const dim3 g1((unsigned)cdiv(Ab.maxn - j, RB), (unsigned)cnt);
+                k_trd_c1<<<g1, RB, 0, s>>>(base, Ab.off.p, Ab.ld.p, Ab.n.p, cnt, j, j0, VW.p, dvw.p, part.p, dpa.p);
+                CK_LAUNCH();
+                k_trd_sched<<<1, 1024, 0, s>>>(base, Ab.off.p, Ab.ld.p, Ab.n.p, cnt, j, d, e, tau, toff, part.p,
+                                               dpa.p, scal.p, pre.p);
+                CK_LAUNCH();
+                if (j >= Ab.maxn - 1) break;
+                k_trd_c3<<<g3, RB, 0, s>>>(base, Ab.off.p, Ab.ld.p, Ab.n.p, cnt, j, j0, e, tau, toff, scal.p, VW.p,
+                                           WV.p, dvw.p, vbuf.p, part.p, dpa.p);
+                CK_LAUNCH();
+            }
+            {
+                KTime ks(KC_SYMV, s, 0.0, by);
+                k_trd_symv<<<symv_grid, 256, 0, s>>>(F.p, dfo.p, Ab.n.p, cnt, j, toff, vbuf.p, P.p, dpo.p, pre.p);
+                CK_LAUNCH();
+            }
+            {
+                KTime kt(KC_SYTD2, s);
+                k_trd_w2<<<g3, RB, 0, s>>>(Ab.n.p, cnt, j, j0, tau, toff, vbuf.p, P.p, dpo.p, VW.p, WV.p, dvw.p,
+                                           ybuf.p, part.p, dpa.p);
+                CK_LAUNCH();
+                k_trd_w3<<<g3, RB, 0, s>>>(Ab.n.p, cnt, j, j0, tau, toff, vbuf.p, VW.p, WV.p, dvw.p, ybuf.p, part.p,
+                                           dpa.p);
+                CK_LAUNCH();
+            }
         }
         // trailing update A22 -= V W^T + W V^T over rows / columns >= j1, K = 2 PNB
         std::vector<oz::SplitJob> sa, sb;
