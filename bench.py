@@ -85,11 +85,42 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--oracle-sample", type=int, default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--dgemm", type=str, default=None, metavar="M,N,K",
+                    help="instead of the benchmark: time the tensor-core FP64 product C = A B^T + C of this "
+                         "shape (lsamg_dgemm_nt, device operands) and print its FP64-equivalent rate")
     ap.add_argument("--closure-sweep", type=str, default=None, metavar="N,N,...",
                     help="instead of the benchmark: stationary V-cycle iterations with the G-row and "
                          "the A-closure on CG1 triangles of these mesh sizes (the Table 2 comparison), "
                          "one JSON line per size and closure")
     return ap.parse_args()
+
+
+def dgemm_rate(shape, reps=5):
+    """FP64-equivalent rate of one product shape through the C ABI (column-major operands)."""
+    import torch
+    from paper_2607_07485_b300 import lsamg as LB
+    M, N, K = shape
+    dev = torch.device("cuda", 0)
+    g = torch.Generator(device=dev).manual_seed(1)
+    A = torch.randn(K, M, dtype=torch.float64, device=dev, generator=g)    # column-major M x K
+    B = torch.randn(K, N, dtype=torch.float64, device=dev, generator=g)
+    C = torch.zeros(N, M, dtype=torch.float64, device=dev)
+    s = torch.cuda.current_stream().cuda_stream
+
+    def run():
+        LB._check(LB._lib.lsamg_dgemm_nt(M, N, K, 1.0, LB._ptr(A), M, LB._ptr(B), N, 1.0, LB._ptr(C), M,
+                                         LB.C.c_void_p(s)))
+    run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        run()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    print(json.dumps(dict(M=M, N=N, K=K, ms=ms, fp64_equivalent_tflops=2.0 * M * N * K / ms / 1e9,
+                          flops=2.0 * M * N * K)), flush=True)
 
 
 def closure_sweep(sizes):
@@ -323,6 +354,9 @@ def main():
         return
     if args.closure_sweep:
         closure_sweep([int(v) for v in args.closure_sweep.split(",")])
+        return
+    if args.dgemm:
+        dgemm_rate([int(v) for v in args.dgemm.split(",")])
         return
     import torch
     import torch.distributed as dist
