@@ -66,10 +66,11 @@ TC_PAIRS = 28
 # Leaf kernel classes of the library's timers that run on the FP64 pipe (bound "alu"); the
 # split-operand products are "tensor", the classes with algorithmic bytes "hbm"
 ALU_CLASSES = ("potrf", "trsm", "pstrf", "ormtr", "elem_factor")
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the leaf kernels from an
-# ncu capture of the kernel as it now stands (the summaries under profiles/); a kernel changed since
-# its capture has no entry
-TRAFFIC = {}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per algorithmic byte of the leaf
+# kernels, from an ncu capture of the kernel as it now stands (profiles/tc_dgemm_8192x8192x256.md:
+# 1131.8 MB measured for 1132.4 MB algorithmic); the line's traffic is this ratio times the
+# algorithmic bytes per launch.  A kernel changed since its capture has no entry.
+TRAFFIC = {"tc_dgemm": 1131.8 / 1132.4}
 
 
 def parse():
@@ -498,8 +499,10 @@ def main():
             r = dict(kernel=name, bound="hbm", achieved=ach, peak=hbm_peak, unit="GB/s", frac=ach / hbm_peak,
                      peak_source="measured" if "hbm_gbs" in peaks else "fallback")
         if r is not None:
+            per_launch = k["bytes"] / max(k["calls"], 1)
             r.update(ms=k["ms"] / args.steps, launches=k["calls"] // max(args.steps, 1),
-                     traffic=TRAFFIC.get(name))
+                     traffic=(TRAFFIC[name] * per_launch if name in TRAFFIC and per_launch > 0 else None),
+                     algorithmic_bytes_per_launch=per_launch or None)
             rooflines.append(r)
     dominant = max(ks.items(), key=lambda kv: kv[1]["ms"])[0] if ks else None
     roof = next((r for r in rooflines if r["kernel"] == dominant), None)

@@ -575,6 +575,8 @@ static void gemm_tc(const __half *slices, const int32_t *exps, double *C, const 
     std::vector<GemmJob> js;
     std::vector<int64_t> cnt;
     double fl = 0.0;   // FP64-equivalent flops of the products (lower: the triangle only)
+    double by = 0.0;   // algorithmic bytes: the FP16 slices of A and B once, C read (beta != 0) and written
+    const double cbytes = beta != 0.0 ? 16.0 : 8.0;
     for (const auto &J0 : jobs) {
         if (J0.M <= 0 || J0.N <= 0) continue;
         GemmJob J = J0;
@@ -585,6 +587,7 @@ static void gemm_tc(const __half *slices, const int32_t *exps, double *C, const 
         js.push_back(J);
         cnt.push_back(J.lower ? tc_lower_prefix(tm, tn) : tm * tn);
         fl += (J.lower ? 1.0 : 2.0) * J.M * (double)J.N * J.K;
+        by += 2.0 * NS * ((double)J.M + J.N) * J.K + (J.lower ? 0.5 : 1.0) * cbytes * J.M * (double)J.N;
     }
     if (js.empty()) return;
     DBuf<int64_t> buf;
@@ -593,7 +596,7 @@ static void gemm_tc(const __half *slices, const int32_t *exps, double *C, const 
     const int64_t total = upload_jobs(js, cnt, buf, dj, dp, s);
     if (total == 0) return;
     if (total > 0x7fffffff) fail(LSAMG_LIMIT, "product grid too large");
-    KTime kt(KC_TC_GEMM, s, fl);
+    KTime kt(KC_TC_GEMM, s, fl, by);
     CK(cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tcg::SMEM));
     const unsigned grid = (unsigned)std::min<int64_t>(total, device_sms());
     k_gemm_tc<<<grid, tcg::THREADS, tcg::SMEM, s>>>(slices, exps, C, dj, dp, (int)js.size(), make_scale(alpha, beta),
