@@ -106,6 +106,16 @@ struct DBuf {
         n = count;
         if (count > 0) {
             cudaError_t e = cudaMallocAsync((void **)&p, (size_t)count * sizeof(T), st);
+            if (e == cudaErrorMemoryAllocation) {
+                // memory freed earlier may still sit in the stream-ordered pool in blocks too small
+                // for this request: return it to the device and try once more
+                cudaGetLastError();
+                int dev = 0;
+                cudaMemPool_t pool;
+                if (cudaStreamSynchronize(st) == cudaSuccess && cudaGetDevice(&dev) == cudaSuccess &&
+                    cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess && cudaMemPoolTrimTo(pool, 0) == cudaSuccess)
+                    e = cudaMallocAsync((void **)&p, (size_t)count * sizeof(T), st);
+            }
             if (e != cudaSuccess) {
                 p = nullptr;
                 n = 0;
