@@ -63,11 +63,11 @@ __global__ void k_potf2(double *base, const int64_t *off, const int32_t *ld, con
                 p = (d > tol) ? sqrt(d) : 0.0;
             }
             s[k][k] = p;
-            piv = p;
+            piv = (p > 0.0) ? 1.0 / p : 0.0;   // one division per column (the FP64 pipe is scarce)
         }
         __syncthreads();
-        double p = piv;
-        for (int i = k + 1 + threadIdx.x; i < bs; i += blockDim.x) s[i][k] = (p > 0.0) ? s[i][k] / p : 0.0;
+        const double rp = piv;
+        for (int i = k + 1 + threadIdx.x; i < bs; i += blockDim.x) s[i][k] *= rp;
         __syncthreads();
         int m = bs - k - 1;
         for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
@@ -94,10 +94,13 @@ __global__ void __launch_bounds__(128) k_potrf_panel(double *base, const int64_t
     int L = ld[b];
     double *A = base + off[b];
     __shared__ double l[PB][PB + 1];
+    __shared__ double rdiag[PB];
     for (int t = threadIdx.x; t < bs * bs; t += blockDim.x) {
         int i = t % bs, j = t / bs;
         l[i][j] = (i >= j) ? A[(j0 + i) + (int64_t)(j0 + j) * L] : 0.0;
     }
+    __syncthreads();
+    for (int c = threadIdx.x; c < bs; c += blockDim.x) rdiag[c] = (l[c][c] != 0.0) ? 1.0 / l[c][c] : 0.0;
     __syncthreads();
     int r = j0 + bs + blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
@@ -112,7 +115,7 @@ __global__ void __launch_bounds__(128) k_potrf_panel(double *base, const int64_t
 #pragma unroll
             for (int k = 0; k < PB; k++)
                 if (k < c) v -= x[k] * l[c][k];
-            x[c] = (l[c][c] != 0.0) ? v / l[c][c] : 0.0;
+            x[c] = v * rdiag[c];
         }
     }
 #pragma unroll
@@ -220,12 +223,12 @@ __global__ void __launch_bounds__(256) k_pstf_panel(double *base, const int64_t 
             }
             __syncthreads();
         }
-        const double ljj = sqrt(w[j]);
+        const double ljj = sqrt(w[j]), rjj = 1.0 / ljj;
         // column j: l_ij = (a_ij - sum_{k in panel, k<j} l_ik l_jk) / l_jj
         for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) {
             double v = A[i + (int64_t)j * L];
             for (int k = j0; k < j; k++) v -= A[i + (int64_t)k * L] * A[j + (int64_t)k * L];
-            v /= ljj;
+            v *= rjj;
             A[i + (int64_t)j * L] = v;
             w[i] -= v * v;
         }
@@ -268,9 +271,12 @@ __global__ void __launch_bounds__(256) k_trsm_diag(const double *baseL, const in
         X[i][c] = (i < bs && c < cs) ? B[(r0 + i) + (int64_t)c * LB] : 0.0;
     }
     __syncthreads();
+    __shared__ double rdiag[TB];
+    for (int c = threadIdx.x; c < bs; c += blockDim.x) rdiag[c] = (Ls[c][c] != 0.0) ? 1.0 / Ls[c][c] : 0.0;
+    __syncthreads();
     for (int step = 0; step < bs; step++) {
         const int k = trans ? bs - 1 - step : step;
-        if (threadIdx.x < SW) X[k][threadIdx.x] = (Ls[k][k] != 0.0) ? X[k][threadIdx.x] / Ls[k][k] : 0.0;
+        if (threadIdx.x < SW) X[k][threadIdx.x] *= rdiag[k];
         __syncthreads();
         if (!trans) {
             const int m = bs - k - 1;
