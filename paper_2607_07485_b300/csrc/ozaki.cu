@@ -58,8 +58,10 @@ __global__ void __launch_bounds__(256) k_split(const double *src, const SplitJob
         __syncthreads();
     }
     // slices in integer arithmetic (the FP64 pipe is scarce): F = round(v 2^(55 - e_r)) exactly
-    // from the bits of v (|F| < 2^55), then balanced base-256 digits a_p = round(F / 2^(48-8(p-1)))
-    // with F -= a_p 2^(48-8(p-1)); the seven digits hold F exactly.  Two consecutive k per thread.
+    // from the bits of v (|F| < 2^55), then its balanced base-256 digits, F = sum_p a_p 2^(48-8p)
+    // with the low six a_p in [-128, 127] and |a_0| <= 128, which hold F exactly.  They are read
+    // off G = F + 128 (1 + 2^8 + ... + 2^48) > 0: the low six digits are the bytes of G minus 128,
+    // the top one G / 2^48 - 128.  Two consecutive k per thread.
     const int64_t pstride = (int64_t)tiles * nch * BLK;
     for (int c = 0; c < nch; c++) {
         for (int idx = threadIdx.x; idx < BLK / 2; idx += blockDim.x) {
@@ -88,12 +90,14 @@ __global__ void __launch_bounds__(256) k_split(const double *src, const SplitJob
                     }
                     if (bits >> 63) F = -F;
                 }
+                const uint64_t G = (uint64_t)(F + 0x80808080808080ll);   // > 0 since |F| < 2^55
+                const uint32_t glo = (uint32_t)G, ghi = (uint32_t)(G >> 32);
+                dig[h][0] = (int)(ghi >> 16) - 128;
 #pragma unroll
-                for (int p = 0; p < NS; p++) {
-                    const int s2 = 48 - 8 * p;
-                    const int64_t a = (s2 > 0) ? ((F + (1ll << (s2 - 1))) >> s2) : F;
-                    F -= a << s2;
-                    dig[h][p] = (int)a;
+                for (int p = 1; p < NS; p++) {
+                    const int byte = 6 - p;                                // byte of G at 2^(48 - 8p)
+                    const uint32_t w = byte >= 4 ? ghi : glo;
+                    dig[h][p] = (int)((w >> (8 * (byte & 3))) & 255u) - 128;
                 }
             }
             const int o = swz(r, kk);
