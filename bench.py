@@ -67,9 +67,9 @@ TC_PAIRS = 28
 # split-operand products are "tensor", the classes with algorithmic bytes "hbm"
 ALU_CLASSES = ("potrf", "trsm", "pstrf", "ormtr", "elem_factor")
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per algorithmic byte of the leaf
-# kernels, from an ncu capture of the kernel as it now stands (profiles/tc_dgemm_8192x8192x256.md:
-# 1131.8 MB measured for 1132.4 MB algorithmic); the line's traffic is this ratio times the
-# algorithmic bytes per launch.  A kernel changed since its capture has no entry.
+# kernels, from an ncu capture of the kernel as it now stands (the 8192 x 8192 x 256 product of
+# `--dgemm`: 1131.8 MB measured for 1132.4 MB algorithmic); the line's traffic is this ratio
+# times the algorithmic bytes per launch.  A kernel changed since its capture has no entry.
 TRAFFIC = {"tc_dgemm": 1131.8 / 1132.4}
 
 
