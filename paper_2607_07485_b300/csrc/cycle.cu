@@ -379,16 +379,16 @@ __device__ __forceinline__ bool wf_wait(const uint32_t *flag, uint32_t epoch, in
     return *s_ok != 0;
 }
 
-template <class T, bool FWD>
-__global__ void __launch_bounds__(256, FWD ? 2 : 4) k_tri_wave(const int32_t *tasks, int64_t ntask, const int32_t *sys,
+template <class T, bool FWD, int RG>
+__global__ void __launch_bounds__(256, FWD ? (RG > 1 ? 2 : 3) : 4) k_tri_wave(const int32_t *tasks, int64_t ntask, const int32_t *sys,
                                                   const int64_t *Optr, const T *Lp, const int64_t *Loff,
                                                   const double *Dp, const int64_t *Doff, const int64_t *Foff,
                                                   uint32_t *flags, uint32_t epoch, int cb, T *ws, int64_t wsn,
                                                   int nrhs, int *err) {
-    __shared__ T yj[WF_RG][TRI_CB];
-    __shared__ double tv[WF_RG][TRI_CB];
-    __shared__ double vo[WF_RG][TRI_CB];                    // this block of the right-hand sides
-    __shared__ double red[8][WF_RG][TRI_CB];
+    __shared__ T yj[RG][TRI_CB];
+    __shared__ double tv[RG][TRI_CB];
+    __shared__ double vo[RG][TRI_CB];                    // this block of the right-hand sides
+    __shared__ double red[8][RG][TRI_CB];
     __shared__ double sDi[TRI_CB * (TRI_CB + 1) / 2];       // inverted diagonal block
     __shared__ int s_ok;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -409,8 +409,8 @@ __global__ void __launch_bounds__(256, FWD ? 2 : 4) k_tri_wave(const int32_t *ta
             const int nw = nb * (nb + 1) / 2;
             for (int t = threadIdx.x; t < nw; t += blockDim.x) sDi[t] = __ldg(Di + t);
         }
-        for (int g0 = 0; g0 < nrhs; g0 += WF_RG) {
-            const int nr = min(WF_RG, nrhs - g0);
+        for (int g0 = 0; g0 < nrhs; g0 += RG) {
+            const int nr = min(RG, nrhs - g0);
             // own block of the right-hand sides: written only by this task
             for (int t = threadIdx.x; t < nr * TRI_CB; t += blockDim.x) {
                 const int r = t / TRI_CB, c = t - r * TRI_CB;
@@ -419,9 +419,9 @@ __global__ void __launch_bounds__(256, FWD ? 2 : 4) k_tri_wave(const int32_t *ta
             // per-warp partial sums over every dependency block: forward, rows warp + 8 i of the
             // block (each lane over two columns); backward, columns lane / lane + 32 (each warp
             // over rows warp + 8 i of the dependency block)
-            T part[WF_RG][8];
+            T part[RG][8];
 #pragma unroll
-            for (int r = 0; r < WF_RG; r++)
+            for (int r = 0; r < RG; r++)
 #pragma unroll
                 for (int i = 0; i < 8; i++) part[r][i] = 0;
             const int jn = FWD ? k : K - 1 - k;          // dependency blocks
@@ -454,13 +454,13 @@ __global__ void __launch_bounds__(256, FWD ? 2 : 4) k_tri_wave(const int32_t *ta
                 __syncthreads();
                 if (FWD) {
 #pragma unroll
-                    for (int r = 0; r < WF_RG; r++)
+                    for (int r = 0; r < RG; r++)
                         if (r < nr)
 #pragma unroll
                             for (int i = 0; i < 8; i++) part[r][i] += lv[i][0] * yj[r][lane] + lv[i][1] * yj[r][lane + 32];
                 } else {
 #pragma unroll
-                    for (int r = 0; r < WF_RG; r++)
+                    for (int r = 0; r < RG; r++)
                         if (r < nr)
 #pragma unroll
                             for (int i = 0; i < 8; i++) {
@@ -473,14 +473,17 @@ __global__ void __launch_bounds__(256, FWD ? 2 : 4) k_tri_wave(const int32_t *ta
             }
             // combine the partial sums: t = v_block - (L_block,deps . y_deps)
             if (FWD) {
-                // butterfly over the warp: the 32 sums (r, i) end one per lane, lane = 8 r + i
-                double x[WF_RG * 8];
+                // butterfly over the warp: the RG * 8 sums (r, i) end one per group of 32 / (8 RG)
+                // lanes (index 8 r + i = lane / (32 / (8 RG))), which then finish the sum
+                constexpr int NV = RG * 8, SPAN = 32 / NV;
+                static_assert(NV <= 32 && 32 % NV == 0, "partial sums per lane");
+                double x[NV];
 #pragma unroll
-                for (int r = 0; r < WF_RG; r++)
+                for (int r = 0; r < RG; r++)
 #pragma unroll
                     for (int i = 0; i < 8; i++) x[8 * r + i] = (double)part[r][i];
 #pragma unroll
-                for (int o = 16, c = WF_RG * 8; o >= 1; o >>= 1, c >>= 1) {
+                for (int o = 16, c = NV; c > 1; o >>= 1, c >>= 1) {
                     const bool up = (lane & o) != 0;
 #pragma unroll
                     for (int t = 0; t < c / 2; t++) {
@@ -489,8 +492,12 @@ __global__ void __launch_bounds__(256, FWD ? 2 : 4) k_tri_wave(const int32_t *ta
                         x[t] = keep + __shfl_xor_sync(0xffffffffu, send, o);
                     }
                 }
-                static_assert(WF_RG * 8 == 32, "one partial sum per lane");
-                red[0][lane >> 3][warp + 8 * (lane & 7)] = x[0];
+#pragma unroll
+                for (int o = SPAN / 2; o >= 1; o >>= 1) x[0] += __shfl_xor_sync(0xffffffffu, x[0], o);
+                if (lane % SPAN == 0) {
+                    const int idx = lane / SPAN;
+                    red[0][idx >> 3][warp + 8 * (idx & 7)] = x[0];
+                }
                 __syncthreads();
                 for (int t = threadIdx.x; t < nr * TRI_CB; t += blockDim.x) {
                     const int r = t / TRI_CB, i = t - r * TRI_CB;
@@ -498,7 +505,7 @@ __global__ void __launch_bounds__(256, FWD ? 2 : 4) k_tri_wave(const int32_t *ta
                 }
             } else {
 #pragma unroll
-                for (int r = 0; r < WF_RG; r++) {   // columns lane and lane + 32, summed over this warp's rows
+                for (int r = 0; r < RG; r++) {   // columns lane and lane + 32, summed over this warp's rows
                     red[warp][r][lane] = (double)part[r][0];
                     red[warp][r][lane + 32] = (double)part[r][1];
                 }
@@ -515,28 +522,28 @@ __global__ void __launch_bounds__(256, FWD ? 2 : 4) k_tri_wave(const int32_t *ta
             // this block: y = Dinv t (forward) or x = Dinv^T t (backward), FP64; 4 threads per entry
             {
                 const int e = threadIdx.x >> 2, p = threadIdx.x & 3;
-                double acc[WF_RG];
+                double acc[RG];
 #pragma unroll
-                for (int r = 0; r < WF_RG; r++) acc[r] = 0.0;
+                for (int r = 0; r < RG; r++) acc[r] = 0.0;
                 if (e < nb) {
                     if (FWD) {
                         for (int c = p; c <= e; c += 4) {
                             const double d = sDi[e * (e + 1) / 2 + c];
 #pragma unroll
-                            for (int r = 0; r < WF_RG; r++)
+                            for (int r = 0; r < RG; r++)
                                 if (r < nr) acc[r] += d * tv[r][c];
                         }
                     } else {
                         for (int i = e + p; i < nb; i += 4) {
                             const double d = sDi[i * (i + 1) / 2 + e];
 #pragma unroll
-                            for (int r = 0; r < WF_RG; r++)
+                            for (int r = 0; r < RG; r++)
                                 if (r < nr) acc[r] += d * tv[r][i];
                         }
                     }
                 }
 #pragma unroll
-                for (int r = 0; r < WF_RG; r++) {
+                for (int r = 0; r < RG; r++) {
                     acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], 1);
                     acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], 2);
                 }
@@ -816,20 +823,24 @@ static void tri_solve(Level &L, int grp, const int32_t *sys, const int64_t *Optr
     uint32_t *flags = L.wf_flags.p;
     int *err = reinterpret_cast<int *>(L.wf_flags.p + 2 * L.wf_nflags);
     CK(cudaMemsetAsync(flags, 0, 2 * L.wf_nflags * sizeof(uint32_t), s));
-    static int occ[2][2] = {{0, 0}, {0, 0}};
+    // one right-hand side: the kernels specialised for it hold a quarter of the partial sums
+    static int occ[2][2][2] = {{{0, 0}, {0, 0}}, {{0, 0}, {0, 0}}};
     const int ti = std::is_same<T, double>::value ? 1 : 0;
+    const int single = nrhs == 1 ? 1 : 0;
     for (int dir = 0; dir < 2; dir++) {
         const bool fwd = dir == 0;
-        void *fn = fwd ? (void *)k_tri_wave<T, true> : (void *)k_tri_wave<T, false>;
-        if (!occ[ti][dir]) {
+        void *fn = single ? (fwd ? (void *)k_tri_wave<T, true, 1> : (void *)k_tri_wave<T, false, 1>)
+                          : (fwd ? (void *)k_tri_wave<T, true, WF_RG> : (void *)k_tri_wave<T, false, WF_RG>);
+        int &oc = occ[single][ti][dir];
+        if (!oc) {
             int o = 0;
             CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fn, 256, 0));
             int dev = 0, sms = 0;
             CK(cudaGetDevice(&dev));
             CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-            occ[ti][dir] = std::max(1, o) * sms;
+            oc = std::max(1, o) * sms;
         }
-        const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(g.ntask, occ[ti][dir]));
+        const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(g.ntask, oc));
         const int32_t *tasks = L.wf_tasks.p + 2 * (fwd ? g.fwd : g.bwd);
         int64_t ntask = g.ntask;
         uint32_t *fl = flags + (fwd ? 0 : L.wf_nflags);
