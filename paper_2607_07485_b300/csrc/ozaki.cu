@@ -25,45 +25,73 @@ __device__ __forceinline__ int find_job(const int64_t *pre, int njobs, int64_t b
 }
 
 // ------------------------------------------------------------------------------- split
-__global__ void __launch_bounds__(256) k_split(const double *src, const SplitJob *jobs, const int64_t *pre,
-                                               int njobs, __half *dst, int32_t *exps) {
+// Operands are split in three launches so that every (64-row tile, 32-wide K chunk) is its own
+// CTA: the row exponents e_r are first cleared, then raised to the exponent of each chunk's row
+// maximum (integer atomic maxima: the order does not matter), then each chunk is cut into
+// slices.  Exponents are held as e + EXP_BIAS while the maxima are formed; 0 marks a row with no
+// nonzero entry (exponent 0), and a stored value below EXP_BIAS / 2 is already final.
+constexpr int EXP_BIAS = 1 << 20;
+__device__ __forceinline__ int exp_decode(int v) { return v >= EXP_BIAS / 2 ? v - EXP_BIAS : v; }
+
+__global__ void __launch_bounds__(256) k_split_clear(const SplitJob *jobs, const int64_t *pre, int njobs,
+                                                     int32_t *exps) {
+    const int j = find_job(pre, njobs, blockIdx.x);
+    const int t = (int)(blockIdx.x - pre[j]);
+    if (threadIdx.x < TM) exps[jobs[j].exp_off + t * TM + threadIdx.x] = 0;
+}
+
+// unit u of job j: tile u / nch, chunk u % nch
+__global__ void __launch_bounds__(256) k_split_max(const double *src, const SplitJob *jobs, const int64_t *pre,
+                                                   int njobs, int32_t *exps) {
     __shared__ double rmax[TM][5];
-    __shared__ int rexp[TM];
     const int j = find_job(pre, njobs, blockIdx.x);
     const SplitJob J = jobs[j];
-    const int t = (int)(blockIdx.x - pre[j]);
-    const int tiles = (int)stor_tiles(J.rows), nch = dcdiv(max(J.K, 1), TK);
+    const int nch = dcdiv(max(J.K, 1), TK);
+    const int u = (int)(blockIdx.x - pre[j]), t = u / nch, c = u % nch;
     const int i0 = t * TM;
     const bool kfast = (J.ks == 1);
     const double *S = src + J.src_off;
-    // row maxima over the whole K
-    {
-        double m = 0.0;
-        int r, g, gs;
-        if (kfast) { r = threadIdx.x >> 2; g = threadIdx.x & 3; gs = 4; }   // 4 threads per row
-        else       { r = threadIdx.x & 63; g = threadIdx.x >> 6; gs = 4; }
-        const int i = i0 + r;
-        if (i < J.rows)
-            for (int k = g; k < J.K; k += gs) m = fmax(m, fabs(S[(int64_t)i * J.rs + (int64_t)k * J.ks]));
-        rmax[r][g] = m;
-        __syncthreads();
-        if (threadIdx.x < TM) {
-            const double v = fmax(fmax(rmax[threadIdx.x][0], rmax[threadIdx.x][1]),
-                                  fmax(rmax[threadIdx.x][2], rmax[threadIdx.x][3]));
-            int e = 0;
-            if (v > 0.0) frexp(v, &e);     // v < 2^e
-            rexp[threadIdx.x] = e;
-            exps[J.exp_off + i0 + threadIdx.x] = e;
+    double m = 0.0;
+    int r, g;
+    if (kfast) { r = threadIdx.x >> 2; g = threadIdx.x & 3; }   // 4 threads per row
+    else       { r = threadIdx.x & 63; g = threadIdx.x >> 6; }
+    const int i = i0 + r;
+    if (i < J.rows)
+        for (int k = c * TK + g; k < min(J.K, (c + 1) * TK); k += 4)
+            m = fmax(m, fabs(S[(int64_t)i * J.rs + (int64_t)k * J.ks]));
+    rmax[r][g] = m;
+    __syncthreads();
+    if (threadIdx.x < TM) {
+        const double v = fmax(fmax(rmax[threadIdx.x][0], rmax[threadIdx.x][1]),
+                              fmax(rmax[threadIdx.x][2], rmax[threadIdx.x][3]));
+        if (v > 0.0) {
+            int e;
+            frexp(v, &e);     // v < 2^e
+            atomicMax(&exps[J.exp_off + i0 + threadIdx.x], e + EXP_BIAS);
         }
-        __syncthreads();
     }
+}
+
+__global__ void __launch_bounds__(256) k_split(const double *src, const SplitJob *jobs, const int64_t *pre,
+                                               int njobs, __half *dst, int32_t *exps) {
+    __shared__ int rexp[TM];
+    const int j = find_job(pre, njobs, blockIdx.x);
+    const SplitJob J = jobs[j];
+    const int tiles = (int)stor_tiles(J.rows), nch = dcdiv(max(J.K, 1), TK);
+    const int u = (int)(blockIdx.x - pre[j]), t = u / nch, c = u % nch;
+    const int i0 = t * TM;
+    const bool kfast = (J.ks == 1);
+    const double *S = src + J.src_off;
+    if (threadIdx.x < TM) rexp[threadIdx.x] = exp_decode(exps[J.exp_off + i0 + threadIdx.x]);
+    __syncthreads();
+    if (c == 0 && threadIdx.x < TM) exps[J.exp_off + i0 + threadIdx.x] = rexp[threadIdx.x];   // final form
     // slices in integer arithmetic (the FP64 pipe is scarce): F = round(v 2^(55 - e_r)) exactly
     // from the bits of v (|F| < 2^55), then its balanced base-256 digits, F = sum_p a_p 2^(48-8p)
     // with the low six a_p in [-128, 127] and |a_0| <= 128, which hold F exactly.  They are read
     // off G = F + 128 (1 + 2^8 + ... + 2^48) > 0: the low six digits are the bytes of G minus 128,
     // the top one G / 2^48 - 128.  Two consecutive k per thread.
     const int64_t pstride = (int64_t)tiles * nch * BLK;
-    for (int c = 0; c < nch; c++) {
+    {
         for (int idx = threadIdx.x; idx < BLK / 2; idx += blockDim.x) {
             int r, kk;
             if (kfast) { r = idx >> 4; kk = (idx & 15) * 2; } else { r = idx & 63; kk = (idx >> 6) * 2; }
@@ -545,20 +573,27 @@ int64_t upload_jobs(const std::vector<Job> &jobs, const std::vector<int64_t> &cn
 void split(const double *src, const std::vector<SplitJob> &jobs, __half *dst, int32_t *exps, cudaStream_t s) {
     if (jobs.empty()) return;
     static_assert(sizeof(SplitJob) % 8 == 0, "job layout");
-    std::vector<int64_t> cnt(jobs.size());
+    // tiles (padding tiles included: they are zero-filled) and (tile, chunk) units per job
+    std::vector<int64_t> ct(jobs.size()), cu(jobs.size());
     for (size_t i = 0; i < jobs.size(); i++) {
-        cnt[i] = jobs[i].rows > 0 ? stor_tiles(jobs[i].rows) : 0;   // padding blocks are zero-filled
+        ct[i] = jobs[i].rows > 0 ? stor_tiles(jobs[i].rows) : 0;
+        cu[i] = ct[i] * cdiv(std::max(jobs[i].K, 1), TK);
     }
-    DBuf<int64_t> buf;
-    const SplitJob *dj = nullptr;
-    const int64_t *dp = nullptr;
-    const int64_t total = upload_jobs(jobs, cnt, buf, dj, dp, s);
-    if (total == 0) return;
-    if (total > 0x7fffffff) fail(LSAMG_LIMIT, "split grid too large");
-    double by = 0.0;   // FP64 operand read once, NS FP16 slices written
-    for (const auto &J : jobs) by += (double)J.rows * J.K * (8.0 + 2.0 * NS);
+    DBuf<int64_t> bt, bu;
+    const SplitJob *dj = nullptr, *dju = nullptr;
+    const int64_t *dpt = nullptr, *dpu = nullptr;
+    const int64_t tt = upload_jobs(jobs, ct, bt, dj, dpt, s);
+    const int64_t tu = upload_jobs(jobs, cu, bu, dju, dpu, s);
+    if (tt == 0) return;
+    if (tu > 0x7fffffff) fail(LSAMG_LIMIT, "split grid too large");
+    double by = 0.0;   // FP64 operand read twice (maxima, slices), NS FP16 slices written
+    for (const auto &J : jobs) by += (double)J.rows * J.K * (16.0 + 2.0 * NS);
     KTime kt(KC_TC_SPLIT, s, 0.0, by);
-    k_split<<<(unsigned)total, 256, 0, s>>>(src, dj, dp, (int)jobs.size(), dst, exps);
+    k_split_clear<<<(unsigned)tt, 64, 0, s>>>(dj, dpt, (int)jobs.size(), exps);
+    CK_LAUNCH();
+    k_split_max<<<(unsigned)tu, 256, 0, s>>>(src, dju, dpu, (int)jobs.size(), exps);
+    CK_LAUNCH();
+    k_split<<<(unsigned)tu, 256, 0, s>>>(src, dju, dpu, (int)jobs.size(), dst, exps);
     CK_LAUNCH();
 }
 

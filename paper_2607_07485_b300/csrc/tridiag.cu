@@ -51,7 +51,8 @@ constexpr int PSL = 2 + 2 * PNB;
 // reflectors; partial sigma = sum a(r)^2 over rows r >= j+2
 __global__ void __launch_bounds__(RB) k_trd_c1(double *base, const int64_t *off, const int32_t *ld, const int32_t *nn,
                                                int64_t count, int j, int j0, const double *VW, const int64_t *vwoff,
-                                               double *part, const int64_t *partoff) {
+                                               double *part, const int64_t *partoff, double *dd,
+                                               const int64_t *toff, double *alph) {
     __shared__ double red[32];
     __shared__ double wj[PNB], vj[PNB];
     const int64_t b = blockIdx.y;
@@ -75,79 +76,18 @@ __global__ void __launch_bounds__(RB) k_trd_c1(double *base, const int64_t *off,
         for (int q = 0; q < jj; q++) a -= V[r + (int64_t)q * n] * wj[q] + W[r + (int64_t)q * n] * vj[q];
         A[r + (int64_t)j * L] = a;
         if (r >= j + 2) sq = a * a;
+        if (r == j) dd[toff[b] + j] = a;          // d_j
+        if (r == j + 1) alph[b] = a;              // alpha of the reflector
     }
     sq = trd_block_sum(sq, red);
     if (threadIdx.x == 0) part[partoff[b] + (int64_t)blockIdx.x * PSL] = sq;
 }
 
-// one CTA: the Householder scalars of column j for every matrix (d_j, e_j, tau_j, the scale of
-// v), then the tiles of the trailing lower triangle that the symmetric product needs (none when
-// the reflector is the identity) and their exclusive prefix over the batch in pre[0..count]
-__global__ void __launch_bounds__(1024) k_trd_sched(double *base, const int64_t *off, const int32_t *ld,
-                                                    const int32_t *nn, int64_t count, int j, double *dd, double *ee,
-                                                    double *tt, const int64_t *toff, const double *part,
-                                                    const int64_t *partoff, double *scal, int64_t *pre) {
-    __shared__ int64_t cnts[1024];
-    const int64_t per = (count + blockDim.x - 1) / blockDim.x;
-    const int64_t b0 = threadIdx.x * per, b1 = min(count, b0 + per);
-    int64_t s = 0;
-    for (int64_t b = b0; b < b1; b++) {
-        const int n = nn[b];
-        if (j >= n) continue;
-        const int L = ld[b];
-        const double *A = base + off[b];
-        double *d = dd + toff[b], *e = ee + toff[b], *tau = tt + toff[b];
-        d[j] = A[j + (int64_t)j * L];
-        const int m = n - j - 1;
-        if (m <= 0) continue;
-        const int nrb = (n - j + RB - 1) / RB;
-        double sig = 0.0;
-        for (int q = 0; q < nrb; q++) sig += part[partoff[b] + (int64_t)q * PSL];
-        const double alpha = A[(j + 1) + (int64_t)j * L];
-        double t = 0.0, sc = 0.0;
-        if (sig == 0.0) {
-            e[j] = alpha;
-        } else {
-            const double beta = -copysign(sqrt(alpha * alpha + sig), alpha);
-            t = (beta - alpha) / beta;
-            sc = 1.0 / (alpha - beta);
-            e[j] = beta;
-        }
-        tau[j] = t;
-        scal[b] = sc;
-        if (t != 0.0) {
-            const int64_t T = (m + ST - 1) / ST;
-            s += T * (T + 1) / 2;
-        }
-    }
-    cnts[threadIdx.x] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int64_t acc = 0;
-        for (int t = 0; t < (int)blockDim.x; t++) {
-            const int64_t v = cnts[t];
-            cnts[t] = acc;
-            acc += v;
-        }
-        pre[count] = acc;
-    }
-    __syncthreads();
-    int64_t acc = cnts[threadIdx.x];
-    for (int64_t b = b0; b < b1; b++) {
-        pre[b] = acc;
-        const int m = nn[b] - j - 1;
-        if (m > 0 && tt[toff[b] + j] != 0.0) {
-            const int64_t T = (m + ST - 1) / ST;
-            acc += T * (T + 1) / 2;
-        }
-    }
-}
-
 // rows j+1 .. n-1 by blocks: v (unit first entry, the scaled column below it) into A, vbuf, V and
 // WV; partial s1 = W^T v and s2 = V^T v over the panel's earlier columns
 __global__ void __launch_bounds__(RB) k_trd_c3(double *base, const int64_t *off, const int32_t *ld, const int32_t *nn,
-                                               int64_t count, int j, int j0, const double *ee, const double *tt,
-                                               const int64_t *toff, const double *scal, double *VW, double *WV,
+                                               int64_t count, int j, int j0, double *ee, double *tt,
+                                               const int64_t *toff, const double *alph, double *VW, double *WV,
                                                const int64_t *vwoff, double *vbuf, double *part,
                                                const int64_t *partoff) {
     __shared__ double vs[RB];
@@ -161,13 +101,29 @@ __global__ void __launch_bounds__(RB) k_trd_c3(double *base, const int64_t *off,
     double *V = VW + vwoff[b];
     const double *W = V + (int64_t)PNB * n;
     double *V2 = WV + vwoff[b] + (int64_t)PNB * n;
-    const double t = tt[toff[b] + j], sc = scal[b];
+    // the Householder scalars of column j (LAPACK's larfg), from the row blocks' partial sums of
+    // squares below the subdiagonal; every CTA of the matrix forms them, the first one stores them
+    const int nrb = (n - j + RB - 1) / RB;
+    double sig = 0.0;
+    for (int q = 0; q < nrb; q++) sig += part[partoff[b] + (int64_t)q * PSL];
+    const double alpha = alph[b];
+    double t = 0.0, sc = 0.0, ej = alpha;
+    if (sig != 0.0) {
+        const double beta = -copysign(sqrt(alpha * alpha + sig), alpha);
+        t = (beta - alpha) / beta;
+        sc = 1.0 / (alpha - beta);
+        ej = beta;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ee[toff[b] + j] = ej;
+        tt[toff[b] + j] = t;
+    }
     const int r = r0 + threadIdx.x;
     double v = 0.0;
     if (r < n) {
         if (r == j + 1) {
             v = 1.0;
-            A[r + (int64_t)j * L] = ee[toff[b] + j];
+            A[r + (int64_t)j * L] = ej;
         } else if (t != 0.0) {
             v = A[r + (int64_t)j * L] * sc;
             A[r + (int64_t)j * L] = v;
@@ -436,7 +392,7 @@ void sytd2_batched(double *base, const MatBatch &Ab, double *d, double *e, doubl
     const int64_t tn = read1(toff + cnt, s);
     std::vector<int64_t> partoff(cnt + 1, 0);
     for (int64_t b = 0; b < cnt; b++) partoff[b + 1] = partoff[b] + cdiv(Ab.h_n[b], RB) * PSL;
-    DBuf<double> VW, WV, vbuf, ybuf, part, scal;
+    DBuf<double> VW, WV, vbuf, ybuf, part, alph;
     DBuf<float2> P;
     DBuf<int64_t> dvw, dpo, dpa, pre, dfo;
     DBuf<float2> F;
@@ -448,8 +404,26 @@ void sytd2_batched(double *base, const MatBatch &Ab, double *d, double *e, doubl
     vbuf.alloc(std::max<int64_t>(tn, 1), s);
     ybuf.alloc(std::max<int64_t>(tn, 1), s);
     part.alloc(std::max<int64_t>(partoff[cnt], 1), s);
-    scal.alloc(cnt, s);
-    pre.alloc(cnt + 1, s);
+    alph.alloc(cnt, s);
+    // tile schedule of the symmetric products for every column step: tiles of the trailing lower
+    // triangle per matrix and their exclusive prefix over the batch (a matrix whose reflector turns
+    // out to be the identity is multiplied all the same; its w is zeroed)
+    {
+        std::vector<int64_t> h((int64_t)Ab.maxn * (cnt + 1), 0);
+        for (int j = 0; j < Ab.maxn; j++) {
+            int64_t *pj = h.data() + (int64_t)j * (cnt + 1), acc = 0;
+            for (int64_t b = 0; b < cnt; b++) {
+                pj[b] = acc;
+                const int64_t m = Ab.h_n[b] - j - 1;
+                if (m > 0) {
+                    const int64_t T = cdiv(m, ST);
+                    acc += T * (T + 1) / 2;
+                }
+            }
+            pj[cnt] = acc;
+        }
+        upload(pre, h, s);
+    }
     upload(dvw, std::vector<int64_t>(vwoff.begin(), vwoff.end() - 1), s);
     upload(dpo, std::vector<int64_t>(poff.begin(), poff.end() - 1), s);
     upload(dpa, std::vector<int64_t>(partoff.begin(), partoff.end() - 1), s);
@@ -478,19 +452,18 @@ void sytd2_batched(double *base, const MatBatch &Ab, double *d, double *e, doubl
             {
                 KTime kt(KC_SYTD2, s);
                 const dim3 g1((unsigned)cdiv(Ab.maxn - j, RB), (unsigned)cnt);
-                k_trd_c1<<<g1, RB, 0, s>>>(base, Ab.off.p, Ab.ld.p, Ab.n.p, cnt, j, j0, VW.p, dvw.p, part.p, dpa.p);
-                CK_LAUNCH();
-                k_trd_sched<<<1, 1024, 0, s>>>(base, Ab.off.p, Ab.ld.p, Ab.n.p, cnt, j, d, e, tau, toff, part.p,
-                                               dpa.p, scal.p, pre.p);
+                k_trd_c1<<<g1, RB, 0, s>>>(base, Ab.off.p, Ab.ld.p, Ab.n.p, cnt, j, j0, VW.p, dvw.p, part.p, dpa.p, d,
+                                           toff, alph.p);
                 CK_LAUNCH();
                 if (j >= Ab.maxn - 1) break;
-                k_trd_c3<<<g3, RB, 0, s>>>(base, Ab.off.p, Ab.ld.p, Ab.n.p, cnt, j, j0, e, tau, toff, scal.p, VW.p,
+                k_trd_c3<<<g3, RB, 0, s>>>(base, Ab.off.p, Ab.ld.p, Ab.n.p, cnt, j, j0, e, tau, toff, alph.p, VW.p,
                                            WV.p, dvw.p, vbuf.p, part.p, dpa.p);
                 CK_LAUNCH();
             }
             {
                 KTime ks(KC_SYMV, s, 0.0, by);
-                k_trd_symv<<<symv_grid, 256, 0, s>>>(F.p, dfo.p, Ab.n.p, cnt, j, toff, vbuf.p, P.p, dpo.p, pre.p);
+                k_trd_symv<<<symv_grid, 256, 0, s>>>(F.p, dfo.p, Ab.n.p, cnt, j, toff, vbuf.p, P.p, dpo.p,
+                                                     pre.p + (int64_t)j * (cnt + 1));
                 CK_LAUNCH();
             }
             {
