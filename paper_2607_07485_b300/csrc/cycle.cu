@@ -827,6 +827,11 @@ static void tri_solve(Level &L, int grp, const int32_t *sys, const int64_t *Optr
     static int occ[2][2][2] = {{{0, 0}, {0, 0}}, {{0, 0}, {0, 0}}};
     const int ti = std::is_same<T, double>::value ? 1 : 0;
     const int single = nrhs == 1 ? 1 : 0;
+    // right-hand sides in groups of WF_RG, one forward and one backward wavefront per group (epoch
+    // = group + 1 on the same flags): a task publishes its block after all the right-hand sides
+    // it carries, so carrying more of them in one launch would lengthen the critical path with
+    // every group
+    for (int g0 = 0, gi = 0; g0 < nrhs; g0 += WF_RG, gi++)
     for (int dir = 0; dir < 2; dir++) {
         const bool fwd = dir == 0;
         void *fn = single ? (fwd ? (void *)k_tri_wave<T, true, 1> : (void *)k_tri_wave<T, false, 1>)
@@ -844,11 +849,13 @@ static void tri_solve(Level &L, int grp, const int32_t *sys, const int64_t *Optr
         const int32_t *tasks = L.wf_tasks.p + 2 * (fwd ? g.fwd : g.bwd);
         int64_t ntask = g.ntask;
         uint32_t *fl = flags + (fwd ? 0 : L.wf_nflags);
-        uint32_t epoch = 1;
+        uint32_t epoch = (uint32_t)gi + 1;
         const int64_t *foff = L.wf_foff.p;
+        T *wsg = ws + (int64_t)g0 * wsn;
+        int nr = std::min(WF_RG, nrhs - g0);
         void *args[] = {(void *)&tasks, (void *)&ntask, (void *)&sys, (void *)&Optr, (void *)&Lp, (void *)&Loff,
                         (void *)&Dp, (void *)&Doff, (void *)&foff, (void *)&fl, (void *)&epoch, (void *)&cb,
-                        (void *)&ws, (void *)&wsn, (void *)&nrhs, (void *)&err};
+                        (void *)&wsg, (void *)&wsn, (void *)&nr, (void *)&err};
         CK(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(256), args, 0, s));
         count_launch();
     }
