@@ -732,3 +732,30 @@ def test_fp32_emulated_cycle_within_rounding_of_fp64():
     rel = np.linalg.norm(z32 - z64) / np.linalg.norm(z64)
     eps32 = np.finfo(np.float32).eps
     assert 100 * np.finfo(float).eps < rel <= 64 * eps32 * kappa, (rel, kappa)
+
+
+def test_a_closure_on_a_coarse_level_is_inside_the_g_row_closure():
+    # Def. 5.2 on the Galerkin level of the CG1 problem: Omega^A_i is contained in Omega^G_i (an
+    # assembled entry needs an element holding both DOFs), and every interface DOF it keeps has an
+    # entry above the relative cut in a row of omega_i (brute force on the assembled coarse matrix)
+    n, d, K = fegen.cg1_tri(32)
+    H = O.setup(n, d, K, opts=dict(tau_c=1.0, closure="A", max_levels=3, max_density=1.0, agg_passes=1,
+                                    agg_passes_coarse=1))
+    assert len(H.levels) >= 2
+    L1 = H.levels[1]
+    if L1.coarsest:
+        pytest.skip("no coarse aggregation level at this size")
+    agg, nagg = L1.agg, L1.nagg
+    *_, OmG = O.closure(L1.elems, agg, nagg)
+    A1 = L1.A.toarray()
+    dg = np.sqrt(np.abs(np.diag(A1)))
+    for i in range(nagg):
+        w = set(np.flatnonzero(agg == i).tolist())
+        a, g = set(L1.Omega[i].tolist()), set(OmG[i].tolist())
+        assert w <= a <= g
+        for p in a - w:
+            q = np.array(sorted(w))
+            assert np.any(np.abs(A1[q, p]) > OL.ACUT * dg[q] * dg[p])
+        for p in g - a:
+            q = np.array(sorted(w))
+            assert not np.any(np.abs(A1[q, p]) > OL.ACUT * dg[q] * dg[p])
