@@ -385,11 +385,29 @@ def main():
         torch.cuda.synchronize()
         return amg
 
-    def solve(amg, mode):
+    def solve(amg, mode, keep=None):
         t1 = time.perf_counter()
         x, its, rel, rc = amg.solve(d_b, mode=mode)
         torch.cuda.synchronize()
+        if keep is not None:
+            keep[mode] = x
         return time.perf_counter() - t1, int(np.max(its)), float(np.max(rel)), rc
+
+    def check_solutions(amg, xs):
+        """Outside any timed region: the true residual ||b - A x|| / ||b|| of each mode's solution
+        (A applied by the level-0 Gram SpMV, independently of the Krylov recursion) and the
+        distance of the FP32-cycle solution from the all-FP64 one, per right-hand side (maxima)."""
+        B = d_b.reshape(-1, n)
+        out = {}
+        for mode, x in xs.items():
+            X = x.reshape(-1, n)
+            out[mode] = dict(true_relres=max(float(torch.linalg.norm(B[r] - amg.gram_spmv(X[r])) /
+                                                   torch.linalg.norm(B[r])) for r in range(B.shape[0])))
+        if 0 in xs and 1 in xs:
+            X0, X1 = xs[0].reshape(-1, n), xs[1].reshape(-1, n)
+            out[1]["x_rel_diff_vs_fp64_mode"] = max(float(torch.linalg.norm(X1[r] - X0[r]) / torch.linalg.norm(X0[r]))
+                                                    for r in range(X0.shape[0]))
+        return out
 
     def step(mode, profile=0):
         amg = setup(profile)
@@ -406,10 +424,15 @@ def main():
         t0 = time.perf_counter()
         amg = setup()
         st = amg.stats()
+        xs = {} if w == 0 else None
         for mode in ((0, 1) if w == 0 else (best_mode,)):
-            tsol, its, rel, rc = solve(amg, mode)
-            modes[mode] = dict(setup_s=st["setup_seconds"], solve_s=tsol, its=its, relres=rel,
-                               converged=(rc == 0), step_s=time.perf_counter() - t0)
+            tsol, its, rel, rc = solve(amg, mode, xs)
+            modes.setdefault(mode, {}).update(setup_s=st["setup_seconds"], solve_s=tsol, its=its, relres=rel,
+                                              converged=(rc == 0), step_s=time.perf_counter() - t0)
+        if xs:
+            for mode, v in check_solutions(amg, xs).items():
+                modes[mode].update(v)
+            del xs
         amg.close()
         print(f"[bench] warm-up {w}: " + ", ".join(f"mode {m}: set-up {v['setup_s']:.2f} s, solve {v['solve_s']:.2f} s, "
                                                      f"{v['its']} its" for m, v in modes.items()),

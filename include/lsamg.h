@@ -200,7 +200,8 @@ int64_t lsamg_launch_count(void);
  *   (A[i + k lda], B[j + k ldb], C[i + j ldc]; lda >= M, ldb >= N, ldc >= M).
  * Each row of A and of B is scaled by a power of two and cut into seven 8-bit integer slices held
  * exactly in FP16; the 28 slice products that carry FP64 precision are accumulated exactly in
- * FP32 by mma.sync over K chunks of 32 and in int32 across chunks, then combined in FP64.  The
+ * FP32 by tcgen05.mma (accumulators in tensor memory) over K pieces of 128 and in 64-bit
+ * integers across pieces, then rounded once to FP64 and combined with C.  The
  * error of C_ij is a few units of 2^-53 K max_k|A_ik| max_k|B_jk| (the normwise bound of an FP64
  * dot product).  beta == 0 does not read C.  Allocates workspace (about 14 (M + N) K bytes).
  * Returns LSAMG_INVALID_ARG for bad sizes or leading dimensions, LSAMG_DEVICE_TIMEOUT if a staging
