@@ -2,6 +2,7 @@
 #include "common.cuh"
 
 #include <cstdarg>
+#include <deque>
 #include <cstdlib>
 #include <ctime>
 
@@ -28,7 +29,7 @@ struct KPending {
     cudaEvent_t a, b;
     double flops, bytes;
 };
-static std::vector<KPending> g_kpend;
+static std::deque<KPending> g_kpend;
 static KStat g_kacc[KC_N];
 
 static std::vector<cudaEvent_t> g_evpool;
@@ -48,24 +49,41 @@ KTime::KTime(int c, cudaStream_t st, double f, double b) : cls(c), s(st), flops(
     e0 = ev_get();
     cudaEventRecord(e0, s);
 }
+static void kt_account(const KPending &p) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, p.a, p.b);
+    g_kacc[p.cls].ms += ms;
+    g_kacc[p.cls].calls += 1;
+    g_kacc[p.cls].flops += p.flops;
+    g_kacc[p.cls].bytes += p.bytes;
+    g_evpool.push_back(p.a);
+    g_evpool.push_back(p.b);
+}
+
 KTime::~KTime() {
     if (!g_kt_on || !e0) return;
     cudaEvent_t e1 = ev_get();
     cudaEventRecord(e1, s);
     g_kpend.push_back({cls, e0, e1, flops, bytes});
+    // fold the intervals the device has finished into the totals and recycle their events, so
+    // that a long profiled run holds a bounded number of events (polling, never waiting)
+    if (g_kpend.size() >= 4096 && cudaPeekAtLastError() == cudaSuccess) {
+        while (!g_kpend.empty()) {
+            const cudaError_t q = cudaEventQuery(g_kpend.front().b);
+            if (q != cudaSuccess) {
+                if (q == cudaErrorNotReady) (void)cudaGetLastError();   // not an error: still running
+                break;
+            }
+            kt_account(g_kpend.front());
+            g_kpend.pop_front();
+        }
+    }
 }
 
 void ktimer_collect(KStat out[KC_N]) {
     for (auto &p : g_kpend) {
         cudaEventSynchronize(p.b);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, p.a, p.b);
-        g_kacc[p.cls].ms += ms;
-        g_kacc[p.cls].calls += 1;
-        g_kacc[p.cls].flops += p.flops;
-        g_kacc[p.cls].bytes += p.bytes;
-        g_evpool.push_back(p.a);
-        g_evpool.push_back(p.b);
+        kt_account(p);
     }
     g_kpend.clear();
     if (out)
