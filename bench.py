@@ -524,6 +524,10 @@ def main():
             ach = k["bytes"] / t / 1e9
             r = dict(kernel=name, bound="hbm", achieved=ach, peak=hbm_peak, unit="GB/s", frac=ach / hbm_peak,
                      peak_source="measured" if "hbm_gbs" in peaks else "fallback")
+            if k["flops"] > 0:
+                # FP64 multiply-adds beside the bytes (the Gram SpMV: two per 8-byte G_T entry, so
+                # the FP64 pipe caps it below the HBM rate); their share of the FP64 peak
+                r.update(fp64_tflops=k["flops"] / t / 1e12, fp64_pipe_frac=k["flops"] / t / 1e12 / FP64_PEAK_TFLOPS)
         if r is not None:
             per_launch = k["bytes"] / max(k["calls"], 1)
             r.update(ms=k["ms"] / PROFILED_STEPS, launches=k["calls"] // PROFILED_STEPS,

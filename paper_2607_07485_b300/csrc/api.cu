@@ -110,6 +110,7 @@ void finish_level_info(Level &L, cudaStream_t s) {
         gent += (double)gr[e] * (double)(ep[e + 1] - ep[e]);
         ment += (double)(ep[e + 1] - ep[e]);
     }
+    L.spmv_fmas = 2.0 * gent;
     for (int t = 0; t < 2; t++) {
         const double w = t ? 8.0 : 4.0;
         L.spmv_bytes[t] = gent * w + ment * 4.0 + 3.0 * (double)L.n * w;

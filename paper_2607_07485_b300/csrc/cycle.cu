@@ -62,6 +62,7 @@ __global__ void __launch_bounds__(128) k_spmv(const int64_t *eptr, const int32_t
 // to nT + 1: conflict-free row and column reads); t = G_T x_T with lanes on rows, then
 // G_T^T t with lanes on columns, x_T gathered once per right-hand side and broadcast by shuffles.
 constexpr int SPMV_WARPS = 8;
+constexpr int SPMV_LOADS = 8;
 template <class T>
 __global__ void __launch_bounds__(256) k_spmv_warp(const int64_t *eptr, const int32_t *eidx, int64_t ne,
                                                    const T *G, const int64_t *goff, const int32_t *grows,
@@ -75,9 +76,24 @@ __global__ void __launch_bounds__(256) k_spmv_warp(const int64_t *eptr, const in
         const int nT = (int)(eptr[e + 1] - b);
         const int m = grows[e];
         const T *g = G + goff[e];
-        for (int t = lane; t < m * nT; t += 32) {
-            const int i = t / nT, c = t - i * nT;
-            Gs[i * ldt + c] = g[t];
+        // SPMV_LOADS loads per lane in flight before their stores (a load-store loop would wait
+        // for each load in turn)
+        const int tot = m * nT;
+        for (int t0 = 0; t0 < tot; t0 += 32 * SPMV_LOADS) {
+            T v[SPMV_LOADS];
+#pragma unroll
+            for (int u = 0; u < SPMV_LOADS; u++) {
+                const int t = t0 + 32 * u + lane;
+                v[u] = t < tot ? g[t] : (T)0;
+            }
+#pragma unroll
+            for (int u = 0; u < SPMV_LOADS; u++) {
+                const int t = t0 + 32 * u + lane;
+                if (t < tot) {
+                    const int i = t / nT, c = t - i * nT;
+                    Gs[i * ldt + c] = v[u];
+                }
+            }
         }
         const int d0 = lane < nT ? eidx[b + lane] : 0, d1 = lane + 32 < nT ? eidx[b + 32 + lane] : 0;
         __syncwarp();
@@ -104,22 +120,109 @@ __global__ void __launch_bounds__(256) k_spmv_warp(const int64_t *eptr, const in
     }
 }
 
+// Larger elements (the Galerkin levels): a CTA per element.  x_T is gathered once into shared
+// memory; the rows go by chunks of SPMV_RC: first t_i = G_T(i,:) x_T for the chunk's rows (a warp
+// per two rows, lanes along the rows, eight loads per lane in flight), then the chunk's share
+// G_T(chunk,:)^T t of the column sums, which stay in shared memory (each column owned by one
+// thread).  The second pass re-reads a chunk read just before (16 rows, from L1/L2), so G_T
+// crosses HBM once.  The arithmetic order is that of k_spmv: row sums lane-strided then
+// shuffle-reduced, column sums row by row.
+constexpr int SPMV_RC = 16;
+template <class T>
+__global__ void __launch_bounds__(256) k_spmv_rows(const int64_t *eptr, const int32_t *eidx, int64_t ne,
+                                                   const T *G, const int64_t *goff, const int32_t *grows,
+                                                   const T *x, T *y, int64_t n, int nrhs, T sign, int ldx) {
+    extern __shared__ unsigned char smraw[];
+    T *xs = reinterpret_cast<T *>(smraw);
+    T *ys = xs + ldx;
+    T *ts = ys + ldx;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NW = 8;   // warps per CTA (launch bounds 256)
+    for (int64_t e = blockIdx.x; e < ne; e += gridDim.x) {
+        const int64_t b = eptr[e];
+        const int nT = (int)(eptr[e + 1] - b);
+        const int m = grows[e];
+        const T *g = G + goff[e];
+        for (int r = 0; r < nrhs; r++) {
+            const T *xr = x + (int64_t)r * n;
+            for (int c = threadIdx.x; c < nT; c += blockDim.x) {
+                xs[c] = xr[eidx[b + c]];
+                ys[c] = (T)0;
+            }
+            __syncthreads();
+            for (int i0 = 0; i0 < m; i0 += SPMV_RC) {
+                const int rc = min(SPMV_RC, m - i0);
+                if (warp < rc) {
+                    const int i2 = warp + NW;
+                    const bool two = i2 < rc;
+                    const T *g1 = g + (int64_t)(i0 + warp) * nT;
+                    const T *g2 = g + (int64_t)(i0 + (two ? i2 : warp)) * nT;
+                    T s1 = 0, s2 = 0;
+#pragma unroll 4
+                    for (int c = lane; c < nT; c += 32) {
+                        const T xc = xs[c];
+                        s1 += g1[c] * xc;
+                        if (two) s2 += g2[c] * xc;
+                    }
+                    s1 = warp_sum(s1);
+                    s2 = warp_sum(s2);
+                    if (lane == 0) {
+                        ts[warp] = s1;
+                        if (two) ts[i2] = s2;
+                    }
+                }
+                __syncthreads();
+                for (int c = threadIdx.x; c < nT; c += blockDim.x) {
+                    const T *gc = g + (int64_t)i0 * nT + c;
+                    T acc = ys[c];
+#pragma unroll 4
+                    for (int i = 0; i < rc; i++) acc += gc[(int64_t)i * nT] * ts[i];
+                    ys[c] = acc;
+                }
+                __syncthreads();
+            }
+            T *yr = y + (int64_t)r * n;
+            for (int c = threadIdx.x; c < nT; c += blockDim.x) atomicAdd(&yr[eidx[b + c]], sign * ys[c]);
+            __syncthreads();
+        }
+    }
+}
+
+// shared memory of the warp-per-element kernels (eight padded G_T tiles), 0 when the level's
+// element blocks exceed 64 x 64 or the tiles exceed 200 KB
+template <class T>
+size_t spmv_warp_smem(const Level &L) {
+    if (L.max_nT > 64 || L.max_grows_cached > 64) return 0;
+    const size_t sm = (size_t)SPMV_WARPS * std::max(1, L.max_grows_cached) * (L.max_nT + 1) * sizeof(T);
+    return sm <= 200 * 1024 ? sm : 0;
+}
+
 // launches the Gram SpMV of level L: y (+)= sign G^T G x
 template <class T>
 void launch_spmv(const Level &L, const T *G, const T *x, T *y, int nrhs, T sign, cudaStream_t s) {
-    if (L.max_nT <= 64 && L.max_grows_cached <= 64) {
+    const size_t rows_sm = (2 * (size_t)std::max(1, L.max_nT) + SPMV_RC) * sizeof(T);
+    if (const size_t sm = spmv_warp_smem<T>(L)) {
         const int ldt = L.max_nT + 1, rows = std::max(1, L.max_grows_cached);
-        const size_t sm = (size_t)SPMV_WARPS * rows * ldt * sizeof(T);
         CK(cudaFuncSetAttribute(k_spmv_warp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         const unsigned grid = gridv(L.ne, SPMV_WARPS, 148 * 8);
         k_spmv_warp<T><<<grid, 32 * SPMV_WARPS, sm, s>>>(L.eptr.p, L.eidx.p, L.ne, G, L.goff.p, L.grows.p, x, y,
                                                         L.n, nrhs, sign, ldt, rows);
+    } else if (rows_sm <= 160 * 1024) {
+        CK(cudaFuncSetAttribute(k_spmv_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rows_sm));
+        k_spmv_rows<T><<<gridv(L.ne, 1, 148 * 8), 256, rows_sm, s>>>(L.eptr.p, L.eidx.p, L.ne, G, L.goff.p,
+                                                                     L.grows.p, x, y, L.n, nrhs, sign,
+                                                                     std::max(1, L.max_nT));
     } else {
         const size_t sm = (size_t)std::max(1, L.max_grows_cached) * sizeof(T);
         k_spmv<T><<<gridv(L.ne, 1, 148 * 24), 128, sm, s>>>(L.eptr.p, L.eidx.p, L.ne, G, L.goff.p, L.grows.p, x,
                                                           y, L.n, nrhs, sign);
     }
     CK_LAUNCH();
+}
+
+template <class T>
+double spmv_flops(const Level &L, int nrhs) {
+    return std::is_same<T, double>::value ? 2.0 * L.spmv_fmas * nrhs : 0.0;   // FP64 work only
 }
 
 // ---------------------------------------------------------------- packed triangular solves
@@ -684,6 +787,72 @@ __global__ void __launch_bounds__(128) k_sw_scatter(const int32_t *pa, const int
     }
 }
 
+// The same for levels whose element blocks fit 64 x 64 (the fine level): a warp per pair, eight
+// per CTA, G_T staged in the warp's shared tile as in k_spmv_warp (rows padded to nT + 1), the
+// subdomain correction gathered once per right-hand side and broadcast by shuffles.
+template <class T>
+__global__ void __launch_bounds__(256) k_sw_scatter_warp(const int32_t *pa, const int64_t *pj, int64_t npairs,
+                                                         const int64_t *Optr, const int64_t *locoff,
+                                                         const int32_t *loc, const int32_t *oeidx,
+                                                         const int64_t *eptr, const int32_t *eidx, const T *G,
+                                                         const int64_t *goff, const int32_t *grows, const T *ws,
+                                                         T *res, int64_t n, int64_t wsn, int nrhs, int ldt,
+                                                         int rows) {
+    extern __shared__ unsigned char smraw[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T *Gs = reinterpret_cast<T *>(smraw) + (int64_t)warp * rows * ldt;
+    for (int64_t q = (int64_t)blockIdx.x * SPMV_WARPS + warp; q < npairs; q += (int64_t)gridDim.x * SPMV_WARPS) {
+        const int32_t a = pa[q];
+        const int64_t j = pj[q];
+        const int32_t e = oeidx[j];
+        const int64_t b = eptr[e];
+        const int nT = (int)(eptr[e + 1] - b);
+        const int m = grows[e];
+        const T *g = G + goff[e];
+        const int32_t *lc = loc + locoff[j];
+        const int tot = m * nT;
+        for (int t0 = 0; t0 < tot; t0 += 32 * SPMV_LOADS) {
+            T v[SPMV_LOADS];
+#pragma unroll
+            for (int u = 0; u < SPMV_LOADS; u++) {
+                const int t = t0 + 32 * u + lane;
+                v[u] = t < tot ? g[t] : (T)0;
+            }
+#pragma unroll
+            for (int u = 0; u < SPMV_LOADS; u++) {
+                const int t = t0 + 32 * u + lane;
+                if (t < tot) {
+                    const int i = t / nT, c = t - i * nT;
+                    Gs[i * ldt + c] = v[u];
+                }
+            }
+        }
+        const int p0 = lane < nT ? lc[lane] : -1, p1 = lane + 32 < nT ? lc[lane + 32] : -1;
+        const int d0 = lane < nT ? eidx[b + lane] : 0, d1 = lane + 32 < nT ? eidx[b + 32 + lane] : 0;
+        __syncwarp();
+        for (int r = 0; r < nrhs; r++) {
+            const T *v = ws + (int64_t)r * wsn + Optr[a];
+            const T x0 = p0 >= 0 ? v[p0] : (T)0, x1 = p1 >= 0 ? v[p1] : (T)0;
+            T t0 = 0, t1 = 0;
+            for (int c = 0; c < nT; c++) {
+                const T xc = __shfl_sync(0xffffffffu, c < 32 ? x0 : x1, c & 31);
+                if (lane < m) t0 += Gs[lane * ldt + c] * xc;
+                if (lane + 32 < m) t1 += Gs[(lane + 32) * ldt + c] * xc;
+            }
+            T y0 = 0, y1 = 0;
+            for (int i = 0; i < m; i++) {
+                const T ti = __shfl_sync(0xffffffffu, i < 32 ? t0 : t1, i & 31);
+                if (lane < nT) y0 += Gs[i * ldt + lane] * ti;
+                if (lane + 32 < nT) y1 += Gs[i * ldt + lane + 32] * ti;
+            }
+            T *rr = res + (int64_t)r * n;
+            if (lane < nT) atomicAdd(&rr[d0], -y0);
+            if (lane + 32 < nT) atomicAdd(&rr[d1], -y1);
+        }
+        __syncwarp();
+    }
+}
+
 template <class T>
 __global__ void k_fill(T *a, int64_t n, T v) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -773,7 +942,7 @@ void gram_spmv(const Level &L, const T *x, T *y, const T *b, int nrhs, cudaStrea
         CK(cudaMemsetAsync(y, 0, tot * sizeof(T), s));
     }
     if (L.ne == 0) return;
-    KTime kt(KC_SPMV, s, 0.0, L.spmv_bytes[std::is_same<T, double>::value ? 1 : 0] * (nrhs > 1 ? 1.0 : 1.0));
+    KTime kt(KC_SPMV, s, spmv_flops<T>(L, nrhs), L.spmv_bytes[std::is_same<T, double>::value ? 1 : 0]);
     const T *G = std::is_same<T, float>::value ? (const T *)L.G32.p : (const T *)L.G64.p;
     launch_spmv<T>(L, G, x, y, nrhs, b ? (T)-1 : (T)1, s);
 }
@@ -955,7 +1124,17 @@ static void sweep_split(Level &L, int c, int nrhs, cudaStream_t s) {
     k_sw_addx<T><<<gg, 256, 0, s>>>(aggs, L.Optr.p, L.Oidx.p, ws, xvec<T>(L), L.n, L.Omega_total, nrhs);
     CK_LAUNCH();
     const int64_t np = L.colpairs[c + 1] - L.colpairs[c];
-    if (np > 0) {
+    const size_t wsm = spmv_warp_smem<T>(L);
+    if (np > 0 && wsm > 0) {
+        const int ldt = L.max_nT + 1, rows = std::max(1, L.max_grows_cached);
+        const size_t sm = wsm;
+        CK(cudaFuncSetAttribute(k_sw_scatter_warp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_sw_scatter_warp<T><<<gridv(np, SPMV_WARPS, 148 * 8), 32 * SPMV_WARPS, sm, s>>>(
+            L.pair_agg.p + L.colpairs[c], L.pair_ent.p + L.colpairs[c], np, L.Optr.p, L.oelocoff.p, L.oeloc.p,
+            L.oeidx.p, L.eptr.p, L.eidx.p, G, L.goff.p, L.grows.p, ws, rvec<T>(L), L.n, L.Omega_total, nrhs, ldt,
+            rows);
+        CK_LAUNCH();
+    } else if (np > 0) {
         size_t sm = (size_t)std::max(1, L.max_grows_cached) * sizeof(T);
         k_sw_scatter<T><<<(unsigned)std::min<int64_t>(np, 148 * 16), 128, sm, s>>>(
             L.pair_agg.p + L.colpairs[c], L.pair_ent.p + L.colpairs[c], np, L.Optr.p, L.oelocoff.p, L.oeloc.p,
@@ -1084,7 +1263,7 @@ void vcycle(Handle &H, int l, int nrhs, cudaStream_t s) {
     CK(cudaMemcpyAsync(r, b, tot * sizeof(T), cudaMemcpyDeviceToDevice, s));
     {
         LSAMG_PROF(l == 0 ? "vc: L0 residual spmv" : "vc: Lc residual spmv", s);
-        KTime kt(KC_SPMV, s, 0.0, L.spmv_bytes[std::is_same<T, double>::value ? 1 : 0]);
+        KTime kt(KC_SPMV, s, spmv_flops<T>(L, nrhs), L.spmv_bytes[std::is_same<T, double>::value ? 1 : 0]);
         const T *G;
         if constexpr (std::is_same<T, float>::value) G = L.G32.p; else G = L.G64.p;
         launch_spmv<T>(L, G, x, r, nrhs, (T)-1, s);

@@ -101,6 +101,7 @@ struct Level {
     // algorithmic bytes per application (index 0: FP32, 1: FP64): Gram SpMV, one colour of the
     // Schwarz sweep (per colour), the coarsest triangular solves
     double spmv_bytes[2] = {0, 0};
+    double spmv_fmas = 0;               // multiply-adds of one Gram SpMV (two per stored G_T entry)
     std::vector<double> sweep_bytes[2];
     std::vector<int32_t> colmax;        // largest |Omega_i| of each colour
     std::vector<int64_t> colpairs;      // colour c owns pairs [colpairs[c], colpairs[c+1])
