@@ -1,8 +1,7 @@
 """GPU parity for the additive Schwarz smoother (option smoother=1, the parallel block smoother
 Section 2 allows) and the stationary V-cycle solve mode (mode 2, the standalone iteration of
-the Section 6 tests), against the oracle's ``vcycle(smoother="additive")`` and ``stationary``.
-
-Not yet run on a B300: the whole module is skipped until it has passed there once."""
+the Section 6 tests), against the oracle's ``vcycle(smoother="additive")`` and ``stationary``;
+CUDA-graph replay of the V-cycle against eager launches; the tile-shape autotuner on the GPU."""
 import numpy as np
 import pytest
 
