@@ -33,6 +33,9 @@ __device__ __forceinline__ int find_job(const int64_t *pre, int njobs, int64_t b
 constexpr int EXP_BIAS = 1 << 20;
 __device__ __forceinline__ int exp_decode(int v) { return v >= EXP_BIAS / 2 ? v - EXP_BIAS : v; }
 
+constexpr int SPLIT_THREADS = 256;   // threads of k_split_max and k_split (a 64 x 32 chunk per CTA)
+static_assert(BLK / 2 % SPLIT_THREADS == 0, "pairs of a chunk per thread");
+
 __global__ void __launch_bounds__(256) k_split_clear(const SplitJob *jobs, const int64_t *pre, int njobs,
                                                      int32_t *exps) {
     const int j = find_job(pre, njobs, blockIdx.x);
@@ -41,7 +44,7 @@ __global__ void __launch_bounds__(256) k_split_clear(const SplitJob *jobs, const
 }
 
 // unit u of job j: tile u / nch, chunk u % nch
-__global__ void __launch_bounds__(256) k_split_max(const double *src, const SplitJob *jobs, const int64_t *pre,
+__global__ void __launch_bounds__(SPLIT_THREADS) k_split_max(const double *src, const SplitJob *jobs, const int64_t *pre,
                                                    int njobs, int32_t *exps) {
     __shared__ double rmax[TM][5];
     const int j = find_job(pre, njobs, blockIdx.x);
@@ -56,9 +59,14 @@ __global__ void __launch_bounds__(256) k_split_max(const double *src, const Spli
     if (kfast) { r = threadIdx.x >> 2; g = threadIdx.x & 3; }   // 4 threads per row
     else       { r = threadIdx.x & 63; g = threadIdx.x >> 6; }
     const int i = i0 + r;
-    if (i < J.rows)
-        for (int k = c * TK + g; k < min(J.K, (c + 1) * TK); k += 4)
-            m = fmax(m, fabs(S[(int64_t)i * J.rs + (int64_t)k * J.ks]));
+    double v[TK / 4];   // this thread's entries of the chunk, all loads in flight at once
+#pragma unroll
+    for (int q = 0; q < TK / 4; q++) {
+        const int k = c * TK + g + 4 * q;
+        v[q] = (i < J.rows && k < J.K) ? S[(int64_t)i * J.rs + (int64_t)k * J.ks] : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < TK / 4; q++) m = fmax(m, fabs(v[q]));
     rmax[r][g] = m;
     __syncthreads();
     if (threadIdx.x < TM) {
@@ -72,8 +80,8 @@ __global__ void __launch_bounds__(256) k_split_max(const double *src, const Spli
     }
 }
 
-__global__ void __launch_bounds__(256) k_split(const double *src, const SplitJob *jobs, const int64_t *pre,
-                                               int njobs, __half *dst, int32_t *exps) {
+__global__ void __launch_bounds__(SPLIT_THREADS) k_split(const double *src, const SplitJob *jobs, const int64_t *pre,
+                                                         int njobs, __half *dst, int32_t *exps) {
     __shared__ int rexp[TM];
     const int j = find_job(pre, njobs, blockIdx.x);
     const SplitJob J = jobs[j];
@@ -82,6 +90,21 @@ __global__ void __launch_bounds__(256) k_split(const double *src, const SplitJob
     const int i0 = t * TM;
     const bool kfast = (J.ks == 1);
     const double *S = src + J.src_off;
+    // the chunk's entries of this thread are loaded first, all in flight at once
+    constexpr int IT = BLK / 2 / SPLIT_THREADS;
+    double vin[IT][2];
+#pragma unroll
+    for (int it = 0; it < IT; it++) {
+        const int idx = threadIdx.x + it * SPLIT_THREADS;
+        int r, kk;
+        if (kfast) { r = idx >> 4; kk = (idx & 15) * 2; } else { r = idx & 63; kk = (idx >> 6) * 2; }
+        const int i = i0 + r;
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int k = c * TK + kk + h;
+            vin[it][h] = (i < J.rows && k < J.K) ? S[(int64_t)i * J.rs + (int64_t)k * J.ks] : 0.0;
+        }
+    }
     if (threadIdx.x < TM) rexp[threadIdx.x] = exp_decode(exps[J.exp_off + i0 + threadIdx.x]);
     __syncthreads();
     if (c == 0 && threadIdx.x < TM) exps[J.exp_off + i0 + threadIdx.x] = rexp[threadIdx.x];   // final form
@@ -92,16 +115,15 @@ __global__ void __launch_bounds__(256) k_split(const double *src, const SplitJob
     // the top one G / 2^48 - 128.  Two consecutive k per thread.
     const int64_t pstride = (int64_t)tiles * nch * BLK;
     {
-        for (int idx = threadIdx.x; idx < BLK / 2; idx += blockDim.x) {
+#pragma unroll
+        for (int it = 0; it < IT; it++) {
+            const int idx = threadIdx.x + it * SPLIT_THREADS;
             int r, kk;
             if (kfast) { r = idx >> 4; kk = (idx & 15) * 2; } else { r = idx & 63; kk = (idx >> 6) * 2; }
-            const int i = i0 + r;
             int dig[2][NS];
 #pragma unroll
             for (int h = 0; h < 2; h++) {
-                const int k = c * TK + kk + h;
-                double v = 0.0;
-                if (i < J.rows && k < J.K) v = S[(int64_t)i * J.rs + (int64_t)k * J.ks];
+                const double v = vin[it][h];
                 const uint64_t bits = (uint64_t)__double_as_longlong(v);
                 int ef = (int)((bits >> 52) & 0x7ff);
                 uint64_t mant = bits & ((1ull << 52) - 1);
@@ -591,9 +613,9 @@ void split(const double *src, const std::vector<SplitJob> &jobs, __half *dst, in
     KTime kt(KC_TC_SPLIT, s, 0.0, by);
     k_split_clear<<<(unsigned)tt, 64, 0, s>>>(dj, dpt, (int)jobs.size(), exps);
     CK_LAUNCH();
-    k_split_max<<<(unsigned)tu, 256, 0, s>>>(src, dju, dpu, (int)jobs.size(), exps);
+    k_split_max<<<(unsigned)tu, SPLIT_THREADS, 0, s>>>(src, dju, dpu, (int)jobs.size(), exps);
     CK_LAUNCH();
-    k_split<<<(unsigned)tu, 256, 0, s>>>(src, dju, dpu, (int)jobs.size(), dst, exps);
+    k_split<<<(unsigned)tu, SPLIT_THREADS, 0, s>>>(src, dju, dpu, (int)jobs.size(), dst, exps);
     CK_LAUNCH();
 }
 
