@@ -14,6 +14,7 @@ finite elements"), cited by section / equation:
                                 the Section 6 tests use two aggregation passes)
 * Section 2, eqs. (2.3)-(2.4)   row-touching set and G-row closure Omega_i
 * Section 5.4, Def. 5.4/Thm 5.6 element closure (= G-row closure structurally)
+* Section 5.3, Def. 5.2         algebraic A-closure (the Table 2 comparison), option A=
 * Section 2, eqs. (2.5)-(2.7)   multiplicity, weights, exact SPSD splitting
 * Section 2, eqs. (2.8)-(2.9)   local GEP and its Schur-complement reduction
 * Section 2, eq. (2.10)         tau_cut = c * max_j mult(j)
@@ -29,9 +30,10 @@ pseudo-inverse tolerance, eigenvector normalisation) are stated at each function
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test in
 ``tests/test_oracle_pins.py`` against a property the paper or the mathematics
-fixes (identities, brute force, textbook routines, bounds).  Parity unpinned:
-absolute iteration counts and operator complexity relative to the paper's own
-(triangle/Firedrake) runs, and the sign/rotation of individual Z_i columns
+fixes (identities, brute force, textbook routines, bounds, and the Table 2 counts the
+paper prints for the smallest CG(1) mesh, stored under tests/golden/).  Parity
+unpinned: absolute iteration counts and operator complexity relative to the paper's
+own larger (triangle/Firedrake) runs, and the sign/rotation of individual Z_i columns
 (only the spanned projectors are pinned).
 """
 from __future__ import annotations
