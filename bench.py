@@ -293,6 +293,16 @@ def cpu_cores():
     return int(blas or os.cpu_count() or 1)
 
 
+def throughput_entry(n, nrhs, setup_s, solve_s, its):
+    """Set-up and solve throughput of a step: DOFs set up per second, and DOF-iterations per
+    second of the solve (DOFs x right-hand sides x iterations / solve seconds), iterations the
+    mean over the timed steps (each step's maximum over its right-hand sides)."""
+    its_mean = float(np.mean(its)) if len(its) else 0.0
+    return dict(setup_dofs_per_s=(n / setup_s if setup_s > 0 else None),
+                solve_dof_iterations_per_s=(n * nrhs * its_mean / solve_s if solve_s > 0 else None),
+                iterations=its_mean)
+
+
 def cpu_baseline_entry(cfg, n_full, runs=1):
     """The oracle timed on its bounded sample with all BLAS threads and with one; `value` is the
     measured all-thread time of one sample step.  A DOF-ratio extrapolation to the full workload is
@@ -548,6 +558,8 @@ def main():
                     options=opts, l2=l2_note(c),
                     parallelism=f"replicas x{world}"),
         setup_s=statistics.mean(setups), solve_s=statistics.mean(solves), iters=its_list,
+        throughput=throughput_entry(n, int(c["b"].shape[0]), statistics.mean(setups), statistics.mean(solves),
+                                    its_list),
         warmup_modes={("fp32_vcycle_fcg" if m == 1 else "fp64_pcg"): v for m, v in modes.items()},
         residual_note="relres: the Krylov recurrence's ||r_k|| / ||b||, the stopping test; true_relres: "
                       "||b - A x|| / ||b|| evaluated in FP64, which cannot fall much below "

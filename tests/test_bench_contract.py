@@ -41,3 +41,15 @@ def test_l2_note_flags_reduced_sizes():
     import bench
     assert bench.l2_note(bench.workload(256)).startswith("inputs larger than L2")
     assert bench.l2_note(bench.workload(16)).startswith("inputs smaller than L2")
+
+
+def test_throughput_entry():
+    sys.path.insert(0, ROOT)
+    import bench
+    t = bench.throughput_entry(2_000_000, 16, 10.0, 4.0, [10, 12])
+    assert t["setup_dofs_per_s"] == 200_000.0
+    assert t["solve_dof_iterations_per_s"] == 2_000_000 * 16 * 11.0 / 4.0
+    assert t["iterations"] == 11.0
+    z = bench.throughput_entry(5, 1, 0.0, 0.0, [])
+    assert z["setup_dofs_per_s"] is None and z["solve_dof_iterations_per_s"] is None
+    json.dumps(t)
