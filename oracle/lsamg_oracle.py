@@ -48,7 +48,7 @@ import scipy.sparse as sp
 EPS = np.finfo(np.float64).eps
 
 __all__ = [
-    "hash32", "assemble", "element_gram", "structural_graph", "mis2", "aggregate_mis2",
+    "hash32", "assemble", "element_gram", "structural_graph", "mis2", "aggregate_mis2", "aggregate_greedy",
     "aggregate_two_pass", "closure", "local_problem", "local_problem_pinv", "local_gram_rows", "Level", "Hierarchy", "setup",
     "vcycle", "stationary", "pcg", "fcg", "elem_grad", "adjoint_grad", "gram_spmv", "greedy_colouring",
     "options_default",
@@ -61,9 +61,13 @@ __all__ = [
 def options_default():
     """Paper defaults: c = 0.75 (Section 6.1/6.3), 2 aggregation passes, at most 3 levels,
     stop below 10 DOFs or above 25 % density (Section 6 preamble); the G-row closure
-    (closure="A" selects the algebraic A-closure of the Section 5 comparison)."""
+    (closure="A" selects the algebraic A-closure of the Section 5 comparison).  Two
+    comparison options: aggregation="greedy" (the sequential greedy pass instead of MIS(2))
+    and sweep_order="natural" (the multiplicative sweep in aggregate index order instead of
+    colour-major order)."""
     return dict(tau_c=0.75, agg_passes=2, agg_passes_coarse=2, max_levels=3, min_coarse=10,
-                max_density=0.25, rtol=1e-8, maxit=1000, closure="G")
+                max_density=0.25, rtol=1e-8, maxit=1000, closure="G", aggregation="mis2",
+                sweep_order="colour")
 
 
 # -----------------------------------------------------------------------------
@@ -225,15 +229,58 @@ def aggregate_mis2(S, prio):
     return agg, len(roots)
 
 
-def aggregate_two_pass(S, passes=2):
-    """Compose ``passes`` MIS(2) aggregation passes: pass 1 on the node graph S, pass k+1 on
-    the graph of pass-k aggregates (adjacent iff any members are adjacent)."""
+def aggregate_greedy(S):
+    """One pass of the sequential greedy ("standard", Vanek-Mandel-Brezina) aggregation, the
+    kind of routine the paper's serial implementation used; kept as a second option to show
+    that iteration counts and operator complexity do not hinge on the MIS(2) reading.
+    Step 1: visiting nodes in index order, a node whose whole distance-1 neighbourhood is
+    still free becomes a root and its neighbourhood an aggregate (ids in root order).
+    Step 2: every node left free joins the aggregate of its first (lowest-index) neighbour
+    that step 1 aggregated.  Step 3: nodes still free (none on a structural graph, where each
+    of them has an aggregated neighbour) form aggregates with their free neighbours, in
+    index order.  Returns (labels, number of aggregates)."""
+    n = S.shape[0]
+    ptr, idx = S.indptr, S.indices
+    agg = np.full(n, -1, np.int64)
+    nagg = 0
+    for i in range(n):
+        nb = idx[ptr[i]:ptr[i + 1]]
+        if agg[i] < 0 and (agg[nb] < 0).all():
+            agg[nb] = nagg
+            agg[i] = nagg
+            nagg += 1
+    step1 = agg.copy()
+    for i in range(n):
+        if agg[i] < 0:
+            nb = idx[ptr[i]:ptr[i + 1]]
+            joined = nb[step1[nb] >= 0]
+            if len(joined):
+                agg[i] = step1[joined.min()]
+    for i in range(n):
+        if agg[i] < 0:
+            nb = idx[ptr[i]:ptr[i + 1]]
+            free = nb[agg[nb] < 0]
+            agg[free] = nagg
+            agg[i] = nagg
+            nagg += 1
+    return agg, nagg
+
+
+def aggregate_two_pass(S, passes=2, method="mis2"):
+    """Compose ``passes`` aggregation passes (MIS(2), or the greedy pass with
+    method="greedy"): pass 1 on the node graph S, pass k+1 on the graph of pass-k aggregates
+    (adjacent iff any members are adjacent)."""
+    if method not in ("mis2", "greedy"):
+        raise ValueError(f"unknown aggregation {method!r}")
     n = S.shape[0]
     agg = np.arange(n)
     Sk = S
     nagg = n
     for _ in range(passes):
-        a, nagg = aggregate_mis2(Sk, hash32(np.arange(Sk.shape[0])))
+        if method == "greedy":
+            a, nagg = aggregate_greedy(Sk)
+        else:
+            a, nagg = aggregate_mis2(Sk, hash32(np.arange(Sk.shape[0])))
         agg = a[agg]
         C = sp.csr_matrix((np.ones(len(a)), (np.arange(len(a)), a)), shape=(len(a), nagg))
         Sk = (C.T @ Sk @ C).tocsr()
@@ -508,12 +555,12 @@ def setup(n, elems, mats, opts=None, c_tau=None):
             Ad = lev.A.toarray()
             lev.Ldense = np.linalg.cholesky(0.5 * (Ad + Ad.T))
             return H
-        _smoother_setup(lev)
+        _smoother_setup(lev, o.get("sweep_order", "colour"))
         lev = nxt
 
 
 def _coarsen(lev, o, passes):
-    agg, nagg = aggregate_two_pass(lev.S, passes)
+    agg, nagg = aggregate_two_pass(lev.S, passes, o.get("aggregation", "mis2"))
     if o.get("closure", "G") not in ("G", "A"):
         raise ValueError(f"unknown closure {o['closure']!r}")
     eagg, mult, ael, omega, Omega = closure(lev.elems, agg, nagg, A=lev.A if o.get("closure") == "A" else None)
@@ -579,9 +626,12 @@ def _coarsen(lev, o, passes):
     return Level(n=nc, elems=celems, mats=cmats, G=cG)
 
 
-def _smoother_setup(lev):
+def _smoother_setup(lev, order="colour"):
     """Multiplicative Schwarz on the overlaps Omega_i with exact local solves
-    A_Omega = R_Omega A R_Omega^T (Section 2; Section 6 preamble)."""
+    A_Omega = R_Omega A R_Omega^T (Section 2; Section 6 preamble); the forward sweep visits
+    the subdomains colour by colour (order="colour") or in index order (order="natural")."""
+    if order not in ("colour", "natural"):
+        raise ValueError(f"unknown sweep order {order!r}")
     nagg = lev.nagg
     ne = len(lev.elems)
     # B[i, T] = 1 iff element T meets Omega_i
@@ -600,7 +650,8 @@ def _smoother_setup(lev):
     C.eliminate_zeros()
     C.sort_indices()
     lev.colour = greedy_colouring(C)
-    lev.sweep = sorted(range(nagg), key=lambda i: (lev.colour[i], i))
+    lev.sweep = (sorted(range(nagg), key=lambda i: (lev.colour[i], i)) if order == "colour"
+                 else list(range(nagg)))
     lev.chol = []
     for i in range(nagg):
         Om = lev.Omega[i]

@@ -793,3 +793,76 @@ def test_table2_meshes_and_smallest_case_iterations():
         _, got[cl], rel = O.stationary(H, np.zeros(n), x0, rtol=1e-10)
     assert abs(got["G"] - its_g) <= 1, got
     assert got["A"] >= got["G"], got
+
+
+def _grid5(m):
+    rows, cols = [], []
+    for i in range(m):
+        for j in range(m):
+            for di, dj in ((0, 0), (1, 0), (-1, 0), (0, 1), (0, -1)):
+                a, b = i + di, j + dj
+                if 0 <= a < m and 0 <= b < m:
+                    rows.append(m * i + j)
+                    cols.append(m * a + b)
+    S = sp.csr_matrix((np.ones(len(rows)), (rows, cols)), shape=(m * m, m * m))
+    S.sort_indices()
+    return S
+
+
+def test_greedy_aggregation_worked_by_hand():
+    """The sequential greedy pass on two graphs worked out by hand: a path of 10 nodes (roots
+    0, 3, 6, 9 take their neighbourhoods) and the 3 x 3 five-point grid (roots 0 and 5; nodes 6
+    and 7 join the aggregates of their lowest-index aggregated neighbours 3 and 4)."""
+    n = 10
+    S = sp.diags([np.ones(n - 1), np.ones(n), np.ones(n - 1)], [-1, 0, 1], format="csr")
+    S.sort_indices()
+    agg, nagg = OL.aggregate_greedy(S)
+    assert nagg == 4 and agg.tolist() == [0, 0, 1, 1, 1, 2, 2, 2, 3, 3]
+    agg, nagg = OL.aggregate_greedy(_grid5(3))
+    assert nagg == 2 and agg.tolist() == [0, 0, 1, 0, 1, 1, 0, 1, 1]
+
+
+def test_greedy_aggregation_properties(cfg1):
+    """On the structural graph of the 16 x 16 RT_[0] mesh: a disjoint cover by connected
+    aggregates, each holding a root whose whole neighbourhood lies inside it."""
+    c, _, _ = cfg1
+    S = OL.structural_graph(c["n"], c["elem_dofs"])
+    agg, nagg = OL.aggregate_greedy(S)
+    assert agg.min() == 0 and agg.max() == nagg - 1 and len(np.unique(agg)) == nagg
+    for a in range(nagg):
+        mem = np.flatnonzero(agg == a)
+        sub = S[mem][:, mem]
+        ncomp, _ = sp.csgraph.connected_components(sub, directed=False)
+        assert ncomp == 1
+        assert any(set(S.indices[S.indptr[p]:S.indptr[p + 1]]) <= set(mem.tolist()) for p in mem)
+
+
+def test_aggregation_and_sweep_order_readings_give_comparable_solvers(cfg1):
+    """The two readings the paper leaves open (the aggregation routine; the order of the
+    multiplicative sweep) move the iteration counts by at most one on the 16 x 16 RT_[0]
+    mesh (PCG) and on the Table 2 CG(1) mesh (stationary cycle), and the operator
+    complexity by less than a factor of two."""
+    c, mats, H0 = cfg1
+    A = H0.levels[0].A
+    b = c["b"][0]
+    its, ocs = [], []
+    for agg in ("mis2", "greedy"):
+        for order in ("colour", "natural"):
+            H = O.setup(c["n"], c["elem_dofs"], mats, c_tau=c["c_tau"],
+                        opts=dict(aggregation=agg, sweep_order=order))
+            x, it, _ = O.pcg(lambda v: A @ v, b, lambda r: O.vcycle(H, r))
+            assert np.linalg.norm(b - A @ x) <= 1e-8 * np.linalg.norm(b)
+            its.append(it)
+            ocs.append(H.stats()["OC"])
+    assert max(its) - min(its) <= 1, its
+    assert max(ocs) < 2 * min(ocs), ocs
+    n, d, K = fegen.cg1_tri(32)
+    x0 = np.random.default_rng(32).uniform(-1, 1, n)
+    its = []
+    for agg in ("mis2", "greedy"):
+        for order in ("colour", "natural"):
+            H = O.setup(n, d, np.ascontiguousarray(K), opts=dict(tau_c=1.0, aggregation=agg, sweep_order=order))
+            its.append(O.stationary(H, np.zeros(n), x0, rtol=1e-10)[1])
+    assert max(its) - min(its) <= 1, its
+    with pytest.raises(ValueError):
+        OL.aggregate_two_pass(OL.structural_graph(c["n"], c["elem_dofs"]), 2, "vanek")
