@@ -31,7 +31,7 @@ pseudo-inverse tolerance, eigenvector normalisation) are stated at each function
 Parity status: every function here is pinned by a ``-m "not gpu"`` test in
 ``tests/test_oracle_pins.py`` against a property the paper or the mathematics
 fixes (identities, brute force, textbook routines, bounds, and the Table 2 counts the
-paper prints for the smallest CG(1) mesh, stored under tests/golden/).  Parity
+paper prints for the two smallest CG(1) meshes, stored under tests/golden/).  Parity
 unpinned: absolute iteration counts and operator complexity relative to the paper's
 own larger (triangle/Firedrake) runs, and the sign/rotation of individual Z_i columns
 (only the spanned projectors are pinned).

@@ -775,24 +775,27 @@ def _table2():
 
 def test_table2_meshes_and_smallest_case_iterations():
     """Table 2 (Section 5.3) as printed: the DOF counts are those of CG(1) on N x N squares cut
-    into right triangles, N = 32 ... 1024 (vertices of the mesh), and on the smallest mesh the
-    oracle's stationary cycle with the G-row closure takes the printed count within one
-    iteration, while the A-closure takes at least as many (the A-closure drops interface DOFs
-    whose entries cancel, so its splitting is no longer the exact one of Theorem 3.2)."""
+    into right triangles, N = 32 ... 1024 (vertices of the mesh), and on the two smallest
+    meshes the oracle's stationary cycle with the G-row closure takes the printed count within
+    one iteration, while the A-closure takes at least as many, and more where the printed
+    counts differ (the A-closure drops interface DOFs whose entries cancel, so its splitting is
+    no longer the exact one of Theorem 3.2)."""
     rows = _table2()
     assert [r[0] for r in rows] == [(N + 1) ** 2 for N in (32, 64, 128, 256, 512, 1024)]
     for N, (dofs, _, _) in zip((32, 64, 128), rows):
         n, d, K = fegen.cg1_tri(N)
         assert n == dofs and d.shape == (2 * N * N, 3)
-    dofs, its_a, its_g = rows[0]
-    n, d, K = fegen.cg1_tri(32)
-    x0 = np.random.default_rng(32).uniform(-1, 1, n)
-    got = {}
-    for cl in ("G", "A"):
-        H = O.setup(n, d, np.ascontiguousarray(K), opts=dict(tau_c=1.0, closure=cl))
-        _, got[cl], rel = O.stationary(H, np.zeros(n), x0, rtol=1e-10)
-    assert abs(got["G"] - its_g) <= 1, got
-    assert got["A"] >= got["G"], got
+    for N, (dofs, its_a, its_g) in zip((32, 64), rows[:2]):
+        n, d, K = fegen.cg1_tri(N)
+        x0 = np.random.default_rng(N).uniform(-1, 1, n)
+        got = {}
+        for cl in ("G", "A"):
+            H = O.setup(n, d, np.ascontiguousarray(K), opts=dict(tau_c=1.0, closure=cl))
+            _, got[cl], rel = O.stationary(H, np.zeros(n), x0, rtol=1e-10)
+        assert abs(got["G"] - its_g) <= 1, (N, got)
+        assert got["A"] >= got["G"], (N, got)
+        if its_a > its_g:   # the printed gap has opened (4,225 DOFs): it is open here too
+            assert got["A"] > got["G"], (N, got)
 
 
 def _grid5(m):
